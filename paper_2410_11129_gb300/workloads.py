@@ -1,0 +1,92 @@
+"""Synthetic workloads shaped like the paper's channels (arXiv 2410.11129, Sec. 2.5-2.6).
+
+Plain parameter dictionaries and the seeded draw of the batched sweep; no
+arithmetic of the method lives here, so both the CUDA path and the CPU oracle
+read their inputs from this one module. Per-phase values follow Eq. 39's
+ratio convention: rho_r = rho1/rho2 = rho3/rho2 and nu_r = nu1/nu2 = nu3/nu2,
+with the carrier at rho3 = 1, nu3 = 1/6 (tau3 = 1/2).
+"""
+import math
+
+import numpy as np
+
+NU3 = 1.0 / 6.0
+
+
+def _phases(rho_r=1.0, nu_r=1.0):
+    return {"rho": [1.0, 1.0 / rho_r, 1.0], "nu": [NU3, NU3 / nu_r, NU3]}
+
+
+def channel(nx, ny, r1, r2, xc=None, yc=None, xi=5.0, rho_r=1.0, nu_r=1.0, Ca=0.15,
+            Bo_m=0.0, alpha_deg=0.0, ferro="shell", chi_ferro=1.0, u_max=0.01,
+            mag_tol=1e-10, mag_max_iter=200, s13_over_s12=1.0, s23_over_s12=1.0, **extra):
+    """A compound droplet in a periodic, body-force-driven channel."""
+    chi = [0.0, 0.0, 0.0]
+    fp = 0
+    if ferro == "core":
+        chi[0], fp = chi_ferro, 1
+    elif ferro == "shell":
+        chi[1], fp = chi_ferro, 2
+    cfg = {
+        "nx": int(nx), "ny": int(ny), "r1": float(r1), "r2": float(r2),
+        "xc": float(4 * r1 if xc is None else xc),
+        "yc": float(0.5 * (ny - 1) if yc is None else yc),
+        "xi": float(xi), "mobility": 0.3, "eta": 0.0, "chi": chi, "ferro_phase": fp,
+        "Ca": float(Ca), "Bo_m": float(Bo_m), "alpha": math.radians(alpha_deg),
+        "u_max": float(u_max), "mag_tol": float(mag_tol), "mag_max_iter": int(mag_max_iter),
+        "s13_over_s12": float(s13_over_s12), "s23_over_s12": float(s23_over_s12),
+        "sigma23": 0.0, "eps_n": 1e-12,
+    }
+    cfg.update(_phases(rho_r, nu_r))
+    cfg.update(extra)
+    return cfg
+
+
+# 200x40 FP64 parity channel: shell ferrofluid (chi = 1), Ca 0.1, Bo_m 1, alpha 0.
+C1 = dict(channel(200, 40, 6, 12, xc=50, xi=4.0, Ca=0.1, Bo_m=1.0, alpha_deg=0.0,
+                  ferro="shell", chi_ferro=1.0), name="channel-200x40-fp64", steps=1000,
+          precision="fp64")
+
+# 1600x200 FP32 production channel: core ferrofluid (chi = 2), rho_r = nu_r = 2,
+# Ca 0.2, Bo_m 3, alpha 90 deg; droplet centre 4 r1 from the inlet.
+C2 = dict(channel(1600, 200, 30, 60, Ca=0.2, Bo_m=3.0, alpha_deg=90.0, ferro="core",
+                  chi_ferro=2.0, rho_r=2.0, nu_r=2.0, mag_tol=1e-5),
+          name="channel-1600x200-fp32", steps=100000, precision="fp32")
+
+# 2400x300 precision-study channel: the 1600x200 case scaled by 1.5.
+C3 = dict(channel(2400, 300, 45, 90, Ca=0.2, Bo_m=3.0, alpha_deg=90.0, ferro="core",
+                  chi_ferro=2.0, rho_r=2.0, nu_r=2.0, mag_tol=1e-5),
+          name="channel-2400x300", steps=50000, precision="fp32")
+
+# 800x100 gradient channel: shell ferrofluid, Ca 0.15, Bo_m 2, alpha 0.
+C5 = dict(channel(800, 100, 15, 30, Ca=0.15, Bo_m=2.0, alpha_deg=0.0, ferro="shell"),
+          name="channel-800x100", steps=20000, precision="fp64")
+
+# L2-busting roofline channel: the 1600x200 physics on 9600x1200 (droplet x6).
+ROOF = dict(channel(9600, 1200, 180, 360, Ca=0.2, Bo_m=3.0, alpha_deg=90.0, ferro="core",
+                    chi_ferro=2.0, rho_r=2.0, nu_r=2.0, mag_tol=1e-5),
+            name="channel-9600x1200-fp32", steps=200, precision="fp32")
+
+
+def regime_sweep(seed=12345, n_len_align=32):
+    """96 instances: Bo_m x Ca x {core, shell}; lengths U[800, 2400] (rounded down
+    to a multiple of n_len_align), height 200, r1/r2 U[0.3, 0.7] with r2 = 60."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for ferro in ("core", "shell"):
+        for Bo in (0.0, 0.5, 1.0, 2.0, 4.0, 8.0):
+            for Ca in (0.05, 0.1, 0.15, 0.2, 0.3, 0.4, 0.5, 0.6):
+                L = int(rng.uniform(800, 2400)) // n_len_align * n_len_align
+                rr = float(rng.uniform(0.3, 0.7))
+                r2 = 60.0
+                out.append(channel(L, 200, rr * r2, r2, xc=2 * r2 + 10, Ca=Ca, Bo_m=Bo,
+                                   ferro=ferro, mag_tol=1e-5))
+    return out
+
+
+def small(nx=48, ny=20, **kw):
+    """Small droplet channel for parity tests: spans several tiles and a ragged tail."""
+    base = dict(r1=3.0, r2=6.0, xc=14.0, xi=4.0, Ca=0.1, Bo_m=1.0, ferro="shell",
+                chi_ferro=1.0)
+    base.update(kw)
+    return channel(nx, ny, **base)
