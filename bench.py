@@ -1,0 +1,314 @@
+#!/usr/bin/env python
+"""Coupled-step throughput (MLUPS) of the ferrofluid compound-droplet step.
+
+Workload: the 1600x200 FP32 production channel (core ferrofluid, chi 2,
+rho_r = nu_r = 2, Ca 0.2, Bo_m 3, alpha 90 deg, r1 30, r2 60). One step is
+one pass of the whole hot path: phase recovery, multigrid potential solve to
+the channel's tolerance, fused forces + MRT/BGK collide-stream, step counter.
+
+The state (69 MB) fits in L2, so a 256 MiB buffer is written between timed
+steps and only the step itself sits between the CUDA events. Multi-GPU runs
+(torchrun) are independent replicas of the channel, one per GPU.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "coupled-step MLUPS vs HBM roofline; plain vs batched/adjoint at stated error"
+UNIT = "MLUPS"
+FALLBACK_HBM_GBS = 6800.0
+# Algorithmic bytes per node of one collide-stream launch in FP32: f read+write
+# (18 x 4), g read+write (36 x 4), phi_1, phi_2 read (8), psi' read (4) and the
+# stored u_x, u_y, p* (12).
+COLLIDE_BYTES_PER_NODE_F32 = 240
+# DRAM bytes per collide launch measured by ncu on this workload, keyed by the
+# hash of the kernel source it was taken on (null once the source changes).
+NCU_TRAFFIC = {}
+
+
+def kernel_source_hash():
+    p = os.path.join(ROOT, "paper_2410_11129_gb300", "csrc", "fcd_lbm.cu")
+    with open(p, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of the GPU during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.rows = []
+        self.proc = None
+        self.t = None
+
+    def start(self):
+        cmd = ["nvidia-smi", "--query-gpu=" + self.QUERY, "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.t:
+            self.t.join(timeout=5)
+        sm, mx, reasons = [], None, set()
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except ValueError:
+                continue
+            for name, v in zip(self.NAMES, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def oracle_rate(cfg, min_seconds, max_steps, warmup=1):
+    """MLUPS of the FP64 C oracle (single thread) over a bounded sample."""
+    import oracle
+    oracle.build()
+    sim = oracle.Sim(dict(cfg, mag_max_iter=100000))
+    for _ in range(warmup):
+        sim.step(1)
+    t0 = time.perf_counter()
+    n = 0
+    while n < max_steps and (n == 0 or time.perf_counter() - t0 < min_seconds):
+        sim.step(1)
+        n += 1
+    dt = time.perf_counter() - t0
+    return cfg["nx"] * cfg["ny"] * n / dt / 1e6, n, dt
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2410_11129_gb300 import workloads as W
+    cfg = dict(W.C2)
+    budget = float(os.environ.get("FCD_REF_BUDGET_S", "150"))
+    import oracle
+    oracle.build()
+    sim = oracle.Sim(dict(cfg, mag_max_iter=100000))
+    for _ in range(args.warmup):
+        sim.step(1)
+    times = []
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        sim.step(1)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_all > budget:
+            break
+    N = cfg["nx"] * cfg["ny"]
+    tot = sum(times)
+    value = N * len(times) / tot / 1e6
+    sample = ("%s, %d of %d timed steps after %d warm-up steps (whole-grid FP64 oracle steps; "
+              "the run stops at a %.0f s budget)" % (cfg["name"], len(times), args.steps,
+                                                     args.warmup, budget))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": len(times), "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": cfg["name"], "nx": cfg["nx"], "ny": cfg["ny"],
+                   "mag_tol": cfg["mag_tol"], "parallelism": "host, 1 thread"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2410_11129_gb300 import fcd
+    from paper_2410_11129_gb300 import workloads as W
+
+    cfg = dict(W.C2)
+    N = cfg["nx"] * cfg["ny"]
+    ch = fcd.Channel(cfg)
+    ch.set_profiling(True)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        ch.step(1)
+    barrier()
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        uuid = None
+    clk = ClockSampler(uuid)
+    clk.start()
+    time.sleep(0.3)
+    n0 = ch.kernel_launches()
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stage = {"phase": 0.0, "solve": 0.0, "collide": 0.0}
+    cycles = 0
+    barrier()
+    for i in range(args.steps):
+        flush.zero_()                 # L2 flush, outside the timed interval
+        ev0[i].record(stream)
+        ch.step(1)
+        ev1[i].record(stream)
+        prof = ch.last_step_profile()  # synchronises on the step's last event
+        for k in stage:
+            stage[k] += prof[k]
+    barrier()
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    n1 = ch.kernel_launches()
+    obs = ch.observe(allow=(fcd.FCD_ENOCONV,))
+    clocks = clk.stop()
+    total_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = N * args.steps * ws / (total_ms * 1e-3) / 1e6
+
+    # End to end through the C ABI with host buffers: state in (h2d), one step,
+    # state out (d2h), every step.
+    nb = ch.state_bytes()
+    host_in = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
+    host_out = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
+    ch.get_state(host_in)
+    ke = max(3, min(args.steps, 50))
+    for _ in range(2):
+        ch.set_state(host_in)
+        ch.step(1)
+        ch.get_state(host_out)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        ch.set_state(host_in)
+        ch.step(1)
+        ch.get_state(host_out)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / ke
+    e2e = {"value": N * ws / e2e_s / 1e6, "unit": UNIT, "h2d_bytes_per_step": nb,
+           "d2h_bytes_per_step": nb, "steps": ke}
+
+    peak, peak_kind = measured_peak()
+    coll_ms = stage["collide"] / args.steps
+    achieved = COLLIDE_BYTES_PER_NODE_F32 * N / (coll_ms * 1e-3) / 1e9
+    h = kernel_source_hash()
+    traffic = NCU_TRAFFIC.get(h)
+    roofline = {"bound": "hbm", "kernel": "collide_kernel<float, offset-free FP32>",
+                "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "algorithmic_bytes_per_launch": COLLIDE_BYTES_PER_NODE_F32 * N,
+                "launch_ms": coll_ms}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": cfg["name"], "nx": cfg["nx"], "ny": cfg["ny"],
+                   "precision": cfg["precision"], "mag_tol": cfg["mag_tol"],
+                   "l2": "256 MiB buffer written between timed steps (state is 69 MB < L2)",
+                   "parallelism": "replicas x%d" % ws},
+        "stage_ms_per_step": {k: v / args.steps for k, v in stage.items()},
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": int(n1 - n0),
+        "mag_cycles_last_solve": obs["mag_iters"], "mag_resid_last_solve": obs["mag_resid"],
+        "clocks": clocks,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        v, n, dt = oracle_rate(cfg, min_seconds=10.0, max_steps=30)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": "%s, %d whole-grid FP64 oracle steps (%.1f s) after "
+                                          "initialisation and one warm-up step" % (cfg["name"], n, dt)}
+    ch.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

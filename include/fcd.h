@@ -1,0 +1,177 @@
+/*
+ * fcd.h -- C ABI of the GB300 (sm_103a) coupled time step of the ferrofluid
+ * compound-droplet model of arXiv 2410.11129 ("Deformation and breakup of a
+ * ferrofluid compound droplet migrating in a microchannel under a magnetic
+ * field: a phase-field-based multiple-relaxation time lattice Boltzmann study").
+ *
+ * One step advances, on one GPU:
+ *   - the phase fields phi_1 (core), phi_2 (shell) by the conservative
+ *     Allen-Cahn lattice Boltzmann equation (Sec. 2.3-2.4, Eqs. 23-32),
+ *   - the magnetic scalar potential psi of div[(1+chi) grad psi] = 0 under a
+ *     uniform field H0 at angle alpha (Sec. 2.1, Eqs. 1-9), solved by multigrid,
+ *   - the ternary flow by the D2Q9 MRT lattice Boltzmann equation with surface
+ *     tension, Kelvin, pressure, viscous and driving forces (Sec. 2.2, Eqs. 10-22),
+ *   - half-way bounce-back walls at y = -1/2 and y = ny - 1/2, periodic x.
+ *
+ * Conventions shared by every call:
+ *   - Every call returns an fcd_status; none aborts, traps or exits. On failure
+ *     fcd_last_error() holds a one-line reason.
+ *   - The context owns its device memory (allocated in fcd_create through the
+ *     allocator installed by fcd_set_allocator, else cudaMalloc) and frees it in
+ *     fcd_destroy. Buffers passed in by the caller stay the caller's.
+ *   - Work is queued on the context's stream (fcd_set_stream; default: the
+ *     legacy default stream). fcd_step returns once the work is queued; calls
+ *     that return data to the host synchronise that stream.
+ *   - Lattice units: dx = dt = 1, c_s^2 = 1/3, mu0 = 1.
+ *   - Field arrays exchanged with the caller are FP64, row-major, unpadded:
+ *     a[y*nx + x]; populations f[a][y][x] (9 planes, D2Q9 order rest, E, N,
+ *     W, S, NE, NW, SW, SE), g[i][a][y][x] (2 x 9 planes, i = 0 core, 1 shell).
+ *     Pointers may be host or device memory (unified addressing decides).
+ */
+#ifndef FCD_H
+#define FCD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fcd_ctx fcd_ctx;
+
+typedef enum {
+    FCD_OK = 0,
+    FCD_EINVAL = 1,     /* bad argument or parameter set */
+    FCD_ENOMEM = 2,     /* device allocation failed */
+    FCD_ECUDA = 3,      /* a CUDA call failed; the message names it */
+    FCD_ENOCONV = 4,    /* potential solve hit its cycle cap before the tolerance */
+    FCD_EUNSTABLE = 5,  /* non-finite values detected */
+    FCD_ESTATE = 6      /* snapshot does not match this context */
+} fcd_status;
+
+typedef enum { FCD_FP64 = 0, FCD_FP32 = 1, FCD_FP32_OFFSET = 2 } fcd_precision;
+
+/* Problem statement of Sec. 2.5 in lattice units. Phases: 1 core, 2 shell,
+ * 3 carrier (index 0, 1, 2 in the arrays). */
+typedef struct {
+    int nx, ny;            /* lattice nodes along / across the channel; nx even, >= 4; ny >= 2 */
+    double rho[3];         /* densities (Eq. 33 mixes them linearly) */
+    double nu[3];          /* kinematic viscosities; tau_i = nu_i / c_s^2 (Eq. 14) */
+    double chi[3];         /* magnetic susceptibilities (Eq. 8 mixes 1 + chi harmonically) */
+    double mobility;       /* M of Eq. 30 (0.3 in the paper) */
+    double xi;             /* interface width (Eq. 23; 5 in the paper) */
+    double eta;            /* Eq. 28 eta (0: partial spreading) */
+    double Ca;             /* Eq. 40, fixes sigma_23 = rho3 nu3 u_avg / Ca */
+    double Bo_m;           /* Eq. 41, fixes mu0 H0^2 */
+    double alpha;          /* field angle to the x axis, radians */
+    double r1, r2;         /* core and shell radii */
+    double xc, yc;         /* droplet centre */
+    double s13_over_s12;   /* sigma_13 / sigma_12 (Table 2) */
+    double s23_over_s12;   /* sigma_23 / sigma_12 (Table 2) */
+    double sigma23;        /* > 0: use this sigma_23 instead of the Eq. 40 relation */
+    double u_max;          /* centre-line speed of the body-force-driven channel flow */
+    int ferro_phase;       /* 1 core, 2 shell, 0 none: selects the Eq. 41 branch */
+    int precision;         /* fcd_precision: storage and arithmetic of the populations */
+    double mag_tol;        /* potential solve target ||L psi||_inf / H0 per step */
+    int mag_max_iter;      /* multigrid V-cycle cap per solve */
+    double eps_n;          /* regulariser of n = grad phi / (|grad phi| + eps_n) */
+} fcd_params;
+
+/* Observables (Sec. 2.5, Eqs. 38 and 42). */
+typedef struct {
+    long step;              /* time steps taken since fcd_create */
+    double t_star;          /* Eq. 38: step * u_avg / (2 r2), u_avg = 2 u_max / 3 */
+    double T_o, T_i;        /* Eq. 42 deformation of the shell and the core */
+    double lx_o, ly_o, lx_i, ly_i; /* extents of the 1/2 level sets */
+    double xc_core, yc_core, xc_shell, yc_shell; /* indicator-weighted centroids */
+    double mass[3];         /* sum over nodes of phi_1, phi_2, phi_3 (FP64) */
+    int breakup;            /* 1 once the core has touched the carrier */
+    long b_step;            /* step of the first touch, -1 if none */
+    double xb, yb;          /* node of the first touch (smallest (y, x)) */
+    double tb_star, Lb_star, yb_star; /* t_b* (Eq. 38), x_b / H, |y_b - centre| / H */
+    int mag_iters;          /* V-cycles of the most recent potential solve */
+    double mag_resid;       /* its final ||L psi||_inf / H0 */
+} fcd_obs;
+
+/* Fields for fcd_get_field (FP64, nx*ny values). The macroscopic fields are
+ * those of the most recent collision (initial values right after create). */
+typedef enum {
+    FCD_FIELD_PHI1 = 0, FCD_FIELD_PHI2 = 1, FCD_FIELD_PHI3 = 2,
+    FCD_FIELD_UX = 3, FCD_FIELD_UY = 4, FCD_FIELD_PSTAR = 5, FCD_FIELD_PSI = 6
+} fcd_field;
+
+/* Optional allocator used by later fcd_create calls (process-wide; NULL
+ * restores cudaMalloc/cudaFree). alloc returns a device pointer or NULL. */
+typedef void *(*fcd_alloc_fn)(size_t bytes, void *user);
+typedef void (*fcd_free_fn)(void *ptr, void *user);
+void fcd_set_allocator(fcd_alloc_fn alloc, fcd_free_fn release, void *user);
+
+/* Maps the dimensionless groups to lattice units (Eqs. 14, 26-27, 30, 40-41),
+ * allocates the state, sets the initial condition (concentric tanh profiles
+ * of width xi, Poiseuille flow, f = f^eq, g = phi Gamma) and solves the
+ * potential once. EINVAL for nx odd or < 4, ny < 2, r1 > r2, non-positive
+ * density, viscosity, mobility or xi, a gamma_i <= 0 (total spreading, Eq. 27),
+ * or an Eq. 41 branch without a magnetic phase. *out is NULL on failure. */
+fcd_status fcd_create(const fcd_params *params, fcd_ctx **out);
+
+/* Queue later work on this cudaStream_t (passed as void*). */
+fcd_status fcd_set_stream(fcd_ctx *ctx, void *cuda_stream);
+
+/* Advance n >= 0 coupled steps: phase recovery (Eq. 32), permeability (Eq. 8),
+ * potential solve (Eq. 6, to mag_tol or mag_max_iter V-cycles), forces and
+ * velocity (Eqs. 5-9, 19-22, 25-28, 33-36), MRT collision of f (Eqs. 12-18),
+ * BGK collision of g^1, g^2 (Eqs. 29-31), push streaming with bounce-back.
+ * Asynchronous; an unconverged solve is reported by the next synchronising
+ * call as FCD_ENOCONV. */
+fcd_status fcd_step(fcd_ctx *ctx, long n);
+
+/* Solve the potential for the current phase fields (Eqs. 6-8). Synchronous.
+ * tol <= 0 or max_iter <= 0 take the values from the parameters. */
+fcd_status fcd_solve_magnetic(fcd_ctx *ctx, double tol, int max_iter, int *iters,
+                              double *resid);
+
+/* Observables of the current state (Eqs. 38, 42; breakup of Sec. 2.5). Synchronous. */
+fcd_status fcd_observables(fcd_ctx *ctx, fcd_obs *out);
+
+/* Copy one field (fcd_field) into dst (nx*ny doubles, host or device). Synchronous. */
+fcd_status fcd_get_field(fcd_ctx *ctx, int which, double *dst, size_t n);
+
+/* Populations and perturbation potential psi' in the FP64 exchange layout
+ * (f: 9*nx*ny, g: 18*nx*ny, psi: nx*ny); any pointer may be NULL to skip it.
+ * set_populations also sets the step counter and clears the breakup record. */
+fcd_status fcd_get_populations(fcd_ctx *ctx, double *f, double *g, double *psi);
+fcd_status fcd_set_populations(fcd_ctx *ctx, const double *f, const double *g,
+                               const double *psi, long step);
+
+/* Opaque snapshot (stored populations in the context's precision, psi',
+ * step, breakup record) for checkpoint and resume; resuming reproduces an
+ * uninterrupted run bit for bit. */
+size_t fcd_state_bytes(const fcd_ctx *ctx);
+fcd_status fcd_get_state(fcd_ctx *ctx, void *dst, size_t bytes);
+fcd_status fcd_set_state(fcd_ctx *ctx, const void *src, size_t bytes);
+
+/* Derived lattice quantities (Eqs. 14, 26-27, 30, 40-41): [u_avg, sigma12,
+ * sigma13, sigma23, gamma1..3, gammaT, tau1..3, tau_phi, mu0H0^2, H0, G]
+ * (15 doubles). */
+fcd_status fcd_get_derived(const fcd_ctx *ctx, double *out15);
+
+/* Number of kernels launched by this context since create (for accounting;
+ * synchronises to read the device-side cycle count). */
+long fcd_kernel_launches(const fcd_ctx *ctx);
+
+/* Timing of the stages of a step with CUDA events recorded on the context's
+ * stream (inside the step graph): enable, run fcd_step, then read
+ * ms4 = [phase recovery + coarse permeabilities, potential solve,
+ * collide-stream, whole step] of the most recent step (synchronises). */
+fcd_status fcd_set_profiling(fcd_ctx *ctx, int enable);
+fcd_status fcd_last_step_profile(fcd_ctx *ctx, double *ms4);
+
+/* Reason of the last failure on ctx; with ctx == NULL, of the last failed
+ * fcd_create on the calling thread. */
+const char *fcd_last_error(const fcd_ctx *ctx);
+void fcd_destroy(fcd_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,783 @@
+// fcd_api.cu -- C ABI of the coupled ferrofluid compound-droplet step
+// (arXiv 2410.11129): parameter mapping, state, CUDA-graph step loop.
+//
+// One step is captured once per (buffer parity, store-macro flag) into a CUDA
+// graph: phase recovery -> coarse permeabilities -> a while node running
+// multigrid V-cycles until the device-side control block reports convergence
+// or the cycle cap -> fused collide-stream -> step counter. fcd_step(n)
+// launches n such graphs; nothing synchronises with the host in between.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "fcd_internal.cuh"
+
+namespace fcd {
+size_t observe_scratch_doubles(int nx, int ny);
+}
+using namespace fcd;
+
+// ---------------------------------------------------------------- allocator
+static fcd_alloc_fn g_alloc = nullptr;
+static fcd_free_fn g_free = nullptr;
+static void *g_user = nullptr;
+
+static void *default_alloc(size_t bytes, void *) {
+    void *p = nullptr;
+    return cudaMalloc(&p, bytes) == cudaSuccess ? p : nullptr;
+}
+static void default_free(void *p, void *) { cudaFree(p); }
+
+extern "C" void fcd_set_allocator(fcd_alloc_fn alloc, fcd_free_fn release, void *user) {
+    if (alloc && release) {
+        g_alloc = alloc;
+        g_free = release;
+        g_user = user;
+    } else {
+        g_alloc = nullptr;
+        g_free = nullptr;
+        g_user = nullptr;
+    }
+}
+
+// ---------------------------------------------------------------- parameters
+struct Derived {
+    double u_avg, s12, s13, s23, gam[3], gamT, tau[3], tau_phi, mu0H0sq, H0, G;
+};
+
+// Lattice values of the dimensionless groups. Returns an error text or null.
+static const char *derive(const fcd_params *p, Derived *d) {
+    if (p->nx < 4 || (p->nx & 1)) return "nx must be even and >= 4";
+    if (p->ny < 2) return "ny must be >= 2";
+    if ((long long)p->nx * p->ny > (1ll << 31) - 1) return "nx*ny exceeds 2^31-1";
+    for (int i = 0; i < 3; i++) {
+        if (!(p->rho[i] > 0)) return "densities must be positive";
+        if (!(p->nu[i] > 0)) return "viscosities must be positive";
+        if (!(p->chi[i] >= 0)) return "susceptibilities must be >= 0";
+    }
+    if (!(p->mobility > 0) || !(p->xi > 0)) return "mobility and xi must be positive";
+    if (p->r1 > p->r2) return "core radius exceeds shell radius";
+    if (p->precision < FCD_FP64 || p->precision > FCD_FP32_OFFSET) return "unknown precision";
+    if (!(p->mag_tol > 0) || p->mag_max_iter < 0) return "mag_tol must be > 0, mag_max_iter >= 0";
+    if (!(p->eps_n >= 0)) return "eps_n must be >= 0";
+    if (!(p->s13_over_s12 > 0) || !(p->s23_over_s12 > 0)) return "surface tension ratios must be > 0";
+    d->u_avg = 2.0 * p->u_max / 3.0;  // mean of the channel's parabolic profile
+    double s23;
+    if (p->sigma23 > 0) s23 = p->sigma23;
+    else if (p->Ca > 0 && p->u_max > 0) s23 = p->rho[2] * p->nu[2] * d->u_avg / p->Ca;  // Eq. 40
+    else return "need Ca > 0 with u_max > 0, or sigma23 > 0";
+    const double s12 = s23 / p->s23_over_s12, s13 = p->s13_over_s12 * s12;
+    d->s12 = s12;
+    d->s13 = s13;
+    d->s23 = s23;
+    d->gam[0] = s12 + s13 - s23;  // Eq. 27
+    d->gam[1] = s12 + s23 - s13;
+    d->gam[2] = s13 + s23 - s12;
+    for (int i = 0; i < 3; i++)
+        if (!(d->gam[i] > 0)) return "a spreading coefficient gamma_i <= 0 (total spreading)";
+    d->gamT = 3.0 / (1.0 / d->gam[0] + 1.0 / d->gam[1] + 1.0 / d->gam[2]);  // Eq. 26
+    for (int i = 0; i < 3; i++) d->tau[i] = 3.0 * p->nu[i];                // Eq. 14
+    d->tau_phi = 3.0 * p->mobility;                                        // Eq. 30
+    d->mu0H0sq = 0.0;
+    if (p->ferro_phase == 1) {
+        if (!(p->chi[0] > 0) || !(p->r1 > 0)) return "core ferrofluid needs chi1 > 0 and r1 > 0";
+        d->mu0H0sq = 2.0 * s12 * p->Bo_m / (p->chi[0] * p->r1);  // Eq. 41, core
+    } else if (p->ferro_phase == 2) {
+        const double den = p->chi[1] * (p->r2 * p->r2 - p->r1 * p->r1);
+        if (!(den > 0)) return "shell ferrofluid needs chi2 > 0 and r2 > r1";
+        d->mu0H0sq = 2.0 * (s12 * p->r1 + s23 * p->r2) * p->Bo_m / den;  // Eq. 41, shell
+    } else if (p->ferro_phase != 0) {
+        return "ferro_phase must be 0, 1 or 2";
+    }
+    if (!(d->mu0H0sq >= 0)) return "Bo_m must be >= 0";
+    d->H0 = std::sqrt(d->mu0H0sq);
+    d->G = 8.0 * p->rho[2] * p->nu[2] * p->u_max / ((double)p->ny * p->ny);
+    return nullptr;
+}
+
+template <typename T>
+static Phys<T> make_phys(const fcd_params *p, const Derived &d, int pitch) {
+    Phys<T> P;
+    std::memset(&P, 0, sizeof(P));
+    P.nx = p->nx;
+    P.ny = p->ny;
+    P.pitch = pitch;
+    P.ps = (long long)pitch * p->ny;
+    for (int i = 0; i < 3; i++) {
+        P.rho[i] = T(p->rho[i]);
+        P.tau[i] = T(d.tau[i]);
+        P.ik[i] = T(1.0 / (1.0 + p->chi[i]));
+        P.gam[i] = T(d.gam[i]);
+        P.lap_coef[i] = T(0.75 * p->xi * d.gam[i]);
+    }
+    P.dk1 = T(1.0 / (1.0 + p->chi[0]) - 1.0 / (1.0 + p->chi[2]));
+    P.dk2 = T(1.0 / (1.0 + p->chi[1]) - 1.0 / (1.0 + p->chi[2]));
+    P.s12 = T(d.s12);
+    P.s13 = T(d.s13);
+    P.s23 = T(d.s23);
+    P.eta = T(p->eta);
+    P.twelve_over_xi = T(12.0 / p->xi);
+    P.four_over_xi = T(4.0 / p->xi);
+    P.eps_n = T(p->eps_n);
+    const double om = 1.0 / (0.5 + d.tau_phi);
+    P.om_phi = T(om);
+    P.keep_phi = T(1.0 - om);
+    P.src_phi = T(1.0 - 0.5 * om);
+    P.H0c = T(d.H0 * std::cos(p->alpha));
+    P.H0s = T(d.H0 * std::sin(p->alpha));
+    P.G = T(d.G);
+    return P;
+}
+
+// ---------------------------------------------------------------- context
+struct fcd_ctx {
+    fcd_params prm;
+    Derived D;
+    char err[512] = {0};
+    cudaStream_t stream = nullptr;
+    long step = 0;
+    virtual ~fcd_ctx() {}
+    virtual fcd_status init() = 0;
+    virtual fcd_status do_step(long n) = 0;
+    virtual fcd_status solve(double tol, int max_iter, int *iters, double *resid) = 0;
+    virtual fcd_status observe(fcd_obs *o) = 0;
+    virtual fcd_status field(int which, double *dst, size_t n) = 0;
+    virtual fcd_status get_pops(double *f, double *g, double *psi) = 0;
+    virtual fcd_status set_pops(const double *f, const double *g, const double *psi, long st) = 0;
+    virtual size_t state_bytes() const = 0;
+    virtual fcd_status get_state(void *dst, size_t bytes) = 0;
+    virtual fcd_status set_state(const void *src, size_t bytes) = 0;
+    virtual long launches() const = 0;
+    virtual fcd_status set_profiling(int on) = 0;
+    virtual fcd_status profile(double *ms) = 0;
+    fcd_status fail(fcd_status s, const char *fmt, ...) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(err, sizeof err, fmt, ap);
+        va_end(ap);
+        return s;
+    }
+};
+
+#define CK(call)                                                                         \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) return fail(FCD_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+__global__ void advance_step(long long *s) { *s += 1; }
+
+struct SnapHeader {
+    unsigned magic, version;
+    int nx, ny, precision, pitch;
+    long long step;
+    unsigned long long brk;
+};
+static const unsigned SNAP_MAGIC = 0x46434453u;  // "FCDS"
+
+template <typename T>
+struct Engine : fcd_ctx {
+    using S = T;  // stored type equals the compute type (FP64 or FP32)
+    int mode = MODE_FP64;
+    int pitch = 0;
+    long long ps = 0;
+    Phys<T> P;
+    void *(*alloc)(size_t, void *) = nullptr;
+    void (*release)(void *, void *) = nullptr;
+    void *user = nullptr;
+    std::vector<void *> mem;
+    void *f[2] = {nullptr, nullptr}, *g[2] = {nullptr, nullptr};
+    int cur = 0;
+    T *phi1 = nullptr, *phi2 = nullptr, *k = nullptr, *psiA = nullptr, *psiB = nullptr,
+      *macro = nullptr;
+    MgCtl *ctl = nullptr;
+    MgHost<T> *mg = nullptr;
+    unsigned long long *brk = nullptr;
+    long long *d_step = nullptr;
+    double *obs_scratch = nullptr;
+    ObsOut *obs_out = nullptr;
+    MgCtl *h_ctl = nullptr;
+    ObsOut *h_obs = nullptr;
+    unsigned long long *h_brk = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    bool use_graph = true;
+    bool profiling = false;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    long host_kernels = 0;
+    int reported_nonconv = 0;
+
+    T *dalloc(size_t bytes) {
+        void *p = alloc(bytes, user);
+        if (p) mem.push_back(p);
+        return static_cast<T *>(p);
+    }
+
+    ~Engine() override {
+        if (stream) cudaStreamSynchronize(stream);
+        cudaDeviceSynchronize();
+        for (int a = 0; a < 2; a++)
+            for (int b = 0; b < 2; b++) {
+                if (gexec[a][b]) cudaGraphExecDestroy(gexec[a][b]);
+                if (graph[a][b]) cudaGraphDestroy(graph[a][b]);
+            }
+        if (mg) mg_destroy(mg);
+        for (void *p : mem) release(p, user);
+        if (h_ctl) cudaFreeHost(h_ctl);
+        if (h_obs) cudaFreeHost(h_obs);
+        if (h_brk) cudaFreeHost(h_brk);
+        if (cap) cudaStreamDestroy(cap);
+        for (auto e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+
+    bool magnetic() const { return D.H0 > 0.0; }
+
+    fcd_status init() override {
+        mode = prm.precision == FCD_FP64 ? MODE_FP64 : (prm.precision == FCD_FP32 ? MODE_FP32 : MODE_FP32_OFFSET);
+        pitch = (prm.nx + 31) / 32 * 32;
+        ps = (long long)pitch * prm.ny;
+        P = make_phys<T>(&prm, D, pitch);
+        const char *nog = getenv("FCD_NO_GRAPH");
+        use_graph = !(nog && nog[0] == '1');
+        for (int b = 0; b < 2; b++) {
+            f[b] = dalloc(9 * ps * sizeof(S));
+            g[b] = dalloc(18 * ps * sizeof(S));
+        }
+        phi1 = dalloc(ps * sizeof(T));
+        phi2 = dalloc(ps * sizeof(T));
+        k = dalloc(ps * sizeof(T));
+        psiA = dalloc(ps * sizeof(T));
+        psiB = dalloc(ps * sizeof(T));
+        macro = dalloc(3 * ps * sizeof(T));
+        ctl = reinterpret_cast<MgCtl *>(dalloc(sizeof(MgCtl)));
+        brk = reinterpret_cast<unsigned long long *>(dalloc(sizeof(unsigned long long)));
+        d_step = reinterpret_cast<long long *>(dalloc(sizeof(long long)));
+        obs_scratch = reinterpret_cast<double *>(dalloc(observe_scratch_doubles(prm.nx, prm.ny) * sizeof(double)));
+        obs_out = reinterpret_cast<ObsOut *>(dalloc(sizeof(ObsOut)));
+        for (void *p : {f[0], f[1], g[0], g[1], (void *)phi1, (void *)phi2, (void *)k, (void *)psiA,
+                        (void *)psiB, (void *)macro, (void *)ctl, (void *)brk, (void *)d_step,
+                        (void *)obs_scratch, (void *)obs_out})
+            if (!p) return fail(FCD_ENOMEM, "device allocation failed");
+        CK(cudaMallocHost(&h_ctl, sizeof(MgCtl)));
+        CK(cudaMallocHost(&h_obs, sizeof(ObsOut)));
+        CK(cudaMallocHost(&h_brk, sizeof(unsigned long long)));
+        CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        for (auto &e : ev) CK(cudaEventCreate(&e));
+        mg = mg_create<T>(prm.nx, prm.ny, pitch, k, psiA, psiB, ctl, alloc, release, user, err, sizeof err);
+        if (!mg) return FCD_ENOMEM;
+        cudaStream_t s = stream;
+        CK(cudaMemsetAsync(ctl, 0, sizeof(MgCtl), s));
+        CK(cudaMemsetAsync(psiA, 0, ps * sizeof(T), s));
+        CK(cudaMemsetAsync(psiB, 0, ps * sizeof(T), s));
+        CK(cudaMemsetAsync(brk, 0xff, sizeof(unsigned long long), s));
+        CK(cudaMemsetAsync(d_step, 0, sizeof(long long), s));
+        // padding columns of every plane stay zero
+        for (int b = 0; b < 2; b++) {
+            CK(cudaMemsetAsync(f[b], 0, 9 * ps * sizeof(S), s));
+            CK(cudaMemsetAsync(g[b], 0, 18 * ps * sizeof(S), s));
+        }
+        CK(cudaMemsetAsync(phi1, 0, ps * sizeof(T), s));
+        CK(cudaMemsetAsync(phi2, 0, ps * sizeof(T), s));
+        CK(cudaMemsetAsync(k, 0, ps * sizeof(T), s));
+        {
+            MgCtl c;
+            std::memset(&c, 0, sizeof c);
+            c.H0 = D.H0;
+            c.tolH0 = prm.mag_tol * D.H0;
+            c.max_iter = prm.mag_max_iter;
+            *h_ctl = c;
+            CK(cudaMemcpyAsync(ctl, h_ctl, sizeof(MgCtl), cudaMemcpyHostToDevice, s));
+            CK(cudaStreamSynchronize(s));
+        }
+        launch_init<T>(mode, P, prm.u_max, prm.r1, prm.r2, prm.xc, prm.yc, prm.xi, f[0], g[0], macro, s);
+        host_kernels++;
+        CK(cudaGetLastError());
+        int it;
+        double res;
+        fcd_status st = solve(prm.mag_tol, prm.mag_max_iter > 100 ? prm.mag_max_iter : 100, &it, &res);
+        if (st != FCD_OK && st != FCD_ENOCONV) return st;
+        return FCD_OK;
+    }
+
+    // ---- one step as kernel launches on stream s (the MG loop by while node
+    // when capturing, by host polling otherwise)
+    fcd_status enqueue_pre(int c, cudaStream_t s) {
+        launch_phase<T>(mode, P, g[c], phi1, phi2, k, s);
+        if (magnetic()) {
+            mg_prepare<T>(mg, s);
+            mg_begin<T>(mg, prm.mag_tol * D.H0, prm.mag_max_iter, s);
+        }
+        return FCD_OK;
+    }
+    void enqueue_post(int c, bool store_macro, cudaStream_t s) {
+        LbmArgs<T> a;
+        a.P = P;
+        a.f_src = f[c];
+        a.g_src = g[c];
+        a.f_dst = f[c ^ 1];
+        a.g_dst = g[c ^ 1];
+        a.phi1 = phi1;
+        a.phi2 = phi2;
+        a.psi0 = psiA;
+        a.psi1 = psiB;
+        a.ctl = ctl;
+        a.macro = store_macro ? macro : nullptr;
+        a.brk = brk;
+        a.step = d_step;
+        launch_collide<T>(mode, a, s);
+        advance_step<<<1, 1, 0, s>>>(d_step);
+    }
+    int pre_kernels() const { return 1 + (magnetic() ? mg_pre_kernels(mg) : 0); }
+
+    fcd_status host_mg_loop(cudaStream_t s) {
+        for (int guard = 0; guard < 1000000; guard++) {
+            mg_cycle<T>(mg, P.H0c, P.H0s, 0, 0, s);
+            CK(cudaGetLastError());
+            CK(cudaMemcpyAsync(h_ctl, ctl, sizeof(MgCtl), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (!h_ctl->keep_going) break;
+        }
+        return FCD_OK;
+    }
+
+    fcd_status build_graph(int c, int sm) {
+        cudaStream_t s = cap;
+        CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        if (profiling) CK(cudaEventRecord(ev[0], s));
+        enqueue_pre(c, s);
+        if (profiling) CK(cudaEventRecord(ev[1], s));
+        if (magnetic()) {
+            cudaStreamCaptureStatus cs;
+            cudaGraph_t gcap;
+            const cudaGraphNode_t *deps = nullptr;
+            size_t nd = 0;
+            CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &gcap, &deps, nullptr, &nd));
+            cudaGraphConditionalHandle h;
+            CK(cudaGraphConditionalHandleCreate(&h, gcap, 1, cudaGraphCondAssignDefault));
+            cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+            cp.conditional.handle = h;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            cudaGraphNode_t wnode;
+            CK(cudaGraphAddNode(&wnode, gcap, deps, nullptr, nd, &cp));
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            cudaStream_t bs;
+            CK(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
+            CK(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+            mg_cycle<T>(mg, P.H0c, P.H0s, h, 1, bs);
+            cudaGraph_t bodyOut;
+            cudaError_t e1 = cudaStreamEndCapture(bs, &bodyOut);
+            cudaStreamDestroy(bs);
+            CK(e1);
+            CK(cudaStreamUpdateCaptureDependencies(s, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+        }
+        if (profiling) CK(cudaEventRecord(ev[2], s));
+        enqueue_post(c, sm != 0, s);
+        if (profiling) CK(cudaEventRecord(ev[3], s));
+        CK(cudaStreamEndCapture(s, &graph[c][sm]));
+        CK(cudaGraphInstantiate(&gexec[c][sm], graph[c][sm], 0));
+        return FCD_OK;
+    }
+
+    fcd_status do_step(long n) override {
+        if (n < 0) return fail(FCD_EINVAL, "negative step count");
+        cudaStream_t s = stream;
+        for (long i = 0; i < n; i++) {
+            const int sm = i == n - 1 ? 1 : 0;
+            if (use_graph) {
+                if (!gexec[cur][sm]) {
+                    fcd_status st = build_graph(cur, sm);
+                    if (st != FCD_OK) return st;
+                }
+                CK(cudaGraphLaunch(gexec[cur][sm], s));
+                host_kernels += pre_kernels() + 2;
+            } else {
+                if (profiling) CK(cudaEventRecord(ev[0], s));
+                enqueue_pre(cur, s);
+                if (profiling) CK(cudaEventRecord(ev[1], s));
+                if (magnetic()) {
+                    fcd_status st = host_mg_loop(s);
+                    if (st != FCD_OK) return st;
+                }
+                if (profiling) CK(cudaEventRecord(ev[2], s));
+                enqueue_post(cur, sm != 0, s);
+                if (profiling) CK(cudaEventRecord(ev[3], s));
+                host_kernels += pre_kernels() + 2;
+                CK(cudaGetLastError());
+            }
+            cur ^= 1;
+            step++;
+        }
+        CK(cudaGetLastError());
+        return FCD_OK;
+    }
+
+    fcd_status sync_ctl() {
+        CK(cudaMemcpyAsync(h_ctl, ctl, sizeof(MgCtl), cudaMemcpyDeviceToHost, stream));
+        CK(cudaStreamSynchronize(stream));
+        return FCD_OK;
+    }
+
+    fcd_status solve(double tol, int max_iter, int *iters, double *resid) override {
+        if (!(tol > 0)) tol = prm.mag_tol;
+        if (max_iter <= 0) max_iter = prm.mag_max_iter;
+        cudaStream_t s = stream;
+        if (!magnetic()) {
+            CK(cudaMemsetAsync(psiA, 0, ps * sizeof(T), s));
+            CK(cudaMemsetAsync(psiB, 0, ps * sizeof(T), s));
+            CK(cudaStreamSynchronize(s));
+            if (iters) *iters = 0;
+            if (resid) *resid = 0.0;
+            return FCD_OK;
+        }
+        launch_phase<T>(mode, P, g[cur], phi1, phi2, k, s);
+        mg_prepare<T>(mg, s);
+        mg_begin<T>(mg, tol * D.H0, max_iter, s);
+        host_kernels += pre_kernels();
+        CK(cudaGetLastError());
+        fcd_status st = host_mg_loop(s);
+        if (st != FCD_OK) return st;
+        if (iters) *iters = h_ctl->last_iters;
+        if (resid) *resid = h_ctl->last_resid;
+        if (!h_ctl->converged) {
+            reported_nonconv = h_ctl->nonconv_count;
+            return fail(FCD_ENOCONV, "potential solve stopped at %d V-cycles with residual %.3e",
+                        h_ctl->last_iters, h_ctl->last_resid);
+        }
+        return FCD_OK;
+    }
+
+    fcd_status observe(fcd_obs *o) override {
+        cudaStream_t s = stream;
+        launch_observe<T>(mode, P, g[cur], obs_scratch, obs_out, s);
+        host_kernels += 4;
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(h_obs, obs_out, sizeof(ObsOut), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(h_brk, brk, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(h_ctl, ctl, sizeof(MgCtl), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        const ObsOut &r = *h_obs;
+        std::memset(o, 0, sizeof *o);
+        o->step = step;
+        o->t_star = step * D.u_avg / (2.0 * prm.r2);  // Eq. 38
+        for (int i = 0; i < 3; i++) o->mass[i] = r.mass[i];
+        o->lx_o = r.lx_o; o->ly_o = r.ly_o; o->lx_i = r.lx_i; o->ly_i = r.ly_i;
+        o->T_o = (r.lx_o + r.ly_o) > 0 ? (r.ly_o - r.lx_o) / (r.ly_o + r.lx_o) : 0.0;  // Eq. 42
+        o->T_i = (r.lx_i + r.ly_i) > 0 ? (r.ly_i - r.lx_i) / (r.ly_i + r.lx_i) : 0.0;
+        o->xc_core = r.xc_core; o->yc_core = r.yc_core;
+        o->xc_shell = r.xc_shell; o->yc_shell = r.yc_shell;
+        long long bstep = -1, bnode = 0;
+        if (*h_brk != ~0ull) {
+            bstep = (long long)(*h_brk >> 32);
+            bnode = (long long)(*h_brk & 0xffffffffull);
+        } else if (r.brk_now != ~0ull) {
+            bstep = step;
+            bnode = (long long)r.brk_now;
+        }
+        o->b_step = bstep;
+        if (bstep >= 0) {
+            o->breakup = 1;
+            o->xb = double(bnode % prm.nx);
+            o->yb = double(bnode / prm.nx);
+            o->tb_star = bstep * D.u_avg / (2.0 * prm.r2);
+            o->Lb_star = o->xb / prm.ny;
+            o->yb_star = std::fabs(o->yb - 0.5 * (prm.ny - 1)) / prm.ny;
+        }
+        o->mag_iters = magnetic() ? h_ctl->last_iters : 0;
+        o->mag_resid = magnetic() ? h_ctl->last_resid : 0.0;
+        if (r.nonfinite) return fail(FCD_EUNSTABLE, "non-finite phase field at step %ld", step);
+        if (h_ctl->nonconv_count > reported_nonconv) {
+            reported_nonconv = h_ctl->nonconv_count;
+            return fail(FCD_ENOCONV, "a potential solve stopped at the cycle cap (residual %.3e)",
+                        h_ctl->last_resid);
+        }
+        return FCD_OK;
+    }
+
+    double *staging(size_t doubles) {
+        void *p = nullptr;
+        if (cudaMalloc(&p, doubles * sizeof(double)) != cudaSuccess) return nullptr;
+        return static_cast<double *>(p);
+    }
+
+    fcd_status field(int which, double *dst, size_t n) override {
+        const size_t N = (size_t)prm.nx * prm.ny;
+        if (!dst || n < N) return fail(FCD_EINVAL, "destination holds %zu of %zu values", n, N);
+        if (which < FCD_FIELD_PHI1 || which > FCD_FIELD_PSI) return fail(FCD_EINVAL, "unknown field %d", which);
+        cudaStream_t s = stream;
+        double *st = staging(N);
+        if (!st) return fail(FCD_ENOMEM, "staging allocation failed");
+        fcd_status rc = FCD_OK;
+        if (which <= FCD_FIELD_PHI3) {
+            launch_phase<T>(mode, P, g[cur], phi1, phi2, nullptr, s);
+            if (which == FCD_FIELD_PHI1) launch_plane_to_f64<T>(phi1, prm.nx, prm.ny, pitch, st, s);
+            else if (which == FCD_FIELD_PHI2) launch_plane_to_f64<T>(phi2, prm.nx, prm.ny, pitch, st, s);
+            else launch_phi3_to_f64<T>(phi1, phi2, prm.nx, prm.ny, pitch, st, s);
+            host_kernels += 2;
+        } else if (which <= FCD_FIELD_PSTAR) {
+            launch_plane_to_f64<T>(macro + (which - FCD_FIELD_UX) * ps, prm.nx, prm.ny, pitch, st, s);
+            host_kernels += 1;
+        } else {
+            if (sync_ctl() != FCD_OK) { cudaFree(st); return FCD_ECUDA; }
+            launch_plane_to_f64<T>(h_ctl->cur ? psiB : psiA, prm.nx, prm.ny, pitch, st, s);
+            host_kernels += 1;
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst, st, N * sizeof(double), cudaMemcpyDefault, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = fail(FCD_ECUDA, "get_field: %s", cudaGetErrorString(e));
+        cudaFree(st);
+        return rc;
+    }
+
+    fcd_status get_pops(double *fo, double *go, double *po) override {
+        const size_t N = (size_t)prm.nx * prm.ny;
+        cudaStream_t s = stream;
+        double *st = staging(28 * N);
+        if (!st) return fail(FCD_ENOMEM, "staging allocation failed");
+        if (sync_ctl() != FCD_OK) { cudaFree(st); return FCD_ECUDA; }
+        launch_export<T>(mode, P, f[cur], g[cur], st, st + 9 * N, s);
+        launch_plane_to_f64<T>(h_ctl->cur ? psiB : psiA, prm.nx, prm.ny, pitch, st + 27 * N, s);
+        host_kernels += 2;
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess && fo) e = cudaMemcpyAsync(fo, st, 9 * N * sizeof(double), cudaMemcpyDefault, s);
+        if (e == cudaSuccess && go) e = cudaMemcpyAsync(go, st + 9 * N, 18 * N * sizeof(double), cudaMemcpyDefault, s);
+        if (e == cudaSuccess && po) e = cudaMemcpyAsync(po, st + 27 * N, N * sizeof(double), cudaMemcpyDefault, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        cudaFree(st);
+        if (e != cudaSuccess) return fail(FCD_ECUDA, "get_populations: %s", cudaGetErrorString(e));
+        return FCD_OK;
+    }
+
+    fcd_status set_pops(const double *fi, const double *gi, const double *pi, long st_) override {
+        const size_t N = (size_t)prm.nx * prm.ny;
+        if (st_ < 0) return fail(FCD_EINVAL, "negative step");
+        cudaStream_t s = stream;
+        double *st = staging(28 * N);
+        if (!st) return fail(FCD_ENOMEM, "staging allocation failed");
+        cudaError_t e = cudaSuccess;
+        if (fi) e = cudaMemcpyAsync(st, fi, 9 * N * sizeof(double), cudaMemcpyDefault, s);
+        if (e == cudaSuccess && gi) e = cudaMemcpyAsync(st + 9 * N, gi, 18 * N * sizeof(double), cudaMemcpyDefault, s);
+        if (e == cudaSuccess && pi) e = cudaMemcpyAsync(st + 27 * N, pi, N * sizeof(double), cudaMemcpyDefault, s);
+        if (e == cudaSuccess) {
+            launch_import<T>(mode, P, fi ? st : nullptr, gi ? st + 9 * N : nullptr, f[cur], g[cur], s);
+            host_kernels++;
+            if (pi) {
+                if (sync_ctl() != FCD_OK) { cudaFree(st); return FCD_ECUDA; }
+                launch_plane_from_f64<T>(st + 27 * N, prm.nx, prm.ny, pitch, h_ctl->cur ? psiB : psiA, s);
+                host_kernels++;
+            }
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemsetAsync(brk, 0xff, sizeof(unsigned long long), s);
+        long long s64 = st_;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_step, &s64, sizeof(long long), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        cudaFree(st);
+        if (e != cudaSuccess) return fail(FCD_ECUDA, "set_populations: %s", cudaGetErrorString(e));
+        step = st_;
+        return FCD_OK;
+    }
+
+    size_t state_bytes() const override {
+        return sizeof(SnapHeader) + 27 * (size_t)ps * sizeof(S) + (size_t)ps * sizeof(T);
+    }
+
+    fcd_status get_state(void *dst, size_t bytes) override {
+        if (!dst || bytes < state_bytes()) return fail(FCD_EINVAL, "snapshot buffer too small");
+        if (sync_ctl() != FCD_OK) return FCD_ECUDA;
+        cudaStream_t s = stream;
+        SnapHeader h;
+        std::memset(&h, 0, sizeof h);
+        h.magic = SNAP_MAGIC;
+        h.version = 1;
+        h.nx = prm.nx;
+        h.ny = prm.ny;
+        h.precision = prm.precision;
+        h.pitch = pitch;
+        h.step = step;
+        CK(cudaMemcpyAsync(h_brk, brk, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        h.brk = *h_brk;
+        char *d = static_cast<char *>(dst);
+        CK(cudaMemcpyAsync(d, &h, sizeof h, cudaMemcpyDefault, s));
+        CK(cudaStreamSynchronize(s));
+        size_t off = sizeof h;
+        CK(cudaMemcpyAsync(d + off, f[cur], 9 * ps * sizeof(S), cudaMemcpyDefault, s));
+        off += 9 * ps * sizeof(S);
+        CK(cudaMemcpyAsync(d + off, g[cur], 18 * ps * sizeof(S), cudaMemcpyDefault, s));
+        off += 18 * ps * sizeof(S);
+        CK(cudaMemcpyAsync(d + off, h_ctl->cur ? psiB : psiA, ps * sizeof(T), cudaMemcpyDefault, s));
+        CK(cudaStreamSynchronize(s));
+        return FCD_OK;
+    }
+
+    fcd_status set_state(const void *src, size_t bytes) override {
+        if (!src || bytes < state_bytes()) return fail(FCD_ESTATE, "snapshot too small");
+        SnapHeader h;
+        cudaStream_t s = stream;
+        CK(cudaMemcpyAsync(&h, src, sizeof h, cudaMemcpyDefault, s));
+        CK(cudaStreamSynchronize(s));
+        if (h.magic != SNAP_MAGIC || h.version != 1 || h.nx != prm.nx || h.ny != prm.ny ||
+            h.precision != prm.precision || h.pitch != pitch)
+            return fail(FCD_ESTATE, "snapshot does not match this context");
+        const char *p = static_cast<const char *>(src);
+        size_t off = sizeof h;
+        CK(cudaMemcpyAsync(f[cur], p + off, 9 * ps * sizeof(S), cudaMemcpyDefault, s));
+        off += 9 * ps * sizeof(S);
+        CK(cudaMemcpyAsync(g[cur], p + off, 18 * ps * sizeof(S), cudaMemcpyDefault, s));
+        off += 18 * ps * sizeof(S);
+        if (sync_ctl() != FCD_OK) return FCD_ECUDA;
+        CK(cudaMemcpyAsync(h_ctl->cur ? psiB : psiA, p + off, ps * sizeof(T), cudaMemcpyDefault, s));
+        *h_brk = h.brk;
+        CK(cudaMemcpyAsync(brk, h_brk, sizeof(unsigned long long), cudaMemcpyHostToDevice, s));
+        long long st64 = h.step;
+        CK(cudaMemcpyAsync(d_step, &st64, sizeof st64, cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+        step = (long)h.step;
+        return FCD_OK;
+    }
+
+    fcd_status set_profiling(int on) override {
+        if ((on != 0) == profiling) return FCD_OK;
+        CK(cudaStreamSynchronize(stream));
+        for (int a = 0; a < 2; a++)
+            for (int b = 0; b < 2; b++) {
+                if (gexec[a][b]) cudaGraphExecDestroy(gexec[a][b]);
+                if (graph[a][b]) cudaGraphDestroy(graph[a][b]);
+                gexec[a][b] = nullptr;
+                graph[a][b] = nullptr;
+            }
+        profiling = on != 0;
+        return FCD_OK;
+    }
+
+    fcd_status profile(double *ms) override {
+        if (!profiling) return fail(FCD_EINVAL, "profiling is off");
+        CK(cudaEventSynchronize(ev[3]));
+        float t[3];
+        for (int i = 0; i < 3; i++) CK(cudaEventElapsedTime(&t[i], ev[i], ev[i + 1]));
+        ms[0] = t[0];
+        ms[1] = t[1];
+        ms[2] = t[2];
+        float tt;
+        CK(cudaEventElapsedTime(&tt, ev[0], ev[3]));
+        ms[3] = tt;
+        return FCD_OK;
+    }
+
+    long launches() const override {
+        MgCtl c;
+        if (cudaMemcpy(&c, ctl, sizeof c, cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+        return host_kernels + (long)c.cycles_launched * mg_kernels_per_cycle(mg);
+    }
+};
+
+// ---------------------------------------------------------------- C ABI
+static thread_local char g_last[512];  // reason of the last failed fcd_create on this thread
+
+extern "C" {
+
+fcd_status fcd_create(const fcd_params *params, fcd_ctx **out) {
+    if (!out) return FCD_EINVAL;
+    *out = nullptr;
+    if (!params) return FCD_EINVAL;
+    Derived d;
+    std::memset(&d, 0, sizeof d);
+    const char *why = derive(params, &d);
+    if (why) {
+        snprintf(g_last, sizeof g_last, "fcd_create: %s", why);
+        return FCD_EINVAL;
+    }
+    fcd_ctx *c = nullptr;
+    if (params->precision == FCD_FP64) {
+        auto *e = new (std::nothrow) Engine<double>();
+        if (e) { e->alloc = g_alloc ? g_alloc : default_alloc; e->release = g_free ? g_free : default_free; e->user = g_alloc ? g_user : nullptr; }
+        c = e;
+    } else {
+        auto *e = new (std::nothrow) Engine<float>();
+        if (e) { e->alloc = g_alloc ? g_alloc : default_alloc; e->release = g_free ? g_free : default_free; e->user = g_alloc ? g_user : nullptr; }
+        c = e;
+    }
+    if (!c) return FCD_ENOMEM;
+    c->prm = *params;
+    c->D = d;
+    fcd_status st = c->init();
+    if (st != FCD_OK) {
+        snprintf(g_last, sizeof g_last, "%s", c->err);
+        delete c;
+        return st;
+    }
+    *out = c;
+    return FCD_OK;
+}
+
+fcd_status fcd_set_stream(fcd_ctx *c, void *stream) {
+    if (!c) return FCD_EINVAL;
+    c->stream = static_cast<cudaStream_t>(stream);
+    return FCD_OK;
+}
+
+fcd_status fcd_step(fcd_ctx *c, long n) { return c ? c->do_step(n) : FCD_EINVAL; }
+
+fcd_status fcd_solve_magnetic(fcd_ctx *c, double tol, int max_iter, int *iters, double *resid) {
+    return c ? c->solve(tol, max_iter, iters, resid) : FCD_EINVAL;
+}
+
+fcd_status fcd_observables(fcd_ctx *c, fcd_obs *o) {
+    if (!c || !o) return FCD_EINVAL;
+    return c->observe(o);
+}
+
+fcd_status fcd_get_field(fcd_ctx *c, int which, double *dst, size_t n) {
+    return c ? c->field(which, dst, n) : FCD_EINVAL;
+}
+
+fcd_status fcd_get_populations(fcd_ctx *c, double *f, double *g, double *psi) {
+    return c ? c->get_pops(f, g, psi) : FCD_EINVAL;
+}
+
+fcd_status fcd_set_populations(fcd_ctx *c, const double *f, const double *g, const double *psi,
+                               long step) {
+    return c ? c->set_pops(f, g, psi, step) : FCD_EINVAL;
+}
+
+size_t fcd_state_bytes(const fcd_ctx *c) { return c ? c->state_bytes() : 0; }
+
+fcd_status fcd_get_state(fcd_ctx *c, void *dst, size_t bytes) {
+    return c ? c->get_state(dst, bytes) : FCD_EINVAL;
+}
+
+fcd_status fcd_set_state(fcd_ctx *c, const void *src, size_t bytes) {
+    return c ? c->set_state(src, bytes) : FCD_EINVAL;
+}
+
+fcd_status fcd_get_derived(const fcd_ctx *c, double *o) {
+    if (!c || !o) return FCD_EINVAL;
+    const Derived &d = c->D;
+    const double v[15] = {d.u_avg, d.s12, d.s13, d.s23, d.gam[0], d.gam[1], d.gam[2], d.gamT,
+                          d.tau[0], d.tau[1], d.tau[2], d.tau_phi, d.mu0H0sq, d.H0, d.G};
+    std::memcpy(o, v, sizeof v);
+    return FCD_OK;
+}
+
+long fcd_kernel_launches(const fcd_ctx *c) { return c ? c->launches() : -1; }
+
+fcd_status fcd_set_profiling(fcd_ctx *c, int enable) { return c ? c->set_profiling(enable) : FCD_EINVAL; }
+
+fcd_status fcd_last_step_profile(fcd_ctx *c, double *ms4) {
+    if (!c || !ms4) return FCD_EINVAL;
+    return c->profile(ms4);
+}
+
+const char *fcd_last_error(const fcd_ctx *c) { return c ? c->err : g_last; }
+
+void fcd_destroy(fcd_ctx *c) { delete c; }
+
+}  // extern "C"

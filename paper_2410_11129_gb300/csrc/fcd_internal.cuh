@@ -1,0 +1,183 @@
+// fcd_internal.cuh -- shared declarations of the CUDA library (not installed).
+//
+// Memory layout in HBM (all planes share one row pitch, a multiple of 32 nodes):
+//   f      : 9 planes  x ny rows x pitch, double buffered      (storage type S)
+//   g      : 18 planes x ny rows x pitch, double buffered      (g[i*9 + a])
+//   phi    : 2 planes (phi_1, phi_2) of the current step       (compute type T)
+//   macro  : 3 planes (ux, uy, p*) of the most recent collision
+//   multigrid level 0: psi' (two buffers), k = 1 + chi (Eq. 8)
+// Storage modes: FP64 stores f, g; FP32 plain stores f + w_a (the absolute,
+// density-like population) and g; FP32 offset stores f and g - w_a / 2.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fcd.h"
+
+namespace fcd {
+
+enum StoreMode { MODE_FP64 = 0, MODE_FP32 = 1, MODE_FP32_OFFSET = 2 };
+
+constexpr int TX = 32;  // collide tile (x)
+constexpr int TY = 8;   // collide tile (y)
+
+// D2Q9 (Eq. 20 order: rest, E, N, W, S, NE, NW, SW, SE).
+__host__ __device__ constexpr int cx(int a) {
+    return a == 1 || a == 5 || a == 8 ? 1 : (a == 3 || a == 6 || a == 7 ? -1 : 0);
+}
+__host__ __device__ constexpr int cy(int a) {
+    return a == 2 || a == 5 || a == 6 ? 1 : (a == 4 || a == 7 || a == 8 ? -1 : 0);
+}
+__host__ __device__ constexpr int opp(int a) {
+    return a == 0 ? 0 : (a <= 4 ? ((a + 1) & 3) + 1 : ((a - 3) & 3) + 5);
+}
+template <typename T>
+__host__ __device__ constexpr T wgt(int a) {
+    return a == 0 ? T(4) / T(9) : (a <= 4 ? T(1) / T(9) : T(1) / T(36));
+}
+
+// Offsets added to the populations before they are stored.
+template <int MODE, typename T>
+__host__ __device__ constexpr T f_off(int a) {
+    return MODE == MODE_FP32 ? wgt<T>(a) : T(0);
+}
+template <int MODE, typename T>
+__host__ __device__ constexpr T g_off(int a) {
+    return MODE == MODE_FP32_OFFSET ? -wgt<T>(a) / T(2) : T(0);
+}
+
+template <typename T>
+__device__ __forceinline__ T clamp01(T v) {
+    return v < T(0) ? T(0) : (v > T(1) ? T(1) : v);
+}
+
+// Physical constants of one context in the compute type.
+template <typename T>
+struct Phys {
+    int nx, ny, pitch;
+    long long ps;                       // plane stride = pitch * ny
+    T rho[3], tau[3];                   // Eq. 33 and Eq. 14
+    T ik[3];                            // 1 / (1 + chi_i)      (Eq. 8)
+    T dk1, dk2;                         // ik[0] - ik[2], ik[1] - ik[2] (Eq. 9)
+    T s12, s13, s23, gam[3], eta;       // Eqs. 27, 28
+    T twelve_over_xi, lap_coef[3];      // 12 / xi, (3/4) xi gamma_i   (Eq. 25)
+    T four_over_xi, eps_n;              // source term of the phase field
+    T om_phi, keep_phi, src_phi;        // 1/(1/2 + tau_phi), 1 - om, 1 - om/2
+    T H0c, H0s, G;                      // H0 (cos a, sin a), driving force
+};
+
+// Multigrid level descriptor (device pointers). Level 0 is the lattice with
+// the 9-point link operator; levels >= 1 are merged tensor grids carrying a
+// 5-point finite-volume operator. Coordinates are in lattice units with the
+// walls at y = 0 and y = ny0 (cell faces) and period nx0 along x.
+template <typename T>
+struct Level {
+    int nx, ny, pitch;
+    T *e, *b, *k;             // correction (level 0: psi'), right-hand side, 1 + chi
+    T *r;                     // scratch (level 0: second psi' buffer)
+    const int *cx0, *cy0;     // children of cell I: parent columns cx0[I] .. cx0[I+1]-1
+    const T *xc, *yc, *wx, *wy;
+    T Lx, ylo, yhi;
+    // prolongation of the next coarser level onto this one
+    const int *px0, *px1, *py0, *py1;  // -1 in py* stands for the wall (value 0)
+    const T *pwx, *pwy;
+};
+
+// Device-side control block of one potential solve.
+struct MgCtl {
+    unsigned long long norm_bits;  // max |r| of the current cycle (bits of a double >= 0)
+    int cur;                       // which level-0 buffer holds psi'
+    int iter;                      // V-cycles done in this solve
+    int done;                      // 1 once converged or capped
+    int converged;                 // 1 if the tolerance was met
+    double tolH0;                  // tol * H0
+    int max_iter;
+    int keep_going;                // host-visible loop flag
+    double last_resid;             // final ||r||_inf / H0
+    int last_iters;
+    long long total_cycles;        // cumulative V-cycles that ran in full
+    long long cycles_launched;     // cumulative cycle launches (launch accounting)
+    int nonconv_count;             // solves that stopped at the cap
+    double H0;
+};
+
+struct ObsOut {
+    double mass[3];
+    double xc_core, yc_core, xc_shell, yc_shell;
+    double lx_o, ly_o, lx_i, ly_i;
+    unsigned long long brk_now;  // touch key of the current state (~0ull if none)
+    int xcut;
+    int nonfinite;
+};
+
+}  // namespace fcd
+
+// ---- host-side launchers (defined in the .cu files) ----
+namespace fcd {
+
+template <typename T>
+struct LbmArgs {
+    Phys<T> P;
+    const void *f_src, *g_src;
+    void *f_dst, *g_dst;
+    const T *phi1, *phi2;
+    const T *psi0, *psi1;        // the two level-0 buffers; ctl->cur picks one
+    const MgCtl *ctl;
+    T *macro;                    // nullptr: do not store the macroscopic fields
+    unsigned long long *brk;     // sticky breakup key (nullptr: no check)
+    const long long *step;       // device step counter (breakup key)
+};
+
+template <typename T>
+void launch_phase(int mode, const Phys<T> &P, const void *g, T *phi1, T *phi2, T *k,
+                  cudaStream_t s);
+template <typename T>
+void launch_collide(int mode, const LbmArgs<T> &a, cudaStream_t s);
+template <typename T>
+void launch_init(int mode, const Phys<T> &P, double u_max, double r1, double r2, double xc,
+                 double yc, double xi, void *f, void *g, T *macro, cudaStream_t s);
+template <typename T>
+void launch_export(int mode, const Phys<T> &P, const void *f, const void *g, double *fo,
+                   double *go, cudaStream_t s);
+template <typename T>
+void launch_import(int mode, const Phys<T> &P, const double *fi, const double *gi, void *f,
+                   void *g, cudaStream_t s);
+template <typename T>
+void launch_plane_to_f64(const T *src, int nx, int ny, int pitch, double *dst, cudaStream_t s);
+template <typename T>
+void launch_plane_from_f64(const double *src, int nx, int ny, int pitch, T *dst, cudaStream_t s);
+template <typename T>
+void launch_phi3_to_f64(const T *p1, const T *p2, int nx, int ny, int pitch, double *dst,
+                        cudaStream_t s);
+
+// multigrid
+template <typename T>
+struct MgHost;  // defined in fcd_mg.cu
+template <typename T>
+MgHost<T> *mg_create(int nx, int ny, int pitch, T *k0, T *psiA, T *psiB, MgCtl *ctl,
+                     void *(*alloc)(size_t, void *), void (*release)(void *, void *), void *user,
+                     char *err, size_t errlen);
+template <typename T>
+void mg_destroy(MgHost<T> *m);
+template <typename T>
+void mg_begin(MgHost<T> *m, double tolH0, int max_iter, cudaStream_t s);
+template <typename T>
+void mg_cycle(MgHost<T> *m, T H0c, T H0s, cudaGraphConditionalHandle h, int in_graph,
+              cudaStream_t s);
+template <typename T>
+int mg_kernels_per_cycle(const MgHost<T> *m);
+template <typename T>
+int mg_levels(const MgHost<T> *m);
+template <typename T>
+int mg_pre_kernels(const MgHost<T> *m);  // kernels of mg_prepare + mg_begin
+template <typename T>
+void mg_prepare(MgHost<T> *m, cudaStream_t s);  // restrict k to the grid-wide coarse levels
+
+// observables
+size_t observe_scratch_doubles(int nx, int ny);
+template <typename T>
+void launch_observe(int mode, const Phys<T> &P, const void *g, double *scratch, ObsOut *out,
+                    cudaStream_t s);
+
+}  // namespace fcd

@@ -1,0 +1,473 @@
+// fcd_lbm.cu -- lattice Boltzmann kernels of the coupled step (arXiv 2410.11129).
+//
+// phase_kernel   : Eq. 32 (phi_i = sum_a g^i_a), Eq. 24, Eq. 8 (k = 1 + chi)
+// collide_kernel : one fused pass per node: isotropic gradients and Laplacians
+//                  (Eqs. 34-35) from shared-memory tiles with a one-node halo,
+//                  chemical potentials and surface tension (Eqs. 25-28, 36),
+//                  Kelvin force (Eqs. 5, 7, 9), pressure, viscous and driving
+//                  forces (Eq. 19), velocity (Eq. 22), MRT collision of f
+//                  (Eqs. 12-18), BGK collision of g^1, g^2 (Eqs. 29-31), push
+//                  streaming with half-way bounce-back.
+// The MRT collision is evaluated in closed form: with every rate 1 except the
+// two stress moments (Eq. 13), the post-collision populations are
+// f^eq + F/2 + (1 - s_nu)/4 [dpxx (row pxx) + dpxy (row pxy)].
+#include "fcd_internal.cuh"
+
+namespace fcd {
+
+template <int MODE>
+struct StoreT { using type = float; };
+template <>
+struct StoreT<MODE_FP64> { using type = double; };
+
+// ---------------------------------------------------------------- phase
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) phase_kernel(Phys<T> P, const void *gv, T *phi1, T *phi2,
+                                                    T *k) {
+    using S = typename StoreT<MODE>::type;
+    const S *g = static_cast<const S *>(gv);
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= P.nx || y >= P.ny) return;
+    long long n = (long long)y * P.pitch + x;
+    T p1 = T(0), p2 = T(0);
+#pragma unroll
+    for (int a = 0; a < 9; a++) {
+        p1 += T(g[a * P.ps + n]) - g_off<MODE, T>(a);
+        p2 += T(g[(9 + a) * P.ps + n]) - g_off<MODE, T>(a);
+    }
+    phi1[n] = p1;
+    phi2[n] = p2;
+    if (k) {
+        T h1 = clamp01(p1), h2 = clamp01(p2), h3 = clamp01(T(1) - p1 - p2);
+        k[n] = T(1) / (P.ik[0] * h1 + P.ik[1] * h2 + P.ik[2] * h3);
+    }
+}
+
+// ---------------------------------------------------------------- collide
+template <typename T>
+struct Stencil {
+    T c, e, w, n, s, ne, nw, sw, se;
+    __device__ __forceinline__ void load(const T (*a)[TX + 2], int lx, int ly) {
+        c = a[ly][lx];
+        e = a[ly][lx + 1];
+        w = a[ly][lx - 1];
+        n = a[ly + 1][lx];
+        s = a[ly - 1][lx];
+        ne = a[ly + 1][lx + 1];
+        nw = a[ly + 1][lx - 1];
+        sw = a[ly - 1][lx - 1];
+        se = a[ly - 1][lx + 1];
+    }
+    // Eq. 34 with c_s^2 = 1/3: 3 sum_a w_a e_a phi_a
+    __device__ __forceinline__ T gx() const {
+        return (e - w) * T(1.0 / 3.0) + ((ne - nw) + (se - sw)) * T(1.0 / 12.0);
+    }
+    __device__ __forceinline__ T gy() const {
+        return (n - s) * T(1.0 / 3.0) + ((ne + nw) - (se + sw)) * T(1.0 / 12.0);
+    }
+    // Eq. 35: 6 sum_a w_a (phi_a - phi_0)
+    __device__ __forceinline__ T lap() const {
+        return (T(4) * ((e + w) + (n + s)) + ((ne + nw) + (se + sw)) - T(20) * c) *
+               T(1.0 / 6.0);
+    }
+};
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(TX *TY) collide_kernel(LbmArgs<T> A) {
+    using S = typename StoreT<MODE>::type;
+    __shared__ T s1[TY + 2][TX + 2], s2[TY + 2][TX + 2], sr[TY + 2][TX + 2], sp[TY + 2][TX + 2];
+    const Phys<T> &P = A.P;
+    const int nx = P.nx, ny = P.ny, pitch = P.pitch;
+    const long long ps = P.ps;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const T *psi = A.ctl->cur ? A.psi1 : A.psi0;
+
+    for (int i = threadIdx.y * TX + threadIdx.x; i < (TX + 2) * (TY + 2); i += TX * TY) {
+        int lx = i % (TX + 2), ly = i / (TX + 2);
+        int gx = x0 - 1 + lx;
+        gx = ((gx % nx) + nx) % nx;
+        int gy = y0 - 1 + ly;
+        bool ghost = gy < 0 || gy >= ny;
+        int my = gy < 0 ? 0 : (gy >= ny ? ny - 1 : gy);
+        long long m = (long long)my * pitch + gx;
+        T p1 = A.phi1[m], p2 = A.phi2[m];
+        s1[ly][lx] = p1;  // mirrored ghost rows: zero normal gradient
+        s2[ly][lx] = p2;
+        sr[ly][lx] = P.rho[0] * clamp01(p1) + P.rho[1] * clamp01(p2) +
+                     P.rho[2] * clamp01(T(1) - p1 - p2);
+        T q = psi[m];
+        sp[ly][lx] = ghost ? -q : q;  // psi' = 0 on the wall faces
+    }
+    __syncthreads();
+
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    if (x >= nx || y >= ny) return;
+    const int lx = threadIdx.x + 1, ly = threadIdx.y + 1;
+    const long long n = (long long)y * pitch + x;
+
+    Stencil<T> st;
+    st.load(s1, lx, ly);
+    const T ph1 = st.c, g1x = st.gx(), g1y = st.gy(), l1 = st.lap();
+    st.load(s2, lx, ly);
+    const T ph2 = st.c, g2x = st.gx(), g2y = st.gy(), l2 = st.lap();
+    const T ph3 = T(1) - ph1 - ph2;
+    const T g3x = -(g1x + g2x), g3y = -(g1y + g2y), l3 = -(l1 + l2);
+    st.load(sr, lx, ly);
+    const T rho = st.c, grx = st.gx(), gry = st.gy();
+    st.load(sp, lx, ly);
+    const T dpx = st.gx(), dpy = st.gy();
+
+    const T h1 = clamp01(ph1), h2 = clamp01(ph2), h3 = clamp01(ph3);
+
+    // Surface tension (Eqs. 25, 28, 36). With phi_3 = 1 - phi_1 - phi_2 the
+    // gradients sum to zero, so the part of mu_i common to all phases drops out:
+    // F_s = sum_i [ (12/xi) dH/dphi_i - (3/4) xi gamma_i lap phi_i ] grad phi_i.
+    T Fx, Fy;
+    {
+        const T gp = P.gam[0] * ph1 + P.gam[1] * ph2 + P.gam[2] * ph3;
+        const T q3 = ph1 * ph2 * ph3;
+        const T a1 = ph1 * ph1, a2 = ph2 * ph2, a3 = ph3 * ph3;
+        const T d1 = T(2) * ph1 * (P.s12 * a2 + P.s13 * a3) + ph2 * ph3 * gp + P.gam[0] * q3 +
+                     T(2) * P.eta * ph1 * a2 * a3;
+        const T d2 = T(2) * ph2 * (P.s12 * a1 + P.s23 * a3) + ph1 * ph3 * gp + P.gam[1] * q3 +
+                     T(2) * P.eta * a1 * ph2 * a3;
+        const T d3 = T(2) * ph3 * (P.s13 * a1 + P.s23 * a2) + ph1 * ph2 * gp + P.gam[2] * q3 +
+                     T(2) * P.eta * a1 * a2 * ph3;
+        const T m1 = P.twelve_over_xi * d1 - P.lap_coef[0] * l1;
+        const T m2 = P.twelve_over_xi * d2 - P.lap_coef[1] * l2;
+        const T m3 = P.twelve_over_xi * d3 - P.lap_coef[2] * l3;
+        Fx = m1 * g1x + m2 * g2x + m3 * g3x;
+        Fy = m1 * g1y + m2 * g2y + m3 * g3y;
+    }
+    // Kelvin force F_m = -(1/2) |H|^2 grad chi (Eq. 7); grad chi by Eq. 9 with
+    // grad phi_3 = -(grad phi_1 + grad phi_2); H = H0 e_alpha - grad psi' (Eq. 5).
+    {
+        const T kk = T(1) / (P.ik[0] * h1 + P.ik[1] * h2 + P.ik[2] * h3);
+        const T gcx = -kk * kk * (P.dk1 * g1x + P.dk2 * g2x);
+        const T gcy = -kk * kk * (P.dk1 * g1y + P.dk2 * g2y);
+        const T Hx = P.H0c - dpx, Hy = P.H0s - dpy;
+        const T hh = T(0.5) * (Hx * Hx + Hy * Hy);
+        Fx -= hh * gcx;
+        Fy -= hh * gcy;
+    }
+
+    // Populations.
+    const S *fs = static_cast<const S *>(A.f_src);
+    T f[9];
+#pragma unroll
+    for (int a = 0; a < 9; a++) f[a] = T(fs[a * ps + n]) - f_off<MODE, T>(a);
+    const T pst = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+    const T jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+    const T jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+    const T mpxx = (f[1] + f[3]) - (f[2] + f[4]);
+    const T mpxy = (f[5] + f[7]) - (f[6] + f[8]);
+    const T me = T(2) * ((f[5] + f[6]) + (f[7] + f[8])) - ((f[1] + f[2]) + (f[3] + f[4])) -
+                 T(4) * f[0];
+
+    // Pressure (F_p = -(p/rho) grad rho with p = rho c_s^2 p*) and driving force.
+    Fx += -pst * T(1.0 / 3.0) * grx + P.G;
+    Fy += -pst * T(1.0 / 3.0) * gry;
+    const T half_inv_rho = T(0.5) / rho;
+    const T upx = jx + Fx * half_inv_rho, upy = jy + Fy * half_inv_rho;
+    const T tau = P.tau[0] * h1 + P.tau[1] * h2 + P.tau[2] * h3;
+    const T snu = T(1) / (T(0.5) + tau);
+    // Viscous force from the non-equilibrium stress (moments of f - f^eq(p*, u')):
+    // Pi = (1/6) m_e + (1/2) s_nu m_pxx on the diagonal, s_nu m_pxy off it.
+    {
+        const T he = me - (T(3) * (upx * upx + upy * upy) - T(2) * pst);
+        const T hxx = mpxx - (upx * upx - upy * upy);
+        const T hxy = mpxy - upx * upy;
+        const T Pxx = he * T(1.0 / 6.0) + T(0.5) * snu * hxx;
+        const T Pyy = he * T(1.0 / 6.0) - T(0.5) * snu * hxx;
+        const T Pxy = snu * hxy;
+        const T Fmx = -tau * (Pxx * grx + Pxy * gry);
+        const T Fmy = -tau * (Pxy * grx + Pyy * gry);
+        Fx += Fmx;
+        Fy += Fmy;
+    }
+    const T ux = jx + Fx * half_inv_rho, uy = jy + Fy * half_inv_rho;
+    const T uu = T(1.5) * (ux * ux + uy * uy);
+
+    if (A.macro) {
+        A.macro[n] = ux;
+        A.macro[ps + n] = uy;
+        A.macro[2 * ps + n] = pst;
+    }
+
+    // Breakup: the core (phi_1 >= 1/2) touches the carrier (phi_3 >= 1/2) at a
+    // D2Q9 neighbour inside the channel; keep the first (step, y, x).
+    if (A.brk && h1 >= T(0.5) && *((volatile unsigned long long *)A.brk) == ~0ull) {
+        bool touch = false;
+#pragma unroll
+        for (int a = 1; a < 9; a++) {
+            int yy = y + cy(a);
+            if (yy < 0 || yy >= ny) continue;
+            T q1 = s1[ly + cy(a)][lx + cx(a)], q2 = s2[ly + cy(a)][lx + cx(a)];
+            touch |= clamp01(T(1) - q1 - q2) >= T(0.5);
+        }
+        if (touch) {
+            unsigned long long key = ((unsigned long long)(*A.step) << 32) |
+                                     (unsigned long long)((long long)y * nx + x);
+            atomicMin(A.brk, key);
+        }
+    }
+
+    // MRT collision in closed form and push streaming of f.
+    S *fd = static_cast<S *>(A.f_dst);
+    const T dxx = mpxx - (ux * ux - uy * uy);
+    const T dxy = mpxy - ux * uy;
+    const T rel = (T(1) - snu) * T(0.25);
+    const T fr = T(3) / rho;
+    const T Ftx = Fx * fr, Fty = Fy * fr;
+#pragma unroll
+    for (int a = 0; a < 9; a++) {
+        const T w = wgt<T>(a);
+        const T eu = T(cx(a)) * ux + T(cy(a)) * uy;
+        T v = w * (pst + T(3) * eu + T(4.5) * eu * eu - uu);
+        v += T(0.5) * w * (T(cx(a)) * Ftx + T(cy(a)) * Fty);
+        const T rxx = (a == 1 || a == 3) ? T(1) : ((a == 2 || a == 4) ? T(-1) : T(0));
+        const T rxy = (a == 5 || a == 7) ? T(1) : ((a == 6 || a == 8) ? T(-1) : T(0));
+        v += rel * (rxx * dxx + rxy * dxy);
+        int xn = x + cx(a);
+        xn = xn < 0 ? nx - 1 : (xn >= nx ? 0 : xn);
+        int yn = y + cy(a);
+        if (yn >= 0 && yn < ny)
+            fd[a * ps + (long long)yn * pitch + xn] = S(v + f_off<MODE, T>(a));
+        else
+            fd[opp(a) * ps + n] = S(v + f_off<MODE, T>(opp(a)));
+    }
+
+    // Phase fields (Eqs. 29-31): g* = (1 - om) g + om phi Gamma + (1 - om/2) F^phi,
+    // F^phi_a = w_a e_a . q_i, q_i = theta_i n_i - (1/3) sum_j theta_j n_j.
+    T qx[2], qy[2];
+    {
+        const T t1 = P.four_over_xi * h1 * (T(1) - h1);
+        const T t2 = P.four_over_xi * h2 * (T(1) - h2);
+        const T t3 = P.four_over_xi * h3 * (T(1) - h3);
+        const T i1 = t1 / (sqrt(g1x * g1x + g1y * g1y) + P.eps_n);
+        const T i2 = t2 / (sqrt(g2x * g2x + g2y * g2y) + P.eps_n);
+        const T i3 = t3 / (sqrt(g3x * g3x + g3y * g3y) + P.eps_n);
+        const T mx = (i1 * g1x + i2 * g2x + i3 * g3x) * T(1.0 / 3.0);
+        const T my = (i1 * g1y + i2 * g2y + i3 * g3y) * T(1.0 / 3.0);
+        qx[0] = i1 * g1x - mx;
+        qy[0] = i1 * g1y - my;
+        qx[1] = i2 * g2x - mx;
+        qy[1] = i2 * g2y - my;
+    }
+    const S *gs = static_cast<const S *>(A.g_src);
+    S *gd = static_cast<S *>(A.g_dst);
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+        const T phi = i == 0 ? ph1 : ph2;
+        const T ophi = P.om_phi * phi;
+        const T sqx = P.src_phi * qx[i], sqy = P.src_phi * qy[i];
+#pragma unroll
+        for (int a = 0; a < 9; a++) {
+            const T w = wgt<T>(a);
+            const T eu = T(cx(a)) * ux + T(cy(a)) * uy;
+            const T gam = w * (T(1) + T(3) * eu + T(4.5) * eu * eu - uu);
+            const T gv = T(gs[(i * 9 + a) * ps + n]) - g_off<MODE, T>(a);
+            const T v = P.keep_phi * gv + ophi * gam + w * (T(cx(a)) * sqx + T(cy(a)) * sqy);
+            int xn = x + cx(a);
+            xn = xn < 0 ? nx - 1 : (xn >= nx ? 0 : xn);
+            int yn = y + cy(a);
+            if (yn >= 0 && yn < ny)
+                gd[(i * 9 + a) * ps + (long long)yn * pitch + xn] = S(v + g_off<MODE, T>(a));
+            else
+                gd[(i * 9 + opp(a)) * ps + n] = S(v + g_off<MODE, T>(opp(a)));
+        }
+    }
+}
+
+// ---------------------------------------------------------------- init
+template <typename T, int MODE>
+__global__ void init_kernel(Phys<T> P, double u_max, double r1, double r2, double xcen,
+                            double ycen, double xi, void *fv, void *gv, T *macro) {
+    using S = typename StoreT<MODE>::type;
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= P.nx || y >= P.ny) return;
+    long long n = (long long)y * P.pitch + x;
+    const double nyd = P.ny;
+    const double u0 = u_max * 4.0 * (y + 0.5) * (nyd - 0.5 - y) / (nyd * nyd);
+    double dx = x - xcen;
+    dx -= P.nx * floor(dx / P.nx + 0.5);  // nearest periodic image
+    const double dy = y - ycen;
+    const double r = sqrt(dx * dx + dy * dy);
+    const double pout = 0.5 * (1.0 - tanh(2.0 * (r - r2) / xi));
+    const double p1 = 0.5 * (1.0 - tanh(2.0 * (r - r1) / xi));
+    const double p2 = pout - p1;
+    S *f = static_cast<S *>(fv);
+    S *g = static_cast<S *>(gv);
+    for (int a = 0; a < 9; a++) {
+        const double w = wgt<double>(a), eu = cx(a) * u0;
+        const double gam = w * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * u0 * u0);
+        f[a * P.ps + n] = S((gam - w) + double(f_off<MODE, T>(a)));
+        g[a * P.ps + n] = S(p1 * gam + double(g_off<MODE, T>(a)));
+        g[(9 + a) * P.ps + n] = S(p2 * gam + double(g_off<MODE, T>(a)));
+    }
+    if (macro) {
+        macro[n] = T(u0);
+        macro[P.ps + n] = T(0);
+        macro[2 * P.ps + n] = T(0);
+    }
+}
+
+// ---------------------------------------------------------------- exchange
+template <typename T, int MODE>
+__global__ void export_kernel(Phys<T> P, const void *fv, const void *gv, double *fo,
+                              double *go) {
+    using S = typename StoreT<MODE>::type;
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= P.nx || y >= P.ny) return;
+    long long n = (long long)y * P.pitch + x, m = (long long)y * P.nx + x;
+    long long N = (long long)P.nx * P.ny;
+    const S *f = static_cast<const S *>(fv);
+    const S *g = static_cast<const S *>(gv);
+    for (int a = 0; a < 9; a++) {
+        if (fo) fo[a * N + m] = double(T(f[a * P.ps + n]) - f_off<MODE, T>(a));
+        if (go) {
+            go[a * N + m] = double(T(g[a * P.ps + n]) - g_off<MODE, T>(a));
+            go[(9 + a) * N + m] = double(T(g[(9 + a) * P.ps + n]) - g_off<MODE, T>(a));
+        }
+    }
+}
+
+template <typename T, int MODE>
+__global__ void import_kernel(Phys<T> P, const double *fi, const double *gi, void *fv,
+                              void *gv) {
+    using S = typename StoreT<MODE>::type;
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= P.nx || y >= P.ny) return;
+    long long n = (long long)y * P.pitch + x, m = (long long)y * P.nx + x;
+    long long N = (long long)P.nx * P.ny;
+    S *f = static_cast<S *>(fv);
+    S *g = static_cast<S *>(gv);
+    for (int a = 0; a < 9; a++) {
+        if (fi) f[a * P.ps + n] = S(fi[a * N + m] + double(f_off<MODE, T>(a)));
+        if (gi) {
+            g[a * P.ps + n] = S(gi[a * N + m] + double(g_off<MODE, T>(a)));
+            g[(9 + a) * P.ps + n] = S(gi[(9 + a) * N + m] + double(g_off<MODE, T>(a)));
+        }
+    }
+}
+
+template <typename T>
+__global__ void plane_to_f64(const T *src, int nx, int ny, int pitch, double *dst) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= nx || y >= ny) return;
+    dst[(long long)y * nx + x] = double(src[(long long)y * pitch + x]);
+}
+
+template <typename T>
+__global__ void plane_from_f64(const double *src, int nx, int ny, int pitch, T *dst) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= nx || y >= ny) return;
+    dst[(long long)y * pitch + x] = T(src[(long long)y * nx + x]);
+}
+
+template <typename T>
+__global__ void phi3_to_f64(const T *p1, const T *p2, int nx, int ny, int pitch, double *dst) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= nx || y >= ny) return;
+    long long n = (long long)y * pitch + x;
+    dst[(long long)y * nx + x] = double(T(1) - p1[n] - p2[n]);
+}
+
+// ---------------------------------------------------------------- launchers
+static dim3 grid2(int nx, int ny, dim3 b) { return dim3((nx + b.x - 1) / b.x, (ny + b.y - 1) / b.y); }
+
+#define FCD_MODE_SWITCH(mode, T, CALL)                                         \
+    do {                                                                       \
+        if constexpr (sizeof(T) == 8) {                                        \
+            constexpr int M = MODE_FP64;                                       \
+            CALL;                                                              \
+        } else {                                                               \
+            if ((mode) == MODE_FP32) {                                         \
+                constexpr int M = MODE_FP32;                                   \
+                CALL;                                                          \
+            } else {                                                           \
+                constexpr int M = MODE_FP32_OFFSET;                            \
+                CALL;                                                          \
+            }                                                                  \
+        }                                                                      \
+    } while (0)
+
+template <typename T>
+void launch_phase(int mode, const Phys<T> &P, const void *g, T *phi1, T *phi2, T *k,
+                  cudaStream_t s) {
+    dim3 b(32, 8), gr = grid2(P.nx, P.ny, b);
+    FCD_MODE_SWITCH(mode, T, (phase_kernel<T, M><<<gr, b, 0, s>>>(P, g, phi1, phi2, k)));
+}
+
+template <typename T>
+void launch_collide(int mode, const LbmArgs<T> &a, cudaStream_t s) {
+    dim3 b(TX, TY), gr = grid2(a.P.nx, a.P.ny, b);
+    FCD_MODE_SWITCH(mode, T, (collide_kernel<T, M><<<gr, b, 0, s>>>(a)));
+}
+
+template <typename T>
+void launch_init(int mode, const Phys<T> &P, double u_max, double r1, double r2, double xc,
+                 double yc, double xi, void *f, void *g, T *macro, cudaStream_t s) {
+    dim3 b(32, 8), gr = grid2(P.nx, P.ny, b);
+    FCD_MODE_SWITCH(mode, T,
+                    (init_kernel<T, M><<<gr, b, 0, s>>>(P, u_max, r1, r2, xc, yc, xi, f, g, macro)));
+}
+
+template <typename T>
+void launch_export(int mode, const Phys<T> &P, const void *f, const void *g, double *fo,
+                   double *go, cudaStream_t s) {
+    dim3 b(32, 8), gr = grid2(P.nx, P.ny, b);
+    FCD_MODE_SWITCH(mode, T, (export_kernel<T, M><<<gr, b, 0, s>>>(P, f, g, fo, go)));
+}
+
+template <typename T>
+void launch_import(int mode, const Phys<T> &P, const double *fi, const double *gi, void *f,
+                   void *g, cudaStream_t s) {
+    dim3 b(32, 8), gr = grid2(P.nx, P.ny, b);
+    FCD_MODE_SWITCH(mode, T, (import_kernel<T, M><<<gr, b, 0, s>>>(P, fi, gi, f, g)));
+}
+
+template <typename T>
+void launch_plane_to_f64(const T *src, int nx, int ny, int pitch, double *dst, cudaStream_t s) {
+    dim3 b(32, 8);
+    plane_to_f64<T><<<grid2(nx, ny, b), b, 0, s>>>(src, nx, ny, pitch, dst);
+}
+
+template <typename T>
+void launch_plane_from_f64(const double *src, int nx, int ny, int pitch, T *dst, cudaStream_t s) {
+    dim3 b(32, 8);
+    plane_from_f64<T><<<grid2(nx, ny, b), b, 0, s>>>(src, nx, ny, pitch, dst);
+}
+
+template <typename T>
+void launch_phi3_to_f64(const T *p1, const T *p2, int nx, int ny, int pitch, double *dst,
+                        cudaStream_t s) {
+    dim3 b(32, 8);
+    phi3_to_f64<T><<<grid2(nx, ny, b), b, 0, s>>>(p1, p2, nx, ny, pitch, dst);
+}
+
+#define FCD_INST(T)                                                                           \
+    template void launch_phase<T>(int, const Phys<T> &, const void *, T *, T *, T *,          \
+                                  cudaStream_t);                                              \
+    template void launch_collide<T>(int, const LbmArgs<T> &, cudaStream_t);                    \
+    template void launch_init<T>(int, const Phys<T> &, double, double, double, double, double, \
+                                 double, void *, void *, T *, cudaStream_t);                   \
+    template void launch_export<T>(int, const Phys<T> &, const void *, const void *, double *, \
+                                   double *, cudaStream_t);                                    \
+    template void launch_import<T>(int, const Phys<T> &, const double *, const double *,       \
+                                   void *, void *, cudaStream_t);                              \
+    template void launch_plane_to_f64<T>(const T *, int, int, int, double *, cudaStream_t);    \
+    template void launch_plane_from_f64<T>(const double *, int, int, int, T *, cudaStream_t);  \
+    template void launch_phi3_to_f64<T>(const T *, const T *, int, int, int, double *,         \
+                                        cudaStream_t);
+FCD_INST(float)
+FCD_INST(double)
+
+}  // namespace fcd

@@ -1,0 +1,280 @@
+"""Thin ctypes binding of libfcd.so (C ABI in include/fcd.h).
+
+Argument marshalling only: every step of the path runs in the CUDA library.
+The functions keep the C names; ``Channel`` wraps one context for Python use
+(PyTorch supplies the CUDA stream and, optionally, the device allocator).
+Loading fails loudly when the library is missing; there is no CPU fallback.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+DP = C.POINTER(C.c_double)
+
+FCD_OK, FCD_EINVAL, FCD_ENOMEM, FCD_ECUDA, FCD_ENOCONV, FCD_EUNSTABLE, FCD_ESTATE = range(7)
+FCD_FP64, FCD_FP32, FCD_FP32_OFFSET = range(3)
+PRECISION = {"fp64": FCD_FP64, "fp32": FCD_FP32, "fp32_offset": FCD_FP32_OFFSET}
+FIELDS = {"phi1": 0, "phi2": 1, "phi3": 2, "ux": 3, "uy": 4, "pstar": 5, "psi": 6}
+STATUS = {0: "FCD_OK", 1: "FCD_EINVAL", 2: "FCD_ENOMEM", 3: "FCD_ECUDA", 4: "FCD_ENOCONV",
+          5: "FCD_EUNSTABLE", 6: "FCD_ESTATE"}
+
+
+class fcd_params(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int), ("ny", C.c_int),
+        ("rho", C.c_double * 3), ("nu", C.c_double * 3), ("chi", C.c_double * 3),
+        ("mobility", C.c_double), ("xi", C.c_double), ("eta", C.c_double),
+        ("Ca", C.c_double), ("Bo_m", C.c_double), ("alpha", C.c_double),
+        ("r1", C.c_double), ("r2", C.c_double), ("xc", C.c_double), ("yc", C.c_double),
+        ("s13_over_s12", C.c_double), ("s23_over_s12", C.c_double), ("sigma23", C.c_double),
+        ("u_max", C.c_double), ("ferro_phase", C.c_int), ("precision", C.c_int),
+        ("mag_tol", C.c_double), ("mag_max_iter", C.c_int), ("eps_n", C.c_double),
+    ]
+
+
+class fcd_obs(C.Structure):
+    _fields_ = [
+        ("step", C.c_long), ("t_star", C.c_double),
+        ("T_o", C.c_double), ("T_i", C.c_double),
+        ("lx_o", C.c_double), ("ly_o", C.c_double), ("lx_i", C.c_double), ("ly_i", C.c_double),
+        ("xc_core", C.c_double), ("yc_core", C.c_double),
+        ("xc_shell", C.c_double), ("yc_shell", C.c_double),
+        ("mass", C.c_double * 3),
+        ("breakup", C.c_int), ("b_step", C.c_long), ("xb", C.c_double), ("yb", C.c_double),
+        ("tb_star", C.c_double), ("Lb_star", C.c_double), ("yb_star", C.c_double),
+        ("mag_iters", C.c_int), ("mag_resid", C.c_double),
+    ]
+
+    def as_dict(self):
+        return {n: (list(getattr(self, n)) if n == "mass" else getattr(self, n))
+                for n, _ in self._fields_}
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+_lib = None
+
+# symbol -> (restype, argtypes)
+_SIGS = {
+    "fcd_set_allocator": (None, [ALLOC_FN, FREE_FN, C.c_void_p]),
+    "fcd_create": (C.c_int, [C.POINTER(fcd_params), C.POINTER(C.c_void_p)]),
+    "fcd_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "fcd_step": (C.c_int, [C.c_void_p, C.c_long]),
+    "fcd_solve_magnetic": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_int), DP]),
+    "fcd_observables": (C.c_int, [C.c_void_p, C.POINTER(fcd_obs)]),
+    "fcd_get_field": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t]),
+    "fcd_get_populations": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "fcd_set_populations": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_long]),
+    "fcd_state_bytes": (C.c_size_t, [C.c_void_p]),
+    "fcd_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "fcd_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "fcd_get_derived": (C.c_int, [C.c_void_p, DP]),
+    "fcd_kernel_launches": (C.c_long, [C.c_void_p]),
+    "fcd_set_profiling": (C.c_int, [C.c_void_p, C.c_int]),
+    "fcd_last_step_profile": (C.c_int, [C.c_void_p, DP]),
+    "fcd_last_error": (C.c_char_p, [C.c_void_p]),
+    "fcd_destroy": (None, [C.c_void_p]),
+}
+
+
+def lib_path():
+    return _build.LIB
+
+
+def load(build=True):
+    """Load libfcd.so (building it first when asked); raises if it cannot."""
+    global _lib
+    if _lib is None:
+        path = _build.build() if build else _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError("libfcd.so is missing at %s; run the build first" % path)
+        L = C.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class FcdError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+def make_params(cfg):
+    """fcd_params from a workload dictionary (see workloads.py)."""
+    p = fcd_params()
+    p.nx, p.ny = int(cfg["nx"]), int(cfg["ny"])
+    for i in range(3):
+        p.rho[i], p.nu[i], p.chi[i] = cfg["rho"][i], cfg["nu"][i], cfg["chi"][i]
+    p.mobility = cfg.get("mobility", 0.3)
+    p.xi = cfg.get("xi", 5.0)
+    p.eta = cfg.get("eta", 0.0)
+    p.Ca = cfg.get("Ca", 0.1)
+    p.Bo_m = cfg.get("Bo_m", 0.0)
+    p.alpha = cfg.get("alpha", 0.0)
+    p.r1, p.r2, p.xc, p.yc = cfg["r1"], cfg["r2"], cfg["xc"], cfg["yc"]
+    p.s13_over_s12 = cfg.get("s13_over_s12", 1.0)
+    p.s23_over_s12 = cfg.get("s23_over_s12", 1.0)
+    p.sigma23 = cfg.get("sigma23", 0.0)
+    p.u_max = cfg.get("u_max", 0.01)
+    p.ferro_phase = int(cfg.get("ferro_phase", 0))
+    prec = cfg.get("precision", "fp64")
+    p.precision = PRECISION[prec] if isinstance(prec, str) else int(prec)
+    p.mag_tol = cfg.get("mag_tol", 1e-10)
+    p.mag_max_iter = int(cfg.get("mag_max_iter", 200))
+    p.eps_n = cfg.get("eps_n", 1e-12 if p.precision == FCD_FP64 else 1e-6)
+    return p
+
+
+_torch_alloc = None
+
+
+def use_torch_allocator():
+    """Route later fcd_create allocations through PyTorch's caching allocator."""
+    global _torch_alloc
+    import torch
+
+    def _alloc(size, user):
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(size)))
+        except Exception:
+            return None
+
+    def _free(ptr, user):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    _torch_alloc = (ALLOC_FN(_alloc), FREE_FN(_free))
+    load().fcd_set_allocator(_torch_alloc[0], _torch_alloc[1], None)
+
+
+class Channel:
+    """One context of the coupled step (owns the C handle)."""
+
+    def __init__(self, cfg, stream=None, torch_alloc=True):
+        L = load()
+        self.cfg = dict(cfg)
+        if torch_alloc and _torch_alloc is None:
+            use_torch_allocator()
+        self.params = make_params(cfg)
+        h = C.c_void_p()
+        st = L.fcd_create(C.byref(self.params), C.byref(h))
+        if st != FCD_OK:
+            raise FcdError(st, L.fcd_last_error(None).decode())
+        self.h = h
+        self.nx, self.ny = self.params.nx, self.params.ny
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        self.check(L.fcd_set_stream(self.h, C.c_void_p(stream)))
+
+    def check(self, st, allow=()):
+        if st != FCD_OK and st not in allow:
+            raise FcdError(st, load().fcd_last_error(self.h).decode())
+        return st
+
+    def step(self, n=1):
+        return self.check(load().fcd_step(self.h, int(n)))
+
+    def solve_magnetic(self, tol=0.0, max_iter=0):
+        it, res = C.c_int(0), C.c_double(0)
+        st = load().fcd_solve_magnetic(self.h, tol, max_iter, C.byref(it), C.byref(res))
+        self.check(st, allow=(FCD_ENOCONV,))
+        return it.value, res.value, st
+
+    def observe(self, allow=()):
+        o = fcd_obs()
+        st = load().fcd_observables(self.h, C.byref(o))
+        self.check(st, allow=allow)
+        return o.as_dict()
+
+    def field(self, name, out=None):
+        N = self.nx * self.ny
+        if out is None:
+            out = np.empty((self.ny, self.nx))
+        ptr = out.ctypes.data if isinstance(out, np.ndarray) else int(out.data_ptr())
+        self.check(load().fcd_get_field(self.h, FIELDS[name], C.c_void_p(ptr), N))
+        return out
+
+    def populations(self):
+        f = np.empty((9, self.ny, self.nx))
+        g = np.empty((2, 9, self.ny, self.nx))
+        psi = np.empty((self.ny, self.nx))
+        self.check(load().fcd_get_populations(self.h, C.c_void_p(f.ctypes.data),
+                                              C.c_void_p(g.ctypes.data), C.c_void_p(psi.ctypes.data)))
+        return f, g, psi
+
+    def set_populations(self, f=None, g=None, psi=None, step=0):
+        ptr = lambda a: None if a is None else C.c_void_p(np.ascontiguousarray(a, np.float64).ctypes.data)
+        keep = [np.ascontiguousarray(a, np.float64) if a is not None else None for a in (f, g, psi)]
+        self.check(load().fcd_set_populations(self.h, *[ptr(a) for a in keep], int(step)))
+
+    def state_bytes(self):
+        return load().fcd_state_bytes(self.h)
+
+    def get_state(self, buf):
+        """buf: writable host numpy uint8 array or torch tensor (host or device)."""
+        ptr = buf.ctypes.data if isinstance(buf, np.ndarray) else int(buf.data_ptr())
+        n = buf.nbytes if isinstance(buf, np.ndarray) else buf.numel() * buf.element_size()
+        return self.check(load().fcd_get_state(self.h, C.c_void_p(ptr), n))
+
+    def set_state(self, buf):
+        ptr = buf.ctypes.data if isinstance(buf, np.ndarray) else int(buf.data_ptr())
+        n = buf.nbytes if isinstance(buf, np.ndarray) else buf.numel() * buf.element_size()
+        return self.check(load().fcd_set_state(self.h, C.c_void_p(ptr), n))
+
+    def derived(self):
+        out = (C.c_double * 15)()
+        self.check(load().fcd_get_derived(self.h, out))
+        names = ["u_avg", "sigma12", "sigma13", "sigma23", "gamma1", "gamma2", "gamma3", "gammaT",
+                 "tau1", "tau2", "tau3", "tau_phi", "mu0H0sq", "H0", "G"]
+        return dict(zip(names, list(out)))
+
+    def set_profiling(self, on=True):
+        self.check(load().fcd_set_profiling(self.h, 1 if on else 0))
+
+    def last_step_profile(self):
+        ms = (C.c_double * 4)()
+        self.check(load().fcd_last_step_profile(self.h, ms))
+        return dict(zip(["phase", "solve", "collide", "step"], list(ms)))
+
+    def kernel_launches(self):
+        return load().fcd_kernel_launches(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().fcd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# C-name aliases (same names as the ABI)
+def fcd_create(cfg):
+    return Channel(cfg)
+
+
+def fcd_step(ch, n):
+    return ch.step(n)
+
+
+def fcd_solve_magnetic(ch, tol=0.0, max_iter=0):
+    return ch.solve_magnetic(tol, max_iter)
+
+
+def fcd_observables(ch):
+    return ch.observe()
+
+
+def fcd_destroy(ch):
+    ch.close()

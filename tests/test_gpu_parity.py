@@ -1,0 +1,215 @@
+"""GPU path against the FP64 oracle, element by element (needs a GB300).
+
+Tolerances: FP64 storage and arithmetic match the oracle to 1e-10 (phase
+fields absolute, velocity relative to its maximum) with both potential
+solves at 1e-13; the FP32 forms match the FP64 oracle to 1e-4.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2410_11129_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fcd():
+    import torch
+    assert torch.cuda.is_available(), "needs a CUDA device"
+    from paper_2410_11129_gb300 import fcd as F
+    F.load()
+    return F
+
+
+def parity_cfg(**kw):
+    base = dict(nx=48, ny=20, r1=3.0, r2=6.0, xc=14.0, xi=4.0, Ca=0.1, Bo_m=2.0,
+                ferro="shell", chi_ferro=1.0, mag_tol=1e-13, mag_max_iter=300)
+    base.update(kw)
+    return W.small(**base)
+
+
+def compare_fp64(orc, cfg, steps, tol=1e-10):
+    from paper_2410_11129_gb300 import fcd as F
+    sim = orc.Sim(cfg)
+    ch = F.Channel(dict(cfg, precision="fp64"))
+    sim.step(steps)
+    ch.step(steps)
+    f, g, psi = ch.populations()
+    ux, uy = ch.field("ux"), ch.field("uy")
+    phi = np.stack([ch.field("phi1"), ch.field("phi2")])
+    ophi = sim.phi()[:2]
+    umax = np.abs(sim.macro[:2]).max()
+    err = {
+        "phi": np.abs(phi - ophi).max(),
+        "u_rel": max(np.abs(ux - sim.macro[0]).max(), np.abs(uy - sim.macro[1]).max()) / umax,
+        "f": np.abs(f - sim.f).max(),
+        "g": np.abs(g - sim.g).max(),
+        "pstar": np.abs(ch.field("pstar") - sim.macro[2]).max(),
+        "psi_rel": np.abs(psi - sim.psi).max() / max(np.abs(sim.psi).max(), 1e-300),
+    }
+    ob, oo = ch.observe(), sim.observe()
+    ch.close()
+    assert err["phi"] <= tol, err
+    assert err["u_rel"] <= tol, err
+    assert err["f"] <= tol and err["g"] <= tol and err["pstar"] <= tol, err
+    assert err["psi_rel"] <= 1e-8 or np.abs(sim.psi).max() == 0, err
+    for k in ("T_o", "T_i", "xc_core", "yc_core", "xc_shell", "yc_shell", "lx_o", "ly_o"):
+        assert abs(ob[k] - oo[k]) <= 1e-8 * max(1.0, abs(oo[k])), (k, ob[k], oo[k])
+    for i in range(3):
+        assert abs(ob["mass"][i] - oo["mass"][i]) <= 1e-9 * abs(oo["mass"][i])
+    assert ob["breakup"] == oo["breakup"] and ob["b_step"] == oo["b_step"]
+    return err
+
+
+@pytest.mark.parametrize("kw", [
+    dict(),                                                           # shell ferro, alpha 0
+    dict(ferro="core", chi_ferro=2.0, alpha=np.pi / 2, rho_r=2.0, nu_r=2.0, Ca=0.2, Bo_m=3.0),
+    dict(nx=38, ny=13, xc=11.0, yc=6.3, alpha=0.6),                   # ragged tiles, odd ny, off-centre
+])
+def test_fp64_parity_small(orc, fcd, kw):
+    compare_fp64(orc, parity_cfg(**kw), 120)
+
+
+def test_fp64_parity_no_field_and_static(orc, fcd):
+    compare_fp64(orc, parity_cfg(Bo_m=0.0), 60)
+    compare_fp64(orc, parity_cfg(u_max=0.0, sigma23=0.01, Ca=0.0), 60)
+
+
+def test_fp64_parity_minimal_grid(orc, fcd):
+    compare_fp64(orc, parity_cfg(nx=4, ny=2, r1=-1000.0, r2=-1000.0, xc=0.0, yc=0.0,
+                                 Bo_m=0.0, ferro="none"), 50)
+
+
+def test_fp64_parity_200x40_channel(orc, fcd):
+    """The 200x40 FP64 channel (shell ferrofluid, Ca 0.1, Bo_m 1) over its 1000
+    steps, both solves at 1e-13."""
+    cfg = dict(W.C1, mag_tol=1e-13, mag_max_iter=300)
+    err = compare_fp64(orc, cfg, 1000)
+    print("200x40 parity", err)
+
+
+def test_solver_matches_oracle_and_layered_exact(orc, fcd):
+    """fcd_solve_magnetic on a droplet state reaches the oracle's CG answer."""
+    cfg = parity_cfg(ferro="core", chi_ferro=2.0, alpha=0.9, Bo_m=4.0)
+    from paper_2410_11129_gb300 import fcd as F
+    ch = F.Channel(dict(cfg, precision="fp64"))
+    it, res, st = ch.solve_magnetic(1e-13, 300)
+    assert st == F.FCD_OK and res <= 1e-13
+    f, g, psi = ch.populations()
+    phi, k = orc.phase(cfg, g)
+    ref, st2, _, _ = orc.mag_solve(k, ch.derived()["H0"], cfg["alpha"], tol=1e-13)
+    assert st2 == 0
+    assert np.abs(psi - ref).max() <= 1e-10 * np.abs(ref).max()
+    ch.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp32_offset"])
+def test_fp32_forms_against_fp64_oracle(orc, fcd, prec):
+    cfg = parity_cfg(mag_tol=1e-5)
+    sim = orc.Sim(dict(cfg, mag_tol=1e-13))
+    from paper_2410_11129_gb300 import fcd as F
+    ch = F.Channel(dict(cfg, precision=prec))
+    sim.step(200)
+    ch.step(200)
+    phi = np.stack([ch.field("phi1"), ch.field("phi2")])
+    err_phi = np.abs(phi - sim.phi()[:2]).max()
+    umax = np.abs(sim.macro[:2]).max()
+    err_u = np.abs(ch.field("ux") - sim.macro[0]).max() / umax
+    ob, oo = ch.observe(), sim.observe()
+    print(prec, "phi", err_phi, "u_rel", err_u, {k: ob[k] - oo[k] for k in ("T_o", "T_i", "xc_shell")})
+    assert err_phi <= 1e-4 and err_u <= 1e-3
+    for k in ("T_o", "T_i", "xc_core", "yc_core", "xc_shell", "yc_shell"):
+        assert abs(ob[k] - oo[k]) <= 1e-4 * max(1.0, abs(oo[k])), k
+    ch.close()
+
+
+def test_mass_conservation_gpu(fcd):
+    from paper_2410_11129_gb300 import fcd as F
+    for prec, tol in (("fp64", 1e-12), ("fp32", 2e-6), ("fp32_offset", 2e-6)):
+        ch = F.Channel(dict(parity_cfg(mag_tol=1e-6 if prec != "fp64" else 1e-10), precision=prec))
+        m0 = np.array(ch.observe()["mass"])
+        ch.step(300)
+        m1 = np.array(ch.observe()["mass"])
+        assert np.all(np.abs(m1 - m0) <= tol * np.abs(m0)), (prec, m1 - m0)
+        ch.close()
+
+
+def test_checkpoint_resume_bitwise(fcd):
+    from paper_2410_11129_gb300 import fcd as F
+    for prec in ("fp64", "fp32_offset"):
+        cfg = dict(parity_cfg(mag_tol=1e-8), precision=prec)
+        a = F.Channel(cfg)
+        a.step(30)
+        snap = np.zeros(a.state_bytes(), np.uint8)
+        a.get_state(snap)
+        a.step(40)
+        fa, ga, pa = a.populations()
+        b = F.Channel(cfg)
+        b.set_state(snap)
+        b.step(40)
+        fb, gb, pb = b.populations()
+        assert np.array_equal(fa, fb) and np.array_equal(ga, gb) and np.array_equal(pa, pb)
+        assert a.observe()["step"] == b.observe()["step"] == 70
+        a.close()
+        b.close()
+
+
+def test_graph_and_host_loop_agree(fcd, monkeypatch):
+    from paper_2410_11129_gb300 import fcd as F
+    cfg = dict(parity_cfg(mag_tol=1e-10), precision="fp64")
+    a = F.Channel(cfg)
+    a.step(25)
+    monkeypatch.setenv("FCD_NO_GRAPH", "1")
+    b = F.Channel(cfg)
+    b.step(25)
+    for x, y in zip(a.populations(), b.populations()):
+        assert np.array_equal(x, y)
+    a.close()
+    b.close()
+
+
+def test_poiseuille_magic_parameter_gpu(fcd):
+    """tau = 3/8 puts the half-way wall exactly: the parabola to round-off."""
+    from paper_2410_11129_gb300 import fcd as F
+    cfg = W.channel(8, 16, -1000.0, -1000.0, xc=0.0, yc=0.0, xi=4.0, Bo_m=0.0, ferro="none")
+    cfg["nu"] = [1 / 8] * 3
+    ch = F.Channel(dict(cfg, precision="fp64"))
+    ch.step(12000)
+    y = np.arange(16)
+    exact = 0.01 * 4 * (y + 0.5) * (16 - 0.5 - y) / 256.0
+    assert np.abs(ch.field("ux")[:, 3] - exact).max() < 1e-10
+    ch.close()
+
+
+def test_breakup_record_gpu(orc, fcd):
+    """A thin shell touches at once: step 0 and the smallest (y, x), as the oracle."""
+    cfg = parity_cfg(r1=4.0, r2=5.0, Bo_m=0.0, ferro="none")
+    from paper_2410_11129_gb300 import fcd as F
+    ch = F.Channel(dict(cfg, precision="fp64"))
+    sim = orc.Sim(cfg)
+    ch.step(3)
+    sim.step(3)
+    ob, oo = ch.observe(), sim.observe()
+    assert ob["breakup"] == oo["breakup"] == 1
+    assert (ob["b_step"], ob["xb"], ob["yb"]) == (oo["b_step"], oo["xb"], oo["yb"])
+    ch.close()
+
+
+def test_full_size_1600x200_fp32_sampled(orc, fcd):
+    """The benchmark's 1600x200 FP32 channel in the same launch path: a few
+    steps against the FP64 oracle on whole fields."""
+    cfg = dict(W.C2)
+    from paper_2410_11129_gb300 import fcd as F
+    ch = F.Channel(cfg)
+    sim = orc.Sim(dict(cfg, mag_tol=1e-10, mag_max_iter=20000))
+    ch.step(3)
+    sim.step(3)
+    phi = np.stack([ch.field("phi1"), ch.field("phi2")])
+    assert np.abs(phi - sim.phi()[:2]).max() <= 1e-4
+    umax = np.abs(sim.macro[:2]).max()
+    assert np.abs(ch.field("ux") - sim.macro[0]).max() <= 1e-3 * umax
+    ob = ch.observe()
+    assert ob["mag_resid"] <= cfg["mag_tol"]
+    ch.close()
