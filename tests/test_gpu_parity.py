@@ -142,8 +142,8 @@ def test_mass_conservation_gpu(fcd):
 
 def test_checkpoint_resume_bitwise(fcd):
     from paper_2410_11129_gb300 import fcd as F
-    for prec in ("fp64", "fp32_offset"):
-        cfg = dict(parity_cfg(mag_tol=1e-8), precision=prec)
+    for prec, tol in (("fp64", 1e-10), ("fp32_offset", 1e-4)):
+        cfg = dict(parity_cfg(mag_tol=tol), precision=prec)
         a = F.Channel(cfg)
         a.step(30)
         snap = np.zeros(a.state_bytes(), np.uint8)
@@ -215,5 +215,5 @@ def test_full_size_1600x200_fp32_sampled(orc, fcd):
     umax = np.abs(sim.macro[:2]).max()
     assert np.abs(ch.field("ux") - sim.macro[0]).max() <= 1e-3 * umax
     ob = ch.observe()
-    assert ob["mag_resid"] <= cfg["mag_tol"]
+    assert ob["mag_resid"] <= cfg["mag_tol"] and ob["mag_iters"] >= 0
     ch.close()
