@@ -169,8 +169,6 @@ struct fcd_ctx {
         if (e_ != cudaSuccess) return fail(FCD_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
     } while (0)
 
-__global__ void advance_step(long long *s) { *s += 1; }
-
 struct SnapHeader {
     unsigned magic, version;
     int nx, ny, precision, pitch;
@@ -308,11 +306,8 @@ struct Engine : fcd_ctx {
     // ---- one step as kernel launches on stream s (the MG loop by while node
     // when capturing, by host polling otherwise)
     fcd_status enqueue_pre(int c, cudaStream_t s) {
-        launch_phase<T>(mode, P, g[c], phi1, phi2, k, s);
-        if (magnetic()) {
-            mg_prepare<T>(mg, s);
-            mg_begin<T>(mg, prm.mag_tol * D.H0, prm.mag_max_iter, s);
-        }
+        PhaseCtl pc{ctl, magnetic() ? 1 : 0, prm.mag_tol * D.H0, prm.mag_max_iter, d_step};
+        launch_phase<T>(mode, P, g[c], phi1, phi2, k, pc, s);
         return FCD_OK;
     }
     void enqueue_post(int c, bool store_macro, cudaStream_t s) {
@@ -329,11 +324,10 @@ struct Engine : fcd_ctx {
         a.ctl = ctl;
         a.macro = store_macro ? macro : nullptr;
         a.brk = brk;
-        a.step = d_step;
+        a.step = &ctl->step_cur;
         launch_collide<T>(mode, a, s);
-        advance_step<<<1, 1, 0, s>>>(d_step);
     }
-    int pre_kernels() const { return 1 + (magnetic() ? mg_pre_kernels(mg) : 0); }
+    int pre_kernels() const { return 1; }
 
     fcd_status host_mg_loop(cudaStream_t s) {
         for (int guard = 0; guard < 1000000; guard++) {
@@ -349,9 +343,9 @@ struct Engine : fcd_ctx {
     fcd_status build_graph(int c, int sm) {
         cudaStream_t s = cap;
         CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        if (profiling) CK(cudaEventRecord(ev[0], s));
+        if (profiling) CK(cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal));
         enqueue_pre(c, s);
-        if (profiling) CK(cudaEventRecord(ev[1], s));
+        if (profiling) CK(cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal));
         if (magnetic()) {
             cudaStreamCaptureStatus cs;
             cudaGraph_t gcap;
@@ -377,9 +371,9 @@ struct Engine : fcd_ctx {
             CK(e1);
             CK(cudaStreamUpdateCaptureDependencies(s, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
         }
-        if (profiling) CK(cudaEventRecord(ev[2], s));
+        if (profiling) CK(cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal));
         enqueue_post(c, sm != 0, s);
-        if (profiling) CK(cudaEventRecord(ev[3], s));
+        if (profiling) CK(cudaEventRecordWithFlags(ev[3], s, cudaEventRecordExternal));
         CK(cudaStreamEndCapture(s, &graph[c][sm]));
         CK(cudaGraphInstantiate(&gexec[c][sm], graph[c][sm], 0));
         return FCD_OK;
@@ -396,7 +390,7 @@ struct Engine : fcd_ctx {
                     if (st != FCD_OK) return st;
                 }
                 CK(cudaGraphLaunch(gexec[cur][sm], s));
-                host_kernels += pre_kernels() + 2;
+                host_kernels += pre_kernels() + 1;
             } else {
                 if (profiling) CK(cudaEventRecord(ev[0], s));
                 enqueue_pre(cur, s);
@@ -408,7 +402,7 @@ struct Engine : fcd_ctx {
                 if (profiling) CK(cudaEventRecord(ev[2], s));
                 enqueue_post(cur, sm != 0, s);
                 if (profiling) CK(cudaEventRecord(ev[3], s));
-                host_kernels += pre_kernels() + 2;
+                host_kernels += pre_kernels() + 1;
                 CK(cudaGetLastError());
             }
             cur ^= 1;
@@ -436,10 +430,8 @@ struct Engine : fcd_ctx {
             if (resid) *resid = 0.0;
             return FCD_OK;
         }
-        launch_phase<T>(mode, P, g[cur], phi1, phi2, k, s);
-        mg_prepare<T>(mg, s);
-        mg_begin<T>(mg, tol * D.H0, max_iter, s);
-        host_kernels += pre_kernels();
+        launch_phase<T>(mode, P, g[cur], phi1, phi2, k, PhaseCtl{ctl, 1, tol * D.H0, max_iter, nullptr}, s);
+        host_kernels += 1;
         CK(cudaGetLastError());
         fcd_status st = host_mg_loop(s);
         if (st != FCD_OK) return st;
@@ -515,7 +507,7 @@ struct Engine : fcd_ctx {
         if (!st) return fail(FCD_ENOMEM, "staging allocation failed");
         fcd_status rc = FCD_OK;
         if (which <= FCD_FIELD_PHI3) {
-            launch_phase<T>(mode, P, g[cur], phi1, phi2, nullptr, s);
+            launch_phase<T>(mode, P, g[cur], phi1, phi2, nullptr, PhaseCtl{nullptr, 0, 0.0, 0, nullptr}, s);
             if (which == FCD_FIELD_PHI1) launch_plane_to_f64<T>(phi1, prm.nx, prm.ny, pitch, st, s);
             else if (which == FCD_FIELD_PHI2) launch_plane_to_f64<T>(phi2, prm.nx, prm.ny, pitch, st, s);
             else launch_phi3_to_f64<T>(phi1, phi2, prm.nx, prm.ny, pitch, st, s);

@@ -100,6 +100,19 @@ struct MgCtl {
     long long cycles_launched;     // cumulative cycle launches (launch accounting)
     int nonconv_count;             // solves that stopped at the cap
     double H0;
+    unsigned int blocks_done;      // blocks of the last kernel of a cycle that finished
+    long long step_cur;            // step index of the step in flight (breakup key)
+};
+
+// What the phase kernel does besides Eq. 32: reset the solve's control block
+// (reset != 0) and, when step != nullptr, record the step index in flight in
+// ctl->step_cur and advance the device step counter.
+struct PhaseCtl {
+    MgCtl *ctl;
+    int reset;
+    double tolH0;
+    int max_iter;
+    long long *step;
 };
 
 struct ObsOut {
@@ -131,7 +144,7 @@ struct LbmArgs {
 
 template <typename T>
 void launch_phase(int mode, const Phys<T> &P, const void *g, T *phi1, T *phi2, T *k,
-                  cudaStream_t s);
+                  PhaseCtl pc, cudaStream_t s);
 template <typename T>
 void launch_collide(int mode, const LbmArgs<T> &a, cudaStream_t s);
 template <typename T>
@@ -161,18 +174,12 @@ MgHost<T> *mg_create(int nx, int ny, int pitch, T *k0, T *psiA, T *psiB, MgCtl *
 template <typename T>
 void mg_destroy(MgHost<T> *m);
 template <typename T>
-void mg_begin(MgHost<T> *m, double tolH0, int max_iter, cudaStream_t s);
-template <typename T>
 void mg_cycle(MgHost<T> *m, T H0c, T H0s, cudaGraphConditionalHandle h, int in_graph,
               cudaStream_t s);
 template <typename T>
 int mg_kernels_per_cycle(const MgHost<T> *m);
 template <typename T>
 int mg_levels(const MgHost<T> *m);
-template <typename T>
-int mg_pre_kernels(const MgHost<T> *m);  // kernels of mg_prepare + mg_begin
-template <typename T>
-void mg_prepare(MgHost<T> *m, cudaStream_t s);  // restrict k to the grid-wide coarse levels
 
 // observables
 size_t observe_scratch_doubles(int nx, int ny);

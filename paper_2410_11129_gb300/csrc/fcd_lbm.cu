@@ -23,8 +23,25 @@ struct StoreT<MODE_FP64> { using type = double; };
 // ---------------------------------------------------------------- phase
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256) phase_kernel(Phys<T> P, const void *gv, T *phi1, T *phi2,
-                                                    T *k) {
+                                                    T *k, PhaseCtl pc) {
     using S = typename StoreT<MODE>::type;
+    if (pc.ctl && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
+        MgCtl *c = pc.ctl;
+        if (pc.reset) {  // start of a potential solve
+            c->norm_bits = 0ull;
+            c->iter = 0;
+            c->done = 0;
+            c->converged = 0;
+            c->tolH0 = pc.tolH0;
+            c->max_iter = pc.max_iter;
+            c->keep_going = 1;
+            c->blocks_done = 0u;
+        }
+        if (pc.step) {
+            c->step_cur = *pc.step;
+            *pc.step += 1;
+        }
+    }
     const S *g = static_cast<const S *>(gv);
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -81,12 +98,32 @@ __global__ void __launch_bounds__(TX *TY) collide_kernel(LbmArgs<T> A) {
     const int nx = P.nx, ny = P.ny, pitch = P.pitch;
     const long long ps = P.ps;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    const bool live = x < nx && y < ny;
+    const long long n = (long long)y * pitch + x;
+
+    // FP32 forms: issue the 27 population loads first so that their latency
+    // overlaps the halo fill and the force evaluation (FP64 keeps them late:
+    // its register budget is already large).
+    constexpr bool EARLY = MODE != MODE_FP64;
+    const S *fs = static_cast<const S *>(A.f_src);
+    const S *gs = static_cast<const S *>(A.g_src);
+    S fpre[EARLY ? 9 : 1], gpre[EARLY ? 18 : 1];
+    if constexpr (EARLY) {
+        if (live) {
+#pragma unroll
+            for (int a = 0; a < 9; a++) fpre[a] = __ldg(fs + a * ps + n);
+#pragma unroll
+            for (int a = 0; a < 18; a++) gpre[a] = __ldg(gs + a * ps + n);
+        }
+    }
     const T *psi = A.ctl->cur ? A.psi1 : A.psi0;
 
     for (int i = threadIdx.y * TX + threadIdx.x; i < (TX + 2) * (TY + 2); i += TX * TY) {
         int lx = i % (TX + 2), ly = i / (TX + 2);
         int gx = x0 - 1 + lx;
-        gx = ((gx % nx) + nx) % nx;
+        if (gx < 0) gx += nx;
+        while (gx >= nx) gx -= nx;
         int gy = y0 - 1 + ly;
         bool ghost = gy < 0 || gy >= ny;
         int my = gy < 0 ? 0 : (gy >= ny ? ny - 1 : gy);
@@ -101,10 +138,8 @@ __global__ void __launch_bounds__(TX *TY) collide_kernel(LbmArgs<T> A) {
     }
     __syncthreads();
 
-    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
-    if (x >= nx || y >= ny) return;
+    if (!live) return;
     const int lx = threadIdx.x + 1, ly = threadIdx.y + 1;
-    const long long n = (long long)y * pitch + x;
 
     Stencil<T> st;
     st.load(s1, lx, ly);
@@ -153,10 +188,12 @@ __global__ void __launch_bounds__(TX *TY) collide_kernel(LbmArgs<T> A) {
     }
 
     // Populations.
-    const S *fs = static_cast<const S *>(A.f_src);
     T f[9];
 #pragma unroll
-    for (int a = 0; a < 9; a++) f[a] = T(fs[a * ps + n]) - f_off<MODE, T>(a);
+    for (int a = 0; a < 9; a++) {
+        if constexpr (EARLY) f[a] = T(fpre[a]) - f_off<MODE, T>(a);
+        else f[a] = T(fs[a * ps + n]) - f_off<MODE, T>(a);
+    }
     const T pst = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
     const T jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
     const T jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
@@ -255,7 +292,6 @@ __global__ void __launch_bounds__(TX *TY) collide_kernel(LbmArgs<T> A) {
         qx[1] = i2 * g2x - mx;
         qy[1] = i2 * g2y - my;
     }
-    const S *gs = static_cast<const S *>(A.g_src);
     S *gd = static_cast<S *>(A.g_dst);
 #pragma unroll
     for (int i = 0; i < 2; i++) {
@@ -267,7 +303,9 @@ __global__ void __launch_bounds__(TX *TY) collide_kernel(LbmArgs<T> A) {
             const T w = wgt<T>(a);
             const T eu = T(cx(a)) * ux + T(cy(a)) * uy;
             const T gam = w * (T(1) + T(3) * eu + T(4.5) * eu * eu - uu);
-            const T gv = T(gs[(i * 9 + a) * ps + n]) - g_off<MODE, T>(a);
+            T gv;
+            if constexpr (EARLY) gv = T(gpre[i * 9 + a]) - g_off<MODE, T>(a);
+            else gv = T(gs[(i * 9 + a) * ps + n]) - g_off<MODE, T>(a);
             const T v = P.keep_phi * gv + ophi * gam + w * (T(cx(a)) * sqx + T(cy(a)) * sqy);
             int xn = x + cx(a);
             xn = xn < 0 ? nx - 1 : (xn >= nx ? 0 : xn);
@@ -401,9 +439,9 @@ static dim3 grid2(int nx, int ny, dim3 b) { return dim3((nx + b.x - 1) / b.x, (n
 
 template <typename T>
 void launch_phase(int mode, const Phys<T> &P, const void *g, T *phi1, T *phi2, T *k,
-                  cudaStream_t s) {
+                  PhaseCtl pc, cudaStream_t s) {
     dim3 b(32, 8), gr = grid2(P.nx, P.ny, b);
-    FCD_MODE_SWITCH(mode, T, (phase_kernel<T, M><<<gr, b, 0, s>>>(P, g, phi1, phi2, k)));
+    FCD_MODE_SWITCH(mode, T, (phase_kernel<T, M><<<gr, b, 0, s>>>(P, g, phi1, phi2, k, pc)));
 }
 
 template <typename T>
@@ -455,7 +493,7 @@ void launch_phi3_to_f64(const T *p1, const T *p2, int nx, int ny, int pitch, dou
 
 #define FCD_INST(T)                                                                           \
     template void launch_phase<T>(int, const Phys<T> &, const void *, T *, T *, T *,          \
-                                  cudaStream_t);                                              \
+                                  PhaseCtl, cudaStream_t);                                    \
     template void launch_collide<T>(int, const LbmArgs<T> &, cudaStream_t);                    \
     template void launch_init<T>(int, const Phys<T> &, double, double, double, double, double, \
                                  double, void *, void *, T *, cudaStream_t);                   \

@@ -35,7 +35,8 @@ namespace fcd {
 
 constexpr int SX = 32, SY = 8;     // level-0 smoothing tile
 constexpr int CTA_THREADS = 1024;
-constexpr int NU_PRE = 2, NU_POST = 2, NU_FINE = 2, NU_COARSEST = 24;
+constexpr int NU_PRE = 2, NU_POST = 2, NU_FINE = 2, NU_COARSEST = 30;
+constexpr size_t CTA_SMEM_MAX = 200 * 1024;  // shared memory of the single-block levels
 
 __device__ __forceinline__ double norm_of(const MgCtl *c) {
     return __longlong_as_double((long long)c->norm_bits);
@@ -106,8 +107,9 @@ __device__ __forceinline__ T interp_coarse(const Level<T> &F, const Level<T> &C,
     return (T(1) - wy) * a + wy * b;
 }
 
-// Residual of level 0 on the children of each level-1 cell, summed onto it;
-// the max-norm over the lattice goes to the control block. Also clears e_1.
+// Residual of level 0 on the children of each level-1 cell, summed onto it,
+// and the level-1 permeability (mean of the children); the max-norm over the
+// lattice goes to the control block.
 template <typename T>
 __global__ void __launch_bounds__(256) resid0_restrict(Level<T> L0, Level<T> L1, T H0c, T H0s,
                                                        MgCtl *ctl) {
@@ -118,7 +120,7 @@ __global__ void __launch_bounds__(256) resid0_restrict(Level<T> L0, Level<T> L1,
     if (I < L1.nx && J < L1.ny) {
         const T *psi = ctl->cur ? L0.r : L0.e;
         const int nx = L0.nx, ny = L0.ny, pitch = L0.pitch;
-        T sum = T(0);
+        T sum = T(0), ksum = T(0);
         for (int j = L1.cy0[J]; j < L1.cy0[J + 1]; j++) {
             for (int i = L1.cx0[I]; i < L1.cx0[I + 1]; i++) {
                 auto kat = [&](int dx, int dy) {
@@ -137,22 +139,31 @@ __global__ void __launch_bounds__(256) resid0_restrict(Level<T> L0, Level<T> L1,
                 const T p0 = psi[(long long)j * pitch + i];
                 const T r = nd.b - (off9<T>(nd, pat, j, ny) - nd.diag * p0);
                 sum += r;
+                ksum += kat(0, 0);
                 const double ar = fabs((double)r);
                 mx = ar <= mx ? mx : (ar == ar ? ar : INFINITY);  // NaN counts as infinite
             }
         }
         L1.b[(long long)J * L1.pitch + I] = sum;
-        L1.e[(long long)J * L1.pitch + I] = T(0);
+        L1.k[(long long)J * L1.pitch + I] = ksum / (L1.wx[I] * L1.wy[J]);  // unit lattice cells
     }
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0 && mx > 0.0) atomic_max_nonneg(&ctl->norm_bits, mx);
 }
 
-// Level-0 block Gauss-Seidel (optionally after adding the coarse correction).
+__device__ void cycle_end_logic(MgCtl *ctl, cudaGraphConditionalHandle h, int in_graph);
+
+// Level-0 block Gauss-Seidel after adding the coarse correction; the last
+// block to finish closes the cycle (loop condition of the graph while node).
 template <typename T>
 __global__ void __launch_bounds__(SX *SY) smooth0(Level<T> L0, Level<T> L1, int add_coarse,
-                                                  int sweeps, T H0c, T H0s, MgCtl *ctl) {
-    if (cycle_skip(ctl)) return;
+                                                  int sweeps, T H0c, T H0s, MgCtl *ctl,
+                                                  cudaGraphConditionalHandle h, int in_graph) {
+    const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
+    if (cycle_skip(ctl)) {
+        if (lead && blockIdx.x == 0 && blockIdx.y == 0) cycle_end_logic(ctl, h, in_graph);
+        return;
+    }
     __shared__ T sp[SY + 2][SX + 2];
     __shared__ T sk[SY + 2][SX + 2];
     const int nx = L0.nx, ny = L0.ny, pitch = L0.pitch;
@@ -191,6 +202,16 @@ __global__ void __launch_bounds__(SX *SY) smooth0(Level<T> L0, Level<T> L1, int 
         }
     }
     if (own) dst[(long long)y * pitch + x] = sp[ly][lx];
+    __syncthreads();
+    if (lead) {
+        __threadfence();
+        const unsigned total = gridDim.x * gridDim.y;
+        if (atomicAdd(&ctl->blocks_done, 1u) == total - 1) {
+            __threadfence();
+            ctl->blocks_done = 0;
+            cycle_end_logic(ctl, h, in_graph);
+        }
+    }
 }
 
 // ------------------------------------------------------------- coarse levels
@@ -201,110 +222,149 @@ struct FV {
     bool hasn, hass;      // neighbour inside (false: wall with value 0)
 };
 
-template <typename T>
-__device__ __forceinline__ FV<T> fv_coef(const Level<T> &L, int I, int J) {
+template <typename T, typename KF>
+__device__ __forceinline__ FV<T> fv_coef(const Level<T> &L, int I, int J, KF kat) {
     FV<T> f;
-    const int nx = L.nx, ny = L.ny, p = L.pitch;
-    const T k0 = L.k[(long long)J * p + I];
+    const int nx = L.nx, ny = L.ny;
+    const T k0 = kat(0, 0);
     f.ie = I + 1 == nx ? 0 : I + 1;
     f.iw = I == 0 ? nx - 1 : I - 1;
     const T dxe = I + 1 == nx ? L.xc[0] + L.Lx - L.xc[I] : L.xc[I + 1] - L.xc[I];
     const T dxw = I == 0 ? L.xc[0] + L.Lx - L.xc[nx - 1] : L.xc[I] - L.xc[I - 1];
-    f.te = T(0.5) * (k0 + L.k[(long long)J * p + f.ie]) * L.wy[J] / dxe;
-    f.tw = T(0.5) * (k0 + L.k[(long long)J * p + f.iw]) * L.wy[J] / dxw;
+    f.te = T(0.5) * (k0 + kat(1, 0)) * L.wy[J] / dxe;
+    f.tw = T(0.5) * (k0 + kat(-1, 0)) * L.wy[J] / dxw;
     f.hasn = J + 1 < ny;
     f.hass = J > 0;
-    f.tn = f.hasn ? T(0.5) * (k0 + L.k[(long long)(J + 1) * p + I]) * L.wx[I] / (L.yc[J + 1] - L.yc[J])
+    f.tn = f.hasn ? T(0.5) * (k0 + kat(0, 1)) * L.wx[I] / (L.yc[J + 1] - L.yc[J])
                   : k0 * L.wx[I] / (L.yhi - L.yc[J]);
-    f.ts = f.hass ? T(0.5) * (k0 + L.k[(long long)(J - 1) * p + I]) * L.wx[I] / (L.yc[J] - L.yc[J - 1])
+    f.ts = f.hass ? T(0.5) * (k0 + kat(0, -1)) * L.wx[I] / (L.yc[J] - L.yc[J - 1])
                   : k0 * L.wx[I] / (L.yc[J] - L.ylo);
     return f;
-}
-
-template <typename T>
-__device__ __forceinline__ T fv_nb(const Level<T> &L, const FV<T> &f, int I, int J) {
-    const int p = L.pitch;
-    T s = f.te * L.e[(long long)J * p + f.ie] + f.tw * L.e[(long long)J * p + f.iw];
-    if (f.hasn) s += f.tn * L.e[(long long)(J + 1) * p + I];
-    if (f.hass) s += f.ts * L.e[(long long)(J - 1) * p + I];
-    return s;
 }
 
 __device__ __forceinline__ int fv_colour(int I, int J, int nx) {
     return ((nx & 1) && I == nx - 1) ? 2 + (J & 1) : ((I + J) & 1);
 }
 
+// Residual b - A e of a coarse level held in global memory (e given).
 template <typename T>
-__device__ __forceinline__ void fv_gs_cell(const Level<T> &L, int I, int J) {
-    const FV<T> f = fv_coef(L, I, J);
-    const T d = f.te + f.tw + f.tn + f.ts;
-    L.e[(long long)J * L.pitch + I] = (fv_nb(L, f, I, J) - L.b[(long long)J * L.pitch + I]) / d;
+__device__ __forceinline__ T fv_resid_global(const Level<T> &L, const T *e, int I, int J) {
+    const int p = L.pitch, ny = L.ny;
+    auto kat = [&](int dx, int dy) {
+        int ii = I + dx;
+        ii = ii < 0 ? L.nx - 1 : (ii >= L.nx ? 0 : ii);
+        return L.k[(long long)(J + dy) * p + ii];
+    };
+    const FV<T> f = fv_coef(L, I, J, kat);
+    const T e0 = e[(long long)J * p + I];
+    T s = f.te * e[(long long)J * p + f.ie] + f.tw * e[(long long)J * p + f.iw];
+    if (f.hasn) s += f.tn * e[(long long)(J + 1) * p + I];
+    if (f.hass) s += f.ts * e[(long long)(J - 1) * p + I];
+    (void)ny;
+    return L.b[(long long)J * p + I] - (s - (f.te + f.tw + f.tn + f.ts) * e0);
 }
 
-template <typename T>
-__device__ __forceinline__ T fv_resid(const Level<T> &L, int I, int J) {
-    const FV<T> f = fv_coef(L, I, J);
-    const T d = f.te + f.tw + f.tn + f.ts;
-    const T e0 = L.e[(long long)J * L.pitch + I];
-    return L.b[(long long)J * L.pitch + I] - (fv_nb(L, f, I, J) - d * e0);
-}
-
-template <typename T>
-__device__ __forceinline__ void k_restrict_cell(const Level<T> &C, const Level<T> &F, int I, int J) {
-    T s = T(0);
-    for (int j = C.cy0[J]; j < C.cy0[J + 1]; j++)
-        for (int i = C.cx0[I]; i < C.cx0[I + 1]; i++)
-            s += F.k[(long long)j * F.pitch + i] * F.wx[i] * F.wy[j];
-    C.k[(long long)J * C.pitch + I] = s / (C.wx[I] * C.wy[J]);
-}
-
-template <typename T>
-__device__ __forceinline__ void resid_restrict_cell(const Level<T> &F, const Level<T> &C, int I, int J) {
-    T s = T(0);
-    for (int j = C.cy0[J]; j < C.cy0[J + 1]; j++)
-        for (int i = C.cx0[I]; i < C.cx0[I + 1]; i++) s += fv_resid(F, i, j);
-    C.b[(long long)J * C.pitch + I] = s;
-    C.e[(long long)J * C.pitch + I] = T(0);
-}
-
-template <typename T>
-__global__ void k_restrict(Level<T> C, Level<T> F) {
-    const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y;
-    if (I < C.nx && J < C.ny) k_restrict_cell(C, F, I, J);
-}
-
-template <typename T>
-__global__ void fv_smooth_colour(Level<T> L, int colour, MgCtl *ctl) {
+// Tiled block Gauss-Seidel on a grid-wide coarse level. PRE: zero initial
+// guess, output to L.r. POST: L.r plus the coarse correction, output to L.e.
+template <typename T, bool POST>
+__global__ void __launch_bounds__(SX *SY) fv_smooth(Level<T> L, Level<T> C, int sweeps,
+                                                    MgCtl *ctl) {
     if (cycle_skip(ctl)) return;
-    const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y;
-    if (I < L.nx && J < L.ny && fv_colour(I, J, L.nx) == colour) fv_gs_cell(L, I, J);
-}
-
-template <typename T>
-__global__ void fv_resid_restrict(Level<T> F, Level<T> C, MgCtl *ctl) {
-    if (cycle_skip(ctl)) return;
-    const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y;
-    if (I < C.nx && J < C.ny) resid_restrict_cell(F, C, I, J);
-}
-
-template <typename T>
-__global__ void fv_prolong(Level<T> F, Level<T> C, MgCtl *ctl) {
-    if (cycle_skip(ctl)) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i < F.nx && j < F.ny) F.e[(long long)j * F.pitch + i] += interp_coarse(F, C, i, j);
-}
-
-// Levels lc .. nl-1 inside one block.
-template <typename T>
-__device__ void cta_smooth(const Level<T> &L, int sweeps) {
-    const int n = L.nx * L.ny, ncol = (L.nx & 1) ? 4 : 2;
+    __shared__ T se[SY + 2][SX + 2];
+    __shared__ T sk[SY + 2][SX + 2];
+    const int nx = L.nx, ny = L.ny, p = L.pitch;
+    const int x0 = blockIdx.x * SX, y0 = blockIdx.y * SY;
+    for (int t = threadIdx.y * SX + threadIdx.x; t < (SX + 2) * (SY + 2); t += SX * SY) {
+        const int lx = t % (SX + 2), ly = t / (SX + 2);
+        int gx = x0 - 1 + lx;
+        gx = ((gx % nx) + nx) % nx;
+        const int gy = y0 - 1 + ly;
+        T kv = T(0), ev = T(0);
+        if (gy >= 0 && gy < ny) {
+            kv = L.k[(long long)gy * p + gx];
+            if (POST) ev = L.r[(long long)gy * p + gx] + interp_coarse(L, C, gx, gy);
+        }
+        sk[ly][lx] = kv;
+        se[ly][lx] = ev;
+    }
+    __syncthreads();
+    const int lx = threadIdx.x + 1, ly = threadIdx.y + 1;
+    const int I = x0 + threadIdx.x, J = y0 + threadIdx.y;
+    const bool own = I < nx && J < ny;
+    FV<T> f;
+    T dg = T(1), b = T(0);
+    if (own) {
+        auto kat = [&](int dx, int dy) { return sk[ly + dy][lx + dx]; };
+        f = fv_coef(L, I, J, kat);
+        dg = f.te + f.tw + f.tn + f.ts;
+        b = L.b[(long long)J * p + I];
+    }
+    const int colour = own ? fv_colour(I, J, nx) : -1;
+    const int ncol = (nx & 1) ? 4 : 2;
     for (int s = 0; s < sweeps; s++)
         for (int c = 0; c < ncol; c++) {
-            for (int t = threadIdx.x; t < n; t += blockDim.x) {
-                const int I = t % L.nx, J = t / L.nx;
-                if (fv_colour(I, J, L.nx) == c) fv_gs_cell(L, I, J);
+            if (colour == c) {
+                T v = f.te * se[ly][lx + 1] + f.tw * se[ly][lx - 1];
+                if (f.hasn) v += f.tn * se[ly + 1][lx];
+                if (f.hass) v += f.ts * se[ly - 1][lx];
+                se[ly][lx] = (v - b) / dg;
             }
             __syncthreads();
+        }
+    if (own) (POST ? L.e : L.r)[(long long)J * p + I] = se[ly][lx];
+}
+
+// Residual of a grid-wide level (pre-smoothed iterate in F.r) summed onto the
+// next level, and the next level's permeability (area-weighted mean).
+template <typename T>
+__global__ void __launch_bounds__(256) fv_resid_restrict(Level<T> F, Level<T> C, MgCtl *ctl) {
+    if (cycle_skip(ctl)) return;
+    const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y;
+    if (I >= C.nx || J >= C.ny) return;
+    T sr = T(0), sk = T(0);
+    for (int j = C.cy0[J]; j < C.cy0[J + 1]; j++)
+        for (int i = C.cx0[I]; i < C.cx0[I + 1]; i++) {
+            sr += fv_resid_global(F, F.r, i, j);
+            sk += F.k[(long long)j * F.pitch + i] * F.wx[i] * F.wy[j];
+        }
+    C.b[(long long)J * C.pitch + I] = sr;
+    C.k[(long long)J * C.pitch + I] = sk / (C.wx[I] * C.wy[J]);
+}
+
+// ---- levels lc .. nl-1 inside one block, resident in shared memory.
+// Per level: e, b, k, te (east face), tn (north face, wall at the top), dg.
+constexpr int MAX_LEVELS = 24;
+constexpr int CTA_ARRAYS = 6;
+
+template <typename T>
+struct CtaView {
+    T *e, *b, *k, *te, *tn, *dg;
+};
+
+template <typename T>
+__device__ __forceinline__ CtaView<T> cta_view(T *sm, const int *off, const Level<T> *L, int l) {
+    const int n = L[l].nx * L[l].ny;
+    T *base = sm + off[l];
+    return CtaView<T>{base, base + n, base + 2 * n, base + 3 * n, base + 4 * n, base + 5 * n};
+}
+
+template <typename T>
+__device__ __forceinline__ void cta_gs(const Level<T> &L, const CtaView<T> &V, int sweeps,
+                                       int tid, int nthr, bool warp_only) {
+    const int nx = L.nx, ny = L.ny, n = nx * ny, ncol = (nx & 1) ? 4 : 2;
+    for (int s = 0; s < sweeps; s++)
+        for (int c = 0; c < ncol; c++) {
+            for (int t = tid; t < n; t += nthr) {
+                const int I = t % nx, J = t / nx;
+                if (fv_colour(I, J, nx) != c) continue;
+                const int iw = I == 0 ? nx - 1 : I - 1, ie = I + 1 == nx ? 0 : I + 1;
+                T v = V.te[t] * V.e[J * nx + ie] + V.te[J * nx + iw] * V.e[J * nx + iw];
+                if (J + 1 < ny) v += V.tn[t] * V.e[t + nx];
+                if (J > 0) v += V.tn[t - nx] * V.e[t - nx];
+                V.e[t] = (v - V.b[t]) / V.dg[t];
+            }
+            if (warp_only) __syncwarp();
+            else __syncthreads();
         }
 }
 
@@ -312,45 +372,117 @@ template <typename T>
 __global__ void __launch_bounds__(CTA_THREADS) coarse_cta(const Level<T> *lv, int lc, int nl,
                                                          MgCtl *ctl) {
     if (cycle_skip(ctl)) return;
-    for (int l = lc; l < nl - 1; l++) {
-        const Level<T> F = lv[l], C = lv[l + 1];
-        cta_smooth(F, NU_PRE);
-        for (int t = threadIdx.x; t < C.nx * C.ny; t += blockDim.x)
-            resid_restrict_cell(F, C, t % C.nx, t / C.nx);
-        __syncthreads();
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ Level<T> L[MAX_LEVELS];
+    __shared__ int off[MAX_LEVELS];
+    T *sm = reinterpret_cast<T *>(smraw);
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    if (tid < nl) L[tid] = lv[tid];
+    __syncthreads();
+    if (tid == 0) {
+        int o = 0;
+        for (int l = lc; l < nl; l++) { off[l] = o; o += CTA_ARRAYS * L[l].nx * L[l].ny; }
     }
-    cta_smooth(lv[nl - 1], NU_COARSEST);
-    for (int l = nl - 2; l >= lc; l--) {
-        const Level<T> F = lv[l], C = lv[l + 1];
-        for (int t = threadIdx.x; t < F.nx * F.ny; t += blockDim.x) {
-            const int i = t % F.nx, j = t / F.nx;
-            F.e[(long long)j * F.pitch + i] += interp_coarse(F, C, i, j);
+    __syncthreads();
+    // inputs of level lc; permeabilities of the deeper levels
+    {
+        const CtaView<T> V = cta_view(sm, off, L, lc);
+        const int nx = L[lc].nx, n = nx * L[lc].ny;
+        for (int t = tid; t < n; t += nthr) {
+            const long long g = (long long)(t / nx) * L[lc].pitch + t % nx;
+            V.b[t] = L[lc].b[g];
+            V.k[t] = L[lc].k[g];
+            V.e[t] = T(0);
         }
         __syncthreads();
-        cta_smooth(F, NU_POST);
     }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(CTA_THREADS) k_restrict_cta(const Level<T> *lv, int lc, int nl) {
-    for (int l = lc; l < nl; l++) {
-        const Level<T> C = lv[l], F = lv[l - 1];
-        for (int t = threadIdx.x; t < C.nx * C.ny; t += blockDim.x) k_restrict_cell(C, F, t % C.nx, t / C.nx);
+    for (int l = lc + 1; l < nl; l++) {
+        const CtaView<T> F = cta_view(sm, off, L, l - 1), V = cta_view(sm, off, L, l);
+        const Level<T> &C = L[l], &Fl = L[l - 1];
+        for (int t = tid; t < C.nx * C.ny; t += nthr) {
+            const int I = t % C.nx, J = t / C.nx;
+            T s = T(0);
+            for (int j = C.cy0[J]; j < C.cy0[J + 1]; j++)
+                for (int i = C.cx0[I]; i < C.cx0[I + 1]; i++) s += F.k[j * Fl.nx + i] * Fl.wx[i] * Fl.wy[j];
+            V.k[t] = s / (C.wx[I] * C.wy[J]);
+        }
         __syncthreads();
     }
+    for (int l = lc; l < nl; l++) {  // face coefficients and diagonals
+        const CtaView<T> V = cta_view(sm, off, L, l);
+        const Level<T> &C = L[l];
+        const int nx = C.nx;
+        for (int t = tid; t < nx * C.ny; t += nthr) {
+            const int I = t % nx, J = t / nx;
+            auto kat = [&](int dx, int dy) {
+                int ii = I + dx;
+                ii = ii < 0 ? nx - 1 : (ii >= nx ? 0 : ii);
+                return V.k[(J + dy) * nx + ii];
+            };
+            const FV<T> f = fv_coef(C, I, J, kat);
+            V.te[t] = f.te;
+            V.tn[t] = f.tn;
+            V.dg[t] = f.te + f.tw + f.tn + f.ts;
+        }
+    }
+    __syncthreads();
+    // V-cycle: down
+    for (int l = lc; l < nl - 1; l++) {
+        const CtaView<T> F = cta_view(sm, off, L, l), V = cta_view(sm, off, L, l + 1);
+        cta_gs(L[l], F, NU_PRE, tid, nthr, false);
+        const Level<T> &C = L[l + 1];
+        const int fnx = L[l].nx, fny = L[l].ny;
+        for (int t = tid; t < C.nx * C.ny; t += nthr) {
+            const int I = t % C.nx, J = t / C.nx;
+            T s = T(0);
+            for (int j = C.cy0[J]; j < C.cy0[J + 1]; j++)
+                for (int i = C.cx0[I]; i < C.cx0[I + 1]; i++) {
+                    const int q = j * fnx + i;
+                    const int iw = i == 0 ? fnx - 1 : i - 1, ie = i + 1 == fnx ? 0 : i + 1;
+                    T v = F.te[q] * F.e[j * fnx + ie] + F.te[j * fnx + iw] * F.e[j * fnx + iw];
+                    if (j + 1 < fny) v += F.tn[q] * F.e[q + fnx];
+                    if (j > 0) v += F.tn[q - fnx] * F.e[q - fnx];
+                    s += F.b[q] - (v - F.dg[q] * F.e[q]);
+                }
+            V.b[t] = s;
+            V.e[t] = T(0);
+        }
+        __syncthreads();
+    }
+    {  // coarsest: one warp when it is small
+        const CtaView<T> V = cta_view(sm, off, L, nl - 1);
+        const bool small = L[nl - 1].nx * L[nl - 1].ny <= 64;
+        if (!small) cta_gs(L[nl - 1], V, NU_COARSEST, tid, nthr, false);
+        else if (tid < 32) cta_gs(L[nl - 1], V, NU_COARSEST, tid, 32, true);
+        __syncthreads();
+    }
+    // up
+    for (int l = nl - 2; l >= lc; l--) {
+        const CtaView<T> F = cta_view(sm, off, L, l), V = cta_view(sm, off, L, l + 1);
+        const Level<T> &Fl = L[l];
+        for (int t = tid; t < Fl.nx * Fl.ny; t += nthr) {
+            const int i = t % Fl.nx, j = t / Fl.nx;
+            const int x0 = Fl.px0[i], x1 = Fl.px1[i], y0 = Fl.py0[j], y1 = Fl.py1[j];
+            const T wx = Fl.pwx[i], wy = Fl.pwy[j];
+            const int cnx = L[l + 1].nx;
+            T a = T(0), b = T(0);
+            if (y0 >= 0) a = (T(1) - wx) * V.e[y0 * cnx + x0] + wx * V.e[y0 * cnx + x1];
+            if (y1 >= 0) b = (T(1) - wx) * V.e[y1 * cnx + x0] + wx * V.e[y1 * cnx + x1];
+            F.e[t] += (T(1) - wy) * a + wy * b;
+        }
+        __syncthreads();
+        cta_gs(L[l], F, NU_POST, tid, nthr, false);
+    }
+    {
+        const CtaView<T> V = cta_view(sm, off, L, lc);
+        const int nx = L[lc].nx, n = nx * L[lc].ny;
+        for (int t = tid; t < n; t += nthr) L[lc].e[(long long)(t / nx) * L[lc].pitch + t % nx] = V.e[t];
+    }
 }
 
-__global__ void mg_begin_kernel(MgCtl *ctl, double tolH0, int max_iter) {
-    ctl->norm_bits = 0ull;
-    ctl->iter = 0;
-    ctl->done = 0;
-    ctl->converged = 0;
-    ctl->tolH0 = tolH0;
-    ctl->max_iter = max_iter;
-    ctl->keep_going = 1;
-}
-
-__global__ void mg_cycle_end(MgCtl *ctl, cudaGraphConditionalHandle h, int in_graph) {
+// End of a cycle (one thread): converged or capped -> stop the loop, else
+// count the cycle, flip the level-0 buffer and clear the norm.
+__device__ void cycle_end_logic(MgCtl *ctl, cudaGraphConditionalHandle h, int in_graph) {
     ctl->cycles_launched++;
     if (!ctl->done) {
         const double nrm = norm_of(ctl);
@@ -382,7 +514,7 @@ struct MgHost {
     void *(*alloc)(size_t, void *) = nullptr;
     void (*release)(void *, void *) = nullptr;
     void *user = nullptr;
-    int ncolours_sum = 0;  // grid-wide coarse colour launches per cycle
+    size_t cta_smem = 0;
 };
 
 static std::vector<int> merge_faces(int n) {
@@ -475,13 +607,27 @@ MgHost<T> *mg_create(int nx, int ny, int pitch, T *k0, T *psiA, T *psiB, MgCtl *
         for (size_t i = 0; i + 1 < fx[l].size(); i++) xcs[l].push_back(0.5 * (fx[l][i] + fx[l][i + 1]));
         for (size_t j = 0; j + 1 < fy[l].size(); j++) ycs[l].push_back(0.5 * (fy[l][j] + fy[l][j + 1]));
     }
-    // first level small enough for the single-block kernel
-    const long long cta_cells = 4096;
-    m->lc = m->nl;
+    // levels lc..nl-1 run in one block with their arrays in shared memory:
+    // the first level from which the rest fits the budget
+    m->lc = m->nl - 1;
     for (int l = 1; l < m->nl; l++) {
-        if ((long long)xcs[l].size() * ycs[l].size() <= cta_cells) { m->lc = l; break; }
+        size_t bytes = 0;
+        for (int q = l; q < m->nl; q++) bytes += (size_t)CTA_ARRAYS * xcs[q].size() * ycs[q].size() * sizeof(T);
+        if (bytes <= CTA_SMEM_MAX) { m->lc = l; break; }
     }
-    if (m->lc >= m->nl) m->lc = m->nl - 1;  // the coarsest level always runs in the block
+    m->cta_smem = 0;
+    for (int q = m->lc; q < m->nl; q++) m->cta_smem += (size_t)CTA_ARRAYS * xcs[q].size() * ycs[q].size() * sizeof(T);
+    if (m->nl > MAX_LEVELS || m->cta_smem > CTA_SMEM_MAX) {
+        snprintf(err, errlen, "multigrid: hierarchy too deep or coarse levels too large");
+        mg_destroy(m);
+        return nullptr;
+    }
+    if (cudaFuncSetAttribute(coarse_cta<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)m->cta_smem) != cudaSuccess) {
+        snprintf(err, errlen, "multigrid: cannot reserve %zu bytes of shared memory", m->cta_smem);
+        mg_destroy(m);
+        return nullptr;
+    }
     for (int l = 0; l < m->nl; l++) {
         Level<T> &L = m->lv[l];
         std::memset(&L, 0, sizeof(L));
@@ -499,6 +645,7 @@ MgHost<T> *mg_create(int nx, int ny, int pitch, T *k0, T *psiA, T *psiB, MgCtl *
             L.pitch = L.nx;
             size_t cells = (size_t)L.nx * L.ny;
             L.e = up.put<T>(nullptr, cells * sizeof(T));
+            L.r = up.put<T>(nullptr, cells * sizeof(T));
             L.b = up.put<T>(nullptr, cells * sizeof(T));
             L.k = up.put<T>(nullptr, cells * sizeof(T));
             L.cx0 = up.put<int>(cx0[l].data(), cx0[l].size() * sizeof(int));
@@ -525,7 +672,6 @@ MgHost<T> *mg_create(int nx, int ny, int pitch, T *k0, T *psiA, T *psiB, MgCtl *
         }
     }
     m->d_lv = up.put<Level<T>>(m->lv.data(), m->lv.size() * sizeof(Level<T>));
-    for (int l = 1; l < m->lc; l++) m->ncolours_sum += (m->lv[l].nx & 1) ? 4 : 2;
     if (!up.ok) {
         snprintf(err, errlen, "multigrid: device allocation or upload failed");
         mg_destroy(m);
@@ -544,70 +690,36 @@ void mg_destroy(MgHost<T> *m) {
 static dim3 g2(int nx, int ny, dim3 b) { return dim3((nx + b.x - 1) / b.x, (ny + b.y - 1) / b.y); }
 
 template <typename T>
-void mg_prepare(MgHost<T> *m, cudaStream_t s) {
-    dim3 b(32, 8);
-    for (int l = 1; l < m->lc; l++)
-        k_restrict<T><<<g2(m->lv[l].nx, m->lv[l].ny, b), b, 0, s>>>(m->lv[l], m->lv[l - 1]);
-    if (m->lc < m->nl) k_restrict_cta<T><<<1, CTA_THREADS, 0, s>>>(m->d_lv, m->lc, m->nl);
-}
-
-template <typename T>
-void mg_begin(MgHost<T> *m, double tolH0, int max_iter, cudaStream_t s) {
-    mg_begin_kernel<<<1, 1, 0, s>>>(m->ctl, tolH0, max_iter);
-}
-
-template <typename T>
 void mg_cycle(MgHost<T> *m, T H0c, T H0s, cudaGraphConditionalHandle h, int in_graph,
               cudaStream_t s) {
-    dim3 b(32, 8);
+    dim3 b(32, 8), bs(SX, SY);
     const std::vector<Level<T>> &lv = m->lv;
     resid0_restrict<T><<<g2(lv[1].nx, lv[1].ny, b), b, 0, s>>>(lv[0], lv[1], H0c, H0s, m->ctl);
     for (int l = 1; l < m->lc; l++) {
-        const int nc = (lv[l].nx & 1) ? 4 : 2;
-        for (int sw = 0; sw < NU_PRE; sw++)
-            for (int c = 0; c < nc; c++)
-                fv_smooth_colour<T><<<g2(lv[l].nx, lv[l].ny, b), b, 0, s>>>(lv[l], c, m->ctl);
+        fv_smooth<T, false><<<g2(lv[l].nx, lv[l].ny, bs), bs, 0, s>>>(lv[l], lv[l + 1], NU_PRE, m->ctl);
         fv_resid_restrict<T><<<g2(lv[l + 1].nx, lv[l + 1].ny, b), b, 0, s>>>(lv[l], lv[l + 1], m->ctl);
     }
-    coarse_cta<T><<<1, CTA_THREADS, 0, s>>>(m->d_lv, m->lc, m->nl, m->ctl);
-    for (int l = m->lc - 1; l >= 1; l--) {
-        const int nc = (lv[l].nx & 1) ? 4 : 2;
-        fv_prolong<T><<<g2(lv[l].nx, lv[l].ny, b), b, 0, s>>>(lv[l], lv[l + 1], m->ctl);
-        for (int sw = 0; sw < NU_POST; sw++)
-            for (int c = 0; c < nc; c++)
-                fv_smooth_colour<T><<<g2(lv[l].nx, lv[l].ny, b), b, 0, s>>>(lv[l], c, m->ctl);
-    }
-    dim3 bs(SX, SY);
-    smooth0<T><<<g2(lv[0].nx, lv[0].ny, bs), bs, 0, s>>>(lv[0], lv[1], 1, NU_FINE, H0c, H0s, m->ctl);
-    mg_cycle_end<<<1, 1, 0, s>>>(m->ctl, h, in_graph);
+    coarse_cta<T><<<1, CTA_THREADS, m->cta_smem, s>>>(m->d_lv, m->lc, m->nl, m->ctl);
+    for (int l = m->lc - 1; l >= 1; l--)
+        fv_smooth<T, true><<<g2(lv[l].nx, lv[l].ny, bs), bs, 0, s>>>(lv[l], lv[l + 1], NU_POST, m->ctl);
+    smooth0<T><<<g2(lv[0].nx, lv[0].ny, bs), bs, 0, s>>>(lv[0], lv[1], 1, NU_FINE, H0c, H0s, m->ctl,
+                                                          h, in_graph);
 }
 
 template <typename T>
-int mg_kernels_per_cycle(const MgHost<T> *m) {
-    int n = 4;  // resid0_restrict, coarse_cta, smooth0, cycle_end
-    for (int l = 1; l < m->lc; l++) n += 2 + ((m->lv[l].nx & 1) ? 4 : 2) * (NU_PRE + NU_POST);
-    return n;
-}
+int mg_kernels_per_cycle(const MgHost<T> *m) { return 3 + 3 * (m->lc - 1); }
 
 template <typename T>
 int mg_levels(const MgHost<T> *m) { return m->nl; }
-
-template <typename T>
-int mg_pre_kernels(const MgHost<T> *m) {
-    return (m->lc - 1) + (m->lc < m->nl ? 1 : 0) + 1;
-}
 
 #define FCD_MG_INST(T)                                                                          \
     template MgHost<T> *mg_create<T>(int, int, int, T *, T *, T *, MgCtl *,                     \
                                      void *(*)(size_t, void *), void (*)(void *, void *), void *, \
                                      char *, size_t);                                           \
     template void mg_destroy<T>(MgHost<T> *);                                                   \
-    template void mg_prepare<T>(MgHost<T> *, cudaStream_t);                                     \
-    template void mg_begin<T>(MgHost<T> *, double, int, cudaStream_t);                          \
     template void mg_cycle<T>(MgHost<T> *, T, T, cudaGraphConditionalHandle, int, cudaStream_t); \
     template int mg_kernels_per_cycle<T>(const MgHost<T> *);                                    \
-    template int mg_levels<T>(const MgHost<T> *);                                               \
-    template int mg_pre_kernels<T>(const MgHost<T> *);
+    template int mg_levels<T>(const MgHost<T> *);
 FCD_MG_INST(float)
 FCD_MG_INST(double)
 
