@@ -191,7 +191,7 @@ struct Engine : fcd_ctx {
     void *f[2] = {nullptr, nullptr}, *g[2] = {nullptr, nullptr};
     int cur = 0;
     T *phi1 = nullptr, *phi2 = nullptr, *k = nullptr, *psiA = nullptr, *psiB = nullptr,
-      *macro = nullptr;
+      *psiP = nullptr, *macro = nullptr;
     MgCtl *ctl = nullptr;
     MgHost<T> *mg = nullptr;
     unsigned long long *brk = nullptr;
@@ -252,6 +252,7 @@ struct Engine : fcd_ctx {
         k = dalloc(ps * sizeof(T));
         psiA = dalloc(ps * sizeof(T));
         psiB = dalloc(ps * sizeof(T));
+        psiP = dalloc(ps * sizeof(T));
         macro = dalloc(3 * ps * sizeof(T));
         ctl = reinterpret_cast<MgCtl *>(dalloc(sizeof(MgCtl)));
         brk = reinterpret_cast<unsigned long long *>(dalloc(sizeof(unsigned long long)));
@@ -259,7 +260,7 @@ struct Engine : fcd_ctx {
         obs_scratch = reinterpret_cast<double *>(dalloc(observe_scratch_doubles(prm.nx, prm.ny) * sizeof(double)));
         obs_out = reinterpret_cast<ObsOut *>(dalloc(sizeof(ObsOut)));
         for (void *p : {f[0], f[1], g[0], g[1], (void *)phi1, (void *)phi2, (void *)k, (void *)psiA,
-                        (void *)psiB, (void *)macro, (void *)ctl, (void *)brk, (void *)d_step,
+                        (void *)psiB, (void *)psiP, (void *)macro, (void *)ctl, (void *)brk, (void *)d_step,
                         (void *)obs_scratch, (void *)obs_out})
             if (!p) return fail(FCD_ENOMEM, "device allocation failed");
         CK(cudaMallocHost(&h_ctl, sizeof(MgCtl)));
@@ -273,6 +274,7 @@ struct Engine : fcd_ctx {
         CK(cudaMemsetAsync(ctl, 0, sizeof(MgCtl), s));
         CK(cudaMemsetAsync(psiA, 0, ps * sizeof(T), s));
         CK(cudaMemsetAsync(psiB, 0, ps * sizeof(T), s));
+        CK(cudaMemsetAsync(psiP, 0, ps * sizeof(T), s));
         CK(cudaMemsetAsync(brk, 0xff, sizeof(unsigned long long), s));
         CK(cudaMemsetAsync(d_step, 0, sizeof(long long), s));
         // padding columns of every plane stay zero
@@ -300,13 +302,22 @@ struct Engine : fcd_ctx {
         double res;
         fcd_status st = solve(prm.mag_tol, prm.mag_max_iter > 100 ? prm.mag_max_iter : 100, &it, &res);
         if (st != FCD_OK && st != FCD_ENOCONV) return st;
+        return keep_history();
+    }
+
+    // The previous potential (for the extrapolated initial guess) := current.
+    fcd_status keep_history() {
+        if (sync_ctl() != FCD_OK) return FCD_ECUDA;
+        CK(cudaMemcpyAsync(psiP, h_ctl->cur ? psiB : psiA, ps * sizeof(T), cudaMemcpyDeviceToDevice, stream));
+        CK(cudaStreamSynchronize(stream));
         return FCD_OK;
     }
 
     // ---- one step as kernel launches on stream s (the MG loop by while node
     // when capturing, by host polling otherwise)
     fcd_status enqueue_pre(int c, cudaStream_t s) {
-        PhaseCtl pc{ctl, magnetic() ? 1 : 0, prm.mag_tol * D.H0, prm.mag_max_iter, d_step};
+        PhaseCtl pc{ctl, magnetic() ? 1 : 0, prm.mag_tol * D.H0, prm.mag_max_iter, d_step,
+                    magnetic() ? 1 : 0, psiA, psiB, psiP};
         launch_phase<T>(mode, P, g[c], phi1, phi2, k, pc, s);
         return FCD_OK;
     }
@@ -425,12 +436,14 @@ struct Engine : fcd_ctx {
         if (!magnetic()) {
             CK(cudaMemsetAsync(psiA, 0, ps * sizeof(T), s));
             CK(cudaMemsetAsync(psiB, 0, ps * sizeof(T), s));
+            CK(cudaMemsetAsync(psiP, 0, ps * sizeof(T), s));
             CK(cudaStreamSynchronize(s));
             if (iters) *iters = 0;
             if (resid) *resid = 0.0;
             return FCD_OK;
         }
-        launch_phase<T>(mode, P, g[cur], phi1, phi2, k, PhaseCtl{ctl, 1, tol * D.H0, max_iter, nullptr}, s);
+        launch_phase<T>(mode, P, g[cur], phi1, phi2, k,
+                        PhaseCtl{ctl, 1, tol * D.H0, max_iter, nullptr, 0, nullptr, nullptr, nullptr}, s);
         host_kernels += 1;
         CK(cudaGetLastError());
         fcd_status st = host_mg_loop(s);
@@ -507,7 +520,8 @@ struct Engine : fcd_ctx {
         if (!st) return fail(FCD_ENOMEM, "staging allocation failed");
         fcd_status rc = FCD_OK;
         if (which <= FCD_FIELD_PHI3) {
-            launch_phase<T>(mode, P, g[cur], phi1, phi2, nullptr, PhaseCtl{nullptr, 0, 0.0, 0, nullptr}, s);
+            launch_phase<T>(mode, P, g[cur], phi1, phi2, nullptr,
+                            PhaseCtl{nullptr, 0, 0.0, 0, nullptr, 0, nullptr, nullptr, nullptr}, s);
             if (which == FCD_FIELD_PHI1) launch_plane_to_f64<T>(phi1, prm.nx, prm.ny, pitch, st, s);
             else if (which == FCD_FIELD_PHI2) launch_plane_to_f64<T>(phi2, prm.nx, prm.ny, pitch, st, s);
             else launch_phi3_to_f64<T>(phi1, phi2, prm.nx, prm.ny, pitch, st, s);
@@ -574,11 +588,11 @@ struct Engine : fcd_ctx {
         cudaFree(st);
         if (e != cudaSuccess) return fail(FCD_ECUDA, "set_populations: %s", cudaGetErrorString(e));
         step = st_;
-        return FCD_OK;
+        return pi ? keep_history() : FCD_OK;
     }
 
     size_t state_bytes() const override {
-        return sizeof(SnapHeader) + 27 * (size_t)ps * sizeof(S) + (size_t)ps * sizeof(T);
+        return sizeof(SnapHeader) + 27 * (size_t)ps * sizeof(S) + 2 * (size_t)ps * sizeof(T);
     }
 
     fcd_status get_state(void *dst, size_t bytes) override {
@@ -588,7 +602,7 @@ struct Engine : fcd_ctx {
         SnapHeader h;
         std::memset(&h, 0, sizeof h);
         h.magic = SNAP_MAGIC;
-        h.version = 1;
+        h.version = 2;
         h.nx = prm.nx;
         h.ny = prm.ny;
         h.precision = prm.precision;
@@ -606,6 +620,8 @@ struct Engine : fcd_ctx {
         CK(cudaMemcpyAsync(d + off, g[cur], 18 * ps * sizeof(S), cudaMemcpyDefault, s));
         off += 18 * ps * sizeof(S);
         CK(cudaMemcpyAsync(d + off, h_ctl->cur ? psiB : psiA, ps * sizeof(T), cudaMemcpyDefault, s));
+        off += ps * sizeof(T);
+        CK(cudaMemcpyAsync(d + off, psiP, ps * sizeof(T), cudaMemcpyDefault, s));
         CK(cudaStreamSynchronize(s));
         return FCD_OK;
     }
@@ -616,7 +632,7 @@ struct Engine : fcd_ctx {
         cudaStream_t s = stream;
         CK(cudaMemcpyAsync(&h, src, sizeof h, cudaMemcpyDefault, s));
         CK(cudaStreamSynchronize(s));
-        if (h.magic != SNAP_MAGIC || h.version != 1 || h.nx != prm.nx || h.ny != prm.ny ||
+        if (h.magic != SNAP_MAGIC || h.version != 2 || h.nx != prm.nx || h.ny != prm.ny ||
             h.precision != prm.precision || h.pitch != pitch)
             return fail(FCD_ESTATE, "snapshot does not match this context");
         const char *p = static_cast<const char *>(src);
@@ -627,6 +643,8 @@ struct Engine : fcd_ctx {
         off += 18 * ps * sizeof(S);
         if (sync_ctl() != FCD_OK) return FCD_ECUDA;
         CK(cudaMemcpyAsync(h_ctl->cur ? psiB : psiA, p + off, ps * sizeof(T), cudaMemcpyDefault, s));
+        off += ps * sizeof(T);
+        CK(cudaMemcpyAsync(psiP, p + off, ps * sizeof(T), cudaMemcpyDefault, s));
         *h_brk = h.brk;
         CK(cudaMemcpyAsync(brk, h_brk, sizeof(unsigned long long), cudaMemcpyHostToDevice, s));
         long long st64 = h.step;

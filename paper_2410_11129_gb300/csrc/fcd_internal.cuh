@@ -113,6 +113,10 @@ struct PhaseCtl {
     double tolH0;
     int max_iter;
     long long *step;
+    // extrap != 0: initial guess of the solve psi' <- 2 psi'(t) - psi'(t-1);
+    // psi_prev keeps the previous solution (buffers of the compute type)
+    int extrap;
+    void *psiA, *psiB, *psi_prev;
 };
 
 struct ObsOut {

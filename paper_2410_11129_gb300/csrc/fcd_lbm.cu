@@ -55,6 +55,13 @@ __global__ void __launch_bounds__(256) phase_kernel(Phys<T> P, const void *gv, T
     }
     phi1[n] = p1;
     phi2[n] = p2;
+    if (pc.extrap) {  // second-order extrapolation in time of the potential
+        T *psi = static_cast<T *>(pc.ctl->cur ? pc.psiB : pc.psiA);
+        T *prev = static_cast<T *>(pc.psi_prev);
+        const T now = psi[n], before = prev[n];
+        prev[n] = now;
+        psi[n] = T(2) * now - before;
+    }
     if (k) {
         T h1 = clamp01(p1), h2 = clamp01(p2), h3 = clamp01(T(1) - p1 - p2);
         k[n] = T(1) / (P.ik[0] * h1 + P.ik[1] * h2 + P.ik[2] * h3);

@@ -37,6 +37,7 @@ constexpr int SX = 32, SY = 8;     // level-0 smoothing tile
 constexpr int CTA_THREADS = 1024;
 constexpr int NU_PRE = 2, NU_POST = 2, NU_FINE = 2, NU_COARSEST = 30;
 constexpr size_t CTA_SMEM_MAX = 200 * 1024;  // shared memory of the single-block levels
+constexpr size_t CTA_CELLS = 2048;            // cells of the single-block levels
 
 __device__ __forceinline__ double norm_of(const MgCtl *c) {
     return __longlong_as_double((long long)c->norm_bits);
@@ -109,37 +110,45 @@ __device__ __forceinline__ T interp_coarse(const Level<T> &F, const Level<T> &C,
 
 // Residual of level 0 on the children of each level-1 cell, summed onto it,
 // and the level-1 permeability (mean of the children); the max-norm over the
-// lattice goes to the control block.
+// lattice goes to the control block. A 32 x 8 block of level-1 cells stages
+// its lattice footprint (at most 65 x 17 cells plus a one-cell ring) of k and
+// psi' in shared memory.
+constexpr int RX = 2 * 32 + 1 + 2, RY = 2 * 8 + 1 + 2;
+
 template <typename T>
 __global__ void __launch_bounds__(256) resid0_restrict(Level<T> L0, Level<T> L1, T H0c, T H0s,
                                                        MgCtl *ctl) {
     if (ctl->done) return;
-    const int I = blockIdx.x * blockDim.x + threadIdx.x;
-    const int J = blockIdx.y * blockDim.y + threadIdx.y;
+    __shared__ T sk[RY][RX], sp[RY][RX];
+    const int nx = L0.nx, ny = L0.ny, pitch = L0.pitch;
+    const int I0 = blockIdx.x * 32, J0 = blockIdx.y * 8;
+    const int I1 = min(I0 + 32, L1.nx), J1 = min(J0 + 8, L1.ny);
+    const int fx0 = L1.cx0[I0], fx1 = L1.cx0[I1], fy0 = L1.cy0[J0], fy1 = L1.cy0[J1];
+    const int wx = fx1 - fx0 + 2, wy = fy1 - fy0 + 2;
+    const T *psi = ctl->cur ? L0.r : L0.e;
+    for (int t = threadIdx.y * 32 + threadIdx.x; t < wx * wy; t += 256) {
+        const int lx = t % wx, ly = t / wx;
+        int gx = fx0 - 1 + lx;
+        gx = gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx);
+        const int gy = fy0 - 1 + ly;
+        const int my = gy < 0 ? 0 : (gy >= ny ? ny - 1 : gy);
+        sk[ly][lx] = L0.k[(long long)my * pitch + gx];  // mirrored ghost rows
+        sp[ly][lx] = psi[(long long)my * pitch + gx];   // ghost rows never read
+    }
+    __syncthreads();
+    const int I = I0 + threadIdx.x, J = J0 + threadIdx.y;
     double mx = 0.0;
     if (I < L1.nx && J < L1.ny) {
-        const T *psi = ctl->cur ? L0.r : L0.e;
-        const int nx = L0.nx, ny = L0.ny, pitch = L0.pitch;
         T sum = T(0), ksum = T(0);
         for (int j = L1.cy0[J]; j < L1.cy0[J + 1]; j++) {
             for (int i = L1.cx0[I]; i < L1.cx0[I + 1]; i++) {
-                auto kat = [&](int dx, int dy) {
-                    int xx = i + dx;
-                    xx = xx < 0 ? xx + nx : (xx >= nx ? xx - nx : xx);
-                    int yy = j + dy;
-                    yy = yy < 0 ? 0 : (yy >= ny ? ny - 1 : yy);
-                    return L0.k[(long long)yy * pitch + xx];
-                };
-                auto pat = [&](int dx, int dy) {
-                    int xx = i + dx;
-                    xx = xx < 0 ? xx + nx : (xx >= nx ? xx - nx : xx);
-                    return psi[(long long)(j + dy) * pitch + xx];
-                };
+                const int lx = i - fx0 + 1, ly = j - fy0 + 1;
+                auto kat = [&](int dx, int dy) { return sk[ly + dy][lx + dx]; };
+                auto pat = [&](int dx, int dy) { return sp[ly + dy][lx + dx]; };
                 const Node9<T> nd = node9<T>(kat, j, ny, H0c, H0s);
-                const T p0 = psi[(long long)j * pitch + i];
-                const T r = nd.b - (off9<T>(nd, pat, j, ny) - nd.diag * p0);
+                const T r = nd.b - (off9<T>(nd, pat, j, ny) - nd.diag * sp[ly][lx]);
                 sum += r;
-                ksum += kat(0, 0);
+                ksum += sk[ly][lx];
                 const double ar = fabs((double)r);
                 mx = ar <= mx ? mx : (ar == ar ? ar : INFINITY);  // NaN counts as infinite
             }
@@ -609,11 +618,15 @@ MgHost<T> *mg_create(int nx, int ny, int pitch, T *k0, T *psiA, T *psiB, MgCtl *
     }
     // levels lc..nl-1 run in one block with their arrays in shared memory:
     // the first level from which the rest fits the budget
+    // (one SM's issue rate bounds that block, so it only takes the small levels)
     m->lc = m->nl - 1;
     for (int l = 1; l < m->nl; l++) {
-        size_t bytes = 0;
-        for (int q = l; q < m->nl; q++) bytes += (size_t)CTA_ARRAYS * xcs[q].size() * ycs[q].size() * sizeof(T);
-        if (bytes <= CTA_SMEM_MAX) { m->lc = l; break; }
+        size_t bytes = 0, cells = 0;
+        for (int q = l; q < m->nl; q++) {
+            cells += xcs[q].size() * ycs[q].size();
+            bytes += (size_t)CTA_ARRAYS * xcs[q].size() * ycs[q].size() * sizeof(T);
+        }
+        if (bytes <= CTA_SMEM_MAX && cells <= CTA_CELLS) { m->lc = l; break; }
     }
     m->cta_smem = 0;
     for (int q = m->lc; q < m->nl; q++) m->cta_smem += (size_t)CTA_ARRAYS * xcs[q].size() * ycs[q].size() * sizeof(T);
