@@ -342,11 +342,13 @@ struct Engine : fcd_ctx {
 
     fcd_status host_mg_loop(cudaStream_t s) {
         for (int guard = 0; guard < 1000000; guard++) {
-            mg_cycle<T>(mg, P.H0c, P.H0s, 0, 0, s);
+            mg_cycle_head<T>(mg, P.H0c, P.H0s, 0, 0, 0, s);
             CK(cudaGetLastError());
             CK(cudaMemcpyAsync(h_ctl, ctl, sizeof(MgCtl), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
             if (!h_ctl->keep_going) break;
+            mg_cycle_rest<T>(mg, P.H0c, P.H0s, s);
+            CK(cudaGetLastError());
         }
         return FCD_OK;
     }
@@ -371,13 +373,42 @@ struct Engine : fcd_ctx {
             cp.conditional.size = 1;
             cudaGraphNode_t wnode;
             CK(cudaGraphAddNode(&wnode, gcap, deps, nullptr, nd, &cp));
+            // while body: lattice residual, then an if node holding the rest
+            // of the V-cycle (both conditions are set by the residual kernel)
             cudaGraph_t body = cp.conditional.phGraph_out[0];
+            cudaGraphConditionalHandle hi;
+            CK(cudaGraphConditionalHandleCreate(&hi, body, 0, cudaGraphCondAssignDefault));
             cudaStream_t bs;
             CK(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
-            CK(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-            mg_cycle<T>(mg, P.H0c, P.H0s, h, 1, bs);
-            cudaGraph_t bodyOut;
-            cudaError_t e1 = cudaStreamEndCapture(bs, &bodyOut);
+            cudaError_t e1 = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0,
+                                                           cudaStreamCaptureModeThreadLocal);
+            cudaGraph_t out1 = nullptr, out2 = nullptr;
+            if (e1 == cudaSuccess) {
+                mg_cycle_head<T>(mg, P.H0c, P.H0s, h, hi, 1, bs);
+                const cudaGraphNode_t *bd = nullptr;
+                size_t bn = 0;
+                cudaStreamCaptureStatus bcs;
+                cudaGraph_t bg;
+                e1 = cudaStreamGetCaptureInfo(bs, &bcs, nullptr, &bg, &bd, nullptr, &bn);
+                cudaGraphNodeParams ip = {cudaGraphNodeTypeConditional};
+                ip.conditional.handle = hi;
+                ip.conditional.type = cudaGraphCondTypeIf;
+                ip.conditional.size = 1;
+                cudaGraphNode_t inode;
+                if (e1 == cudaSuccess) e1 = cudaGraphAddNode(&inode, body, bd, nullptr, bn, &ip);
+                if (e1 == cudaSuccess)
+                    e1 = cudaStreamUpdateCaptureDependencies(bs, &inode, nullptr, 1,
+                                                             cudaStreamSetCaptureDependencies);
+                cudaError_t e2 = cudaStreamEndCapture(bs, &out1);
+                if (e1 == cudaSuccess) e1 = e2;
+                if (e1 == cudaSuccess)
+                    e1 = cudaStreamBeginCaptureToGraph(bs, ip.conditional.phGraph_out[0], nullptr,
+                                                       nullptr, 0, cudaStreamCaptureModeThreadLocal);
+                if (e1 == cudaSuccess) {
+                    mg_cycle_rest<T>(mg, P.H0c, P.H0s, bs);
+                    e1 = cudaStreamEndCapture(bs, &out2);
+                }
+            }
             cudaStreamDestroy(bs);
             CK(e1);
             CK(cudaStreamUpdateCaptureDependencies(s, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
@@ -685,7 +716,7 @@ struct Engine : fcd_ctx {
     long launches() const override {
         MgCtl c;
         if (cudaMemcpy(&c, ctl, sizeof c, cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
-        return host_kernels + (long)c.cycles_launched * mg_kernels_per_cycle(mg);
+        return host_kernels + (long)c.cycles_launched + (long)c.total_cycles * mg_kernels_per_cycle(mg);
     }
 };
 

@@ -97,7 +97,7 @@ struct MgCtl {
     double last_resid;             // final ||r||_inf / H0
     int last_iters;
     long long total_cycles;        // cumulative V-cycles that ran in full
-    long long cycles_launched;     // cumulative cycle launches (launch accounting)
+    long long cycles_launched;     // cumulative cycle heads launched (launch accounting)
     int nonconv_count;             // solves that stopped at the cap
     double H0;
     unsigned int blocks_done;      // blocks of the last kernel of a cycle that finished
@@ -177,9 +177,13 @@ MgHost<T> *mg_create(int nx, int ny, int pitch, T *k0, T *psiA, T *psiB, MgCtl *
                      char *err, size_t errlen);
 template <typename T>
 void mg_destroy(MgHost<T> *m);
+// One V-cycle = head (lattice residual; decides whether the cycle runs) +
+// rest (launched only when the head said so: graph if node or host check).
 template <typename T>
-void mg_cycle(MgHost<T> *m, T H0c, T H0s, cudaGraphConditionalHandle h, int in_graph,
-              cudaStream_t s);
+void mg_cycle_head(MgHost<T> *m, T H0c, T H0s, cudaGraphConditionalHandle hwhile,
+                   cudaGraphConditionalHandle hif, int in_graph, cudaStream_t s);
+template <typename T>
+void mg_cycle_rest(MgHost<T> *m, T H0c, T H0s, cudaStream_t s);
 template <typename T>
 int mg_kernels_per_cycle(const MgHost<T> *m);
 template <typename T>

@@ -35,7 +35,9 @@ namespace fcd {
 
 constexpr int SX = 32, SY = 8;     // level-0 smoothing tile
 constexpr int CTA_THREADS = 1024;
-constexpr int NU_PRE = 2, NU_POST = 2, NU_FINE = 2, NU_COARSEST = 30;
+constexpr int NU_PRE = 2, NU_POST = 2, NU_FINE = 2;  // grid-wide levels: V(2,2); lattice: V(0,2)
+constexpr int NU_CTA = 1, NU_COARSEST = 20;          // single-block levels: V(1,1)
+constexpr int MIN_COARSE = 100;                      // coarsening stops at this many cells
 constexpr size_t CTA_SMEM_MAX = 200 * 1024;  // shared memory of the single-block levels
 constexpr size_t CTA_CELLS = 2048;            // cells of the single-block levels
 
@@ -115,10 +117,18 @@ __device__ __forceinline__ T interp_coarse(const Level<T> &F, const Level<T> &C,
 // psi' in shared memory.
 constexpr int RX = 2 * 32 + 1 + 2, RY = 2 * 8 + 1 + 2;
 
+__device__ void cycle_decide(MgCtl *ctl, cudaGraphConditionalHandle hw,
+                             cudaGraphConditionalHandle hi, int in_graph);
+
 template <typename T>
 __global__ void __launch_bounds__(256) resid0_restrict(Level<T> L0, Level<T> L1, T H0c, T H0s,
-                                                       MgCtl *ctl) {
-    if (ctl->done) return;
+                                                       MgCtl *ctl, cudaGraphConditionalHandle hw,
+                                                       cudaGraphConditionalHandle hi, int in_graph) {
+    const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
+    if (ctl->done) {
+        if (lead && blockIdx.x == 0 && blockIdx.y == 0) cycle_decide(ctl, hw, hi, in_graph);
+        return;
+    }
     __shared__ T sk[RY][RX], sp[RY][RX];
     const int nx = L0.nx, ny = L0.ny, pitch = L0.pitch;
     const int I0 = blockIdx.x * 32, J0 = blockIdx.y * 8;
@@ -158,21 +168,26 @@ __global__ void __launch_bounds__(256) resid0_restrict(Level<T> L0, Level<T> L1,
     }
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0 && mx > 0.0) atomic_max_nonneg(&ctl->norm_bits, mx);
+    __syncthreads();
+    if (lead) {  // the last block to finish sees the whole norm and decides the cycle
+        __threadfence();
+        if (atomicAdd(&ctl->blocks_done, 1u) == gridDim.x * gridDim.y - 1) {
+            __threadfence();
+            ctl->blocks_done = 0;
+            cycle_decide(ctl, hw, hi, in_graph);
+        }
+    }
 }
 
-__device__ void cycle_end_logic(MgCtl *ctl, cudaGraphConditionalHandle h, int in_graph);
+__device__ void cycle_close(MgCtl *ctl);
 
 // Level-0 block Gauss-Seidel after adding the coarse correction; the last
-// block to finish closes the cycle (loop condition of the graph while node).
+// block to finish closes the cycle.
 template <typename T>
 __global__ void __launch_bounds__(SX *SY) smooth0(Level<T> L0, Level<T> L1, int add_coarse,
-                                                  int sweeps, T H0c, T H0s, MgCtl *ctl,
-                                                  cudaGraphConditionalHandle h, int in_graph) {
+                                                  int sweeps, T H0c, T H0s, MgCtl *ctl) {
     const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
-    if (cycle_skip(ctl)) {
-        if (lead && blockIdx.x == 0 && blockIdx.y == 0) cycle_end_logic(ctl, h, in_graph);
-        return;
-    }
+    if (cycle_skip(ctl)) return;
     __shared__ T sp[SY + 2][SX + 2];
     __shared__ T sk[SY + 2][SX + 2];
     const int nx = L0.nx, ny = L0.ny, pitch = L0.pitch;
@@ -218,7 +233,7 @@ __global__ void __launch_bounds__(SX *SY) smooth0(Level<T> L0, Level<T> L1, int 
         if (atomicAdd(&ctl->blocks_done, 1u) == total - 1) {
             __threadfence();
             ctl->blocks_done = 0;
-            cycle_end_logic(ctl, h, in_graph);
+            cycle_close(ctl);
         }
     }
 }
@@ -438,7 +453,7 @@ __global__ void __launch_bounds__(CTA_THREADS) coarse_cta(const Level<T> *lv, in
     // V-cycle: down
     for (int l = lc; l < nl - 1; l++) {
         const CtaView<T> F = cta_view(sm, off, L, l), V = cta_view(sm, off, L, l + 1);
-        cta_gs(L[l], F, NU_PRE, tid, nthr, false);
+        cta_gs(L[l], F, NU_CTA, tid, nthr, false);
         const Level<T> &C = L[l + 1];
         const int fnx = L[l].nx, fny = L[l].ny;
         for (int t = tid; t < C.nx * C.ny; t += nthr) {
@@ -460,7 +475,7 @@ __global__ void __launch_bounds__(CTA_THREADS) coarse_cta(const Level<T> *lv, in
     }
     {  // coarsest: one warp when it is small
         const CtaView<T> V = cta_view(sm, off, L, nl - 1);
-        const bool small = L[nl - 1].nx * L[nl - 1].ny <= 64;
+        const bool small = L[nl - 1].nx * L[nl - 1].ny <= 128;
         if (!small) cta_gs(L[nl - 1], V, NU_COARSEST, tid, nthr, false);
         else if (tid < 32) cta_gs(L[nl - 1], V, NU_COARSEST, tid, 32, true);
         __syncthreads();
@@ -480,7 +495,7 @@ __global__ void __launch_bounds__(CTA_THREADS) coarse_cta(const Level<T> *lv, in
             F.e[t] += (T(1) - wy) * a + wy * b;
         }
         __syncthreads();
-        cta_gs(L[l], F, NU_POST, tid, nthr, false);
+        cta_gs(L[l], F, NU_CTA, tid, nthr, false);
     }
     {
         const CtaView<T> V = cta_view(sm, off, L, lc);
@@ -489,9 +504,11 @@ __global__ void __launch_bounds__(CTA_THREADS) coarse_cta(const Level<T> *lv, in
     }
 }
 
-// End of a cycle (one thread): converged or capped -> stop the loop, else
-// count the cycle, flip the level-0 buffer and clear the norm.
-__device__ void cycle_end_logic(MgCtl *ctl, cudaGraphConditionalHandle h, int in_graph) {
+// Start of a cycle (one thread, after the lattice residual is complete):
+// converged, capped or non-finite -> record the result and stop; otherwise run
+// the rest of the cycle. Sets the graph's while and if conditions.
+__device__ void cycle_decide(MgCtl *ctl, cudaGraphConditionalHandle hw,
+                             cudaGraphConditionalHandle hi, int in_graph) {
     ctl->cycles_launched++;
     if (!ctl->done) {
         const double nrm = norm_of(ctl);
@@ -501,15 +518,22 @@ __device__ void cycle_end_logic(MgCtl *ctl, cudaGraphConditionalHandle h, int in
             if (!ctl->converged) ctl->nonconv_count++;
             ctl->last_resid = ctl->H0 > 0.0 ? nrm / ctl->H0 : 0.0;
             ctl->last_iters = ctl->iter;
-        } else {
-            ctl->iter++;
-            ctl->total_cycles++;
-            ctl->cur ^= 1;
-            ctl->norm_bits = 0ull;
         }
     }
     ctl->keep_going = !ctl->done;
-    if (in_graph) cudaGraphSetConditional(h, ctl->keep_going ? 1u : 0u);
+    if (in_graph) {
+        cudaGraphSetConditional(hi, ctl->keep_going ? 1u : 0u);
+        cudaGraphSetConditional(hw, ctl->keep_going ? 1u : 0u);
+    }
+}
+
+// End of a full cycle (one thread): count it, flip the lattice buffer, clear
+// the norm for the next residual.
+__device__ void cycle_close(MgCtl *ctl) {
+    ctl->iter++;
+    ctl->total_cycles++;
+    ctl->cur ^= 1;
+    ctl->norm_bits = 0ull;
 }
 
 // ------------------------------------------------------------------ host side
@@ -597,7 +621,7 @@ MgHost<T> *mg_create(int nx, int ny, int pitch, T *k0, T *psiA, T *psiB, MgCtl *
     while (true) {
         const int px = (int)fx.back().size() - 1, py = (int)fy.back().size() - 1;
         const bool cxo = px > minc, cyo = py > minc;
-        if (!cxo && !cyo) break;
+        if ((!cxo && !cyo) || (fx.size() > 1 && (long long)px * py <= MIN_COARSE)) break;
         std::vector<int> mx, my;
         if (cxo) mx = merge_faces(px); else for (int i = 0; i <= px; i++) mx.push_back(i);
         if (cyo) my = merge_faces(py); else for (int j = 0; j <= py; j++) my.push_back(j);
@@ -703,11 +727,18 @@ void mg_destroy(MgHost<T> *m) {
 static dim3 g2(int nx, int ny, dim3 b) { return dim3((nx + b.x - 1) / b.x, (ny + b.y - 1) / b.y); }
 
 template <typename T>
-void mg_cycle(MgHost<T> *m, T H0c, T H0s, cudaGraphConditionalHandle h, int in_graph,
-              cudaStream_t s) {
+void mg_cycle_head(MgHost<T> *m, T H0c, T H0s, cudaGraphConditionalHandle hw,
+                   cudaGraphConditionalHandle hi, int in_graph, cudaStream_t s) {
+    dim3 b(32, 8);
+    const std::vector<Level<T>> &lv = m->lv;
+    resid0_restrict<T><<<g2(lv[1].nx, lv[1].ny, b), b, 0, s>>>(lv[0], lv[1], H0c, H0s, m->ctl,
+                                                               hw, hi, in_graph);
+}
+
+template <typename T>
+void mg_cycle_rest(MgHost<T> *m, T H0c, T H0s, cudaStream_t s) {
     dim3 b(32, 8), bs(SX, SY);
     const std::vector<Level<T>> &lv = m->lv;
-    resid0_restrict<T><<<g2(lv[1].nx, lv[1].ny, b), b, 0, s>>>(lv[0], lv[1], H0c, H0s, m->ctl);
     for (int l = 1; l < m->lc; l++) {
         fv_smooth<T, false><<<g2(lv[l].nx, lv[l].ny, bs), bs, 0, s>>>(lv[l], lv[l + 1], NU_PRE, m->ctl);
         fv_resid_restrict<T><<<g2(lv[l + 1].nx, lv[l + 1].ny, b), b, 0, s>>>(lv[l], lv[l + 1], m->ctl);
@@ -715,12 +746,11 @@ void mg_cycle(MgHost<T> *m, T H0c, T H0s, cudaGraphConditionalHandle h, int in_g
     coarse_cta<T><<<1, CTA_THREADS, m->cta_smem, s>>>(m->d_lv, m->lc, m->nl, m->ctl);
     for (int l = m->lc - 1; l >= 1; l--)
         fv_smooth<T, true><<<g2(lv[l].nx, lv[l].ny, bs), bs, 0, s>>>(lv[l], lv[l + 1], NU_POST, m->ctl);
-    smooth0<T><<<g2(lv[0].nx, lv[0].ny, bs), bs, 0, s>>>(lv[0], lv[1], 1, NU_FINE, H0c, H0s, m->ctl,
-                                                          h, in_graph);
+    smooth0<T><<<g2(lv[0].nx, lv[0].ny, bs), bs, 0, s>>>(lv[0], lv[1], 1, NU_FINE, H0c, H0s, m->ctl);
 }
 
 template <typename T>
-int mg_kernels_per_cycle(const MgHost<T> *m) { return 3 + 3 * (m->lc - 1); }
+int mg_kernels_per_cycle(const MgHost<T> *m) { return 2 + 3 * (m->lc - 1); }  // after the head
 
 template <typename T>
 int mg_levels(const MgHost<T> *m) { return m->nl; }
@@ -730,7 +760,9 @@ int mg_levels(const MgHost<T> *m) { return m->nl; }
                                      void *(*)(size_t, void *), void (*)(void *, void *), void *, \
                                      char *, size_t);                                           \
     template void mg_destroy<T>(MgHost<T> *);                                                   \
-    template void mg_cycle<T>(MgHost<T> *, T, T, cudaGraphConditionalHandle, int, cudaStream_t); \
+    template void mg_cycle_head<T>(MgHost<T> *, T, T, cudaGraphConditionalHandle,                \
+                                   cudaGraphConditionalHandle, int, cudaStream_t);              \
+    template void mg_cycle_rest<T>(MgHost<T> *, T, T, cudaStream_t);                             \
     template int mg_kernels_per_cycle<T>(const MgHost<T> *);                                    \
     template int mg_levels<T>(const MgHost<T> *);
 FCD_MG_INST(float)
