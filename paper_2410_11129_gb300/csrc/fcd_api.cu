@@ -347,7 +347,8 @@ struct Engine : fcd_ctx {
             CK(cudaMemcpyAsync(h_ctl, ctl, sizeof(MgCtl), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
             if (!h_ctl->keep_going) break;
-            mg_cycle_rest<T>(mg, P.H0c, P.H0s, s);
+            if (h_ctl->mode == 1) mg_cycle_smooth<T>(mg, P.H0c, P.H0s, s);
+            else mg_cycle_rest<T>(mg, P.H0c, P.H0s, s);
             CK(cudaGetLastError());
         }
         return FCD_OK;
@@ -373,8 +374,9 @@ struct Engine : fcd_ctx {
             cp.conditional.size = 1;
             cudaGraphNode_t wnode;
             CK(cudaGraphAddNode(&wnode, gcap, deps, nullptr, nd, &cp));
-            // while body: lattice residual, then an if node holding the rest
-            // of the V-cycle (both conditions are set by the residual kernel)
+            // while body: lattice residual, then a switch node holding the rest
+            // of the V-cycle (case 0) or lattice sweeps only (case 1); both
+            // conditions are set by the residual kernel
             cudaGraph_t body = cp.conditional.phGraph_out[0];
             cudaGraphConditionalHandle hi;
             CK(cudaGraphConditionalHandleCreate(&hi, body, 0, cudaGraphCondAssignDefault));
@@ -392,8 +394,8 @@ struct Engine : fcd_ctx {
                 e1 = cudaStreamGetCaptureInfo(bs, &bcs, nullptr, &bg, &bd, nullptr, &bn);
                 cudaGraphNodeParams ip = {cudaGraphNodeTypeConditional};
                 ip.conditional.handle = hi;
-                ip.conditional.type = cudaGraphCondTypeIf;
-                ip.conditional.size = 1;
+                ip.conditional.type = cudaGraphCondTypeSwitch;
+                ip.conditional.size = 2;
                 cudaGraphNode_t inode;
                 if (e1 == cudaSuccess) e1 = cudaGraphAddNode(&inode, body, bd, nullptr, bn, &ip);
                 if (e1 == cudaSuccess)
@@ -406,6 +408,13 @@ struct Engine : fcd_ctx {
                                                        nullptr, 0, cudaStreamCaptureModeThreadLocal);
                 if (e1 == cudaSuccess) {
                     mg_cycle_rest<T>(mg, P.H0c, P.H0s, bs);
+                    e1 = cudaStreamEndCapture(bs, &out2);
+                }
+                if (e1 == cudaSuccess)
+                    e1 = cudaStreamBeginCaptureToGraph(bs, ip.conditional.phGraph_out[1], nullptr,
+                                                       nullptr, 0, cudaStreamCaptureModeThreadLocal);
+                if (e1 == cudaSuccess) {
+                    mg_cycle_smooth<T>(mg, P.H0c, P.H0s, bs);
                     e1 = cudaStreamEndCapture(bs, &out2);
                 }
             }
@@ -716,7 +725,8 @@ struct Engine : fcd_ctx {
     long launches() const override {
         MgCtl c;
         if (cudaMemcpy(&c, ctl, sizeof c, cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
-        return host_kernels + (long)c.cycles_launched + (long)c.total_cycles * mg_kernels_per_cycle(mg);
+        return host_kernels + (long)c.cycles_launched + (long)c.total_cycles * mg_kernels_per_cycle(mg) +
+               (long)c.smooth_cycles;
     }
 };
 

@@ -102,6 +102,9 @@ struct MgCtl {
     double H0;
     unsigned int blocks_done;      // blocks of the last kernel of a cycle that finished
     long long step_cur;            // step index of the step in flight (breakup key)
+    int mode;                      // decision of the cycle head: 0 V-cycle, 1 fine smoothing, 2 stop
+    int smooth_left;               // fine-smoothing-only cycles still allowed in this solve
+    long long smooth_cycles;       // cumulative fine-smoothing-only cycles (launch accounting)
 };
 
 // What the phase kernel does besides Eq. 32: reset the solve's control block
@@ -184,6 +187,8 @@ void mg_cycle_head(MgHost<T> *m, T H0c, T H0s, cudaGraphConditionalHandle hwhile
                    cudaGraphConditionalHandle hif, int in_graph, cudaStream_t s);
 template <typename T>
 void mg_cycle_rest(MgHost<T> *m, T H0c, T H0s, cudaStream_t s);
+template <typename T>
+void mg_cycle_smooth(MgHost<T> *m, T H0c, T H0s, cudaStream_t s);
 template <typename T>
 int mg_kernels_per_cycle(const MgHost<T> *m);
 template <typename T>

@@ -36,8 +36,12 @@ namespace fcd {
 constexpr int SX = 32, SY = 8;     // level-0 smoothing tile
 constexpr int CTA_THREADS = 1024;
 constexpr int NU_PRE = 2, NU_POST = 2, NU_FINE = 2;  // grid-wide levels: V(2,2); lattice: V(0,2)
-constexpr int NU_CTA = 1, NU_COARSEST = 20;          // single-block levels: V(1,1)
+constexpr int NU_CTA = 1, NU_COARSEST = 8;           // single-block levels: V(1,1)
 constexpr int MIN_COARSE = 100;                      // coarsening stops at this many cells
+// A cycle whose starting residual is within SMOOTH_RATIO of the tolerance may
+// run NU_SMOOTH_ONLY lattice sweeps instead of a V-cycle (once per solve).
+constexpr double SMOOTH_RATIO = 2.5;
+constexpr int NU_SMOOTH_ONLY = 3;
 constexpr size_t CTA_SMEM_MAX = 200 * 1024;  // shared memory of the single-block levels
 constexpr size_t CTA_CELLS = 2048;            // cells of the single-block levels
 
@@ -473,12 +477,9 @@ __global__ void __launch_bounds__(CTA_THREADS) coarse_cta(const Level<T> *lv, in
         }
         __syncthreads();
     }
-    {  // coarsest: one warp when it is small
+    {  // coarsest (<= 100 cells, walls at most a few cells away: GS converges fast)
         const CtaView<T> V = cta_view(sm, off, L, nl - 1);
-        const bool small = L[nl - 1].nx * L[nl - 1].ny <= 128;
-        if (!small) cta_gs(L[nl - 1], V, NU_COARSEST, tid, nthr, false);
-        else if (tid < 32) cta_gs(L[nl - 1], V, NU_COARSEST, tid, 32, true);
-        __syncthreads();
+        cta_gs(L[nl - 1], V, NU_COARSEST, tid, nthr, false);
     }
     // up
     for (int l = nl - 2; l >= lc; l--) {
@@ -506,7 +507,8 @@ __global__ void __launch_bounds__(CTA_THREADS) coarse_cta(const Level<T> *lv, in
 
 // Start of a cycle (one thread, after the lattice residual is complete):
 // converged, capped or non-finite -> record the result and stop; otherwise run
-// the rest of the cycle. Sets the graph's while and if conditions.
+// a V-cycle, or only lattice sweeps when the residual is already close to the
+// tolerance. Sets the graph's while and switch conditions.
 __device__ void cycle_decide(MgCtl *ctl, cudaGraphConditionalHandle hw,
                              cudaGraphConditionalHandle hi, int in_graph) {
     ctl->cycles_launched++;
@@ -521,8 +523,16 @@ __device__ void cycle_decide(MgCtl *ctl, cudaGraphConditionalHandle hw,
         }
     }
     ctl->keep_going = !ctl->done;
+    if (ctl->done) {
+        ctl->mode = 2;
+    } else if (ctl->smooth_left > 0 && norm_of(ctl) <= SMOOTH_RATIO * ctl->tolH0) {
+        ctl->mode = 1;  // close to the tolerance: lattice sweeps only
+        ctl->smooth_left--;
+    } else {
+        ctl->mode = 0;  // full V-cycle
+    }
     if (in_graph) {
-        cudaGraphSetConditional(hi, ctl->keep_going ? 1u : 0u);
+        cudaGraphSetConditional(hi, (unsigned)ctl->mode);  // switch: 0 V-cycle, 1 sweeps, 2 none
         cudaGraphSetConditional(hw, ctl->keep_going ? 1u : 0u);
     }
 }
@@ -531,7 +541,8 @@ __device__ void cycle_decide(MgCtl *ctl, cudaGraphConditionalHandle hw,
 // the norm for the next residual.
 __device__ void cycle_close(MgCtl *ctl) {
     ctl->iter++;
-    ctl->total_cycles++;
+    if (ctl->mode == 1) ctl->smooth_cycles++;
+    else ctl->total_cycles++;
     ctl->cur ^= 1;
     ctl->norm_bits = 0ull;
 }
@@ -750,6 +761,14 @@ void mg_cycle_rest(MgHost<T> *m, T H0c, T H0s, cudaStream_t s) {
 }
 
 template <typename T>
+void mg_cycle_smooth(MgHost<T> *m, T H0c, T H0s, cudaStream_t s) {
+    dim3 bs(SX, SY);
+    const std::vector<Level<T>> &lv = m->lv;
+    smooth0<T><<<g2(lv[0].nx, lv[0].ny, bs), bs, 0, s>>>(lv[0], lv[1], 0, NU_SMOOTH_ONLY, H0c, H0s,
+                                                          m->ctl);
+}
+
+template <typename T>
 int mg_kernels_per_cycle(const MgHost<T> *m) { return 2 + 3 * (m->lc - 1); }  // after the head
 
 template <typename T>
@@ -763,6 +782,7 @@ int mg_levels(const MgHost<T> *m) { return m->nl; }
     template void mg_cycle_head<T>(MgHost<T> *, T, T, cudaGraphConditionalHandle,                \
                                    cudaGraphConditionalHandle, int, cudaStream_t);              \
     template void mg_cycle_rest<T>(MgHost<T> *, T, T, cudaStream_t);                             \
+    template void mg_cycle_smooth<T>(MgHost<T> *, T, T, cudaStream_t);                           \
     template int mg_kernels_per_cycle<T>(const MgHost<T> *);                                    \
     template int mg_levels<T>(const MgHost<T> *);
 FCD_MG_INST(float)
