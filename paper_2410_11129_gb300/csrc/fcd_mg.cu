@@ -102,12 +102,43 @@ __device__ __forceinline__ T off9(const Node9<T> &n, PF pat, int y, int ny) {
     return s;
 }
 
-template <typename T>
-__device__ __forceinline__ T interp_coarse(const Level<T> &F, const Level<T> &C, int i, int j) {
-    const int x0 = F.px0[i], x1 = F.px1[i];
-    const T wx = F.pwx[i];
-    const int y0 = F.py0[j], y1 = F.py1[j];
-    const T wy = F.pwy[j];
+// Interpolation weights of a tile's columns and rows, staged in shared memory.
+template <typename T, int NXT, int NYT>
+struct ProlongTile {
+    int x0[NXT], x1[NXT], y0[NYT], y1[NYT];
+    T wx[NXT], wy[NYT];
+};
+
+template <typename T, int NXT, int NYT>
+__device__ __forceinline__ void prolong_tile_load(ProlongTile<T, NXT, NYT> &pt, const Level<T> &F,
+                                                  int gx_first, int gy_first) {
+    const int t = threadIdx.y * blockDim.x + threadIdx.x;
+    if (t < NXT) {
+        int gx = gx_first + t;
+        if (gx < 0) gx += F.nx;
+        while (gx >= F.nx) gx -= F.nx;
+        pt.x0[t] = F.px0[gx];
+        pt.x1[t] = F.px1[gx];
+        pt.wx[t] = F.pwx[gx];
+    } else if (t < NXT + NYT) {
+        const int q = t - NXT, gy = gy_first + q;
+        if (gy >= 0 && gy < F.ny) {
+            pt.y0[q] = F.py0[gy];
+            pt.y1[q] = F.py1[gy];
+            pt.wy[q] = F.pwy[gy];
+        } else {
+            pt.y0[q] = -1;
+            pt.y1[q] = -1;
+            pt.wy[q] = T(0);
+        }
+    }
+}
+
+template <typename T, int NXT, int NYT>
+__device__ __forceinline__ T prolong_at(const ProlongTile<T, NXT, NYT> &pt, const Level<T> &C,
+                                        int lx, int ly) {
+    const int x0 = pt.x0[lx], x1 = pt.x1[lx], y0 = pt.y0[ly], y1 = pt.y1[ly];
+    const T wx = pt.wx[lx], wy = pt.wy[ly];
     T a = T(0), b = T(0);
     if (y0 >= 0) a = (T(1) - wx) * C.e[(long long)y0 * C.pitch + x0] + wx * C.e[(long long)y0 * C.pitch + x1];
     if (y1 >= 0) b = (T(1) - wx) * C.e[(long long)y1 * C.pitch + x0] + wx * C.e[(long long)y1 * C.pitch + x1];
@@ -116,31 +147,33 @@ __device__ __forceinline__ T interp_coarse(const Level<T> &F, const Level<T> &C,
 
 // Residual of level 0 on the children of each level-1 cell, summed onto it,
 // and the level-1 permeability (mean of the children); the max-norm over the
-// lattice goes to the control block. A 32 x 8 block of level-1 cells stages
-// its lattice footprint (at most 65 x 17 cells plus a one-cell ring) of k and
-// psi' in shared memory.
-constexpr int RX = 2 * 32 + 1 + 2, RY = 2 * 8 + 1 + 2;
-
+// lattice goes to the control block. A block covers 16 x 8 level-1 cells: it
+// stages their lattice footprint (at most 33 x 17 nodes plus a one-node ring)
+// of k and psi' in shared memory, computes one lattice residual per thread,
+// then sums the children per coarse cell.
 __device__ void cycle_decide(MgCtl *ctl, cudaGraphConditionalHandle hw,
                              cudaGraphConditionalHandle hi, int in_graph);
 
+constexpr int R1X = 16, R1Y = 8, R0T = 512;
+constexpr int RX = 2 * R1X + 1 + 2, RY = 2 * R1Y + 1 + 2;
+
 template <typename T>
-__global__ void __launch_bounds__(256) resid0_restrict(Level<T> L0, Level<T> L1, T H0c, T H0s,
+__global__ void __launch_bounds__(R0T) resid0_restrict(Level<T> L0, Level<T> L1, T H0c, T H0s,
                                                        MgCtl *ctl, cudaGraphConditionalHandle hw,
                                                        cudaGraphConditionalHandle hi, int in_graph) {
-    const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
+    const bool lead = threadIdx.x == 0;
     if (ctl->done) {
         if (lead && blockIdx.x == 0 && blockIdx.y == 0) cycle_decide(ctl, hw, hi, in_graph);
         return;
     }
-    __shared__ T sk[RY][RX], sp[RY][RX];
+    __shared__ T sk[RY][RX], sp[RY][RX], sr[RY - 2][RX - 2];
     const int nx = L0.nx, ny = L0.ny, pitch = L0.pitch;
-    const int I0 = blockIdx.x * 32, J0 = blockIdx.y * 8;
-    const int I1 = min(I0 + 32, L1.nx), J1 = min(J0 + 8, L1.ny);
+    const int I0 = blockIdx.x * R1X, J0 = blockIdx.y * R1Y;
+    const int I1 = min(I0 + R1X, L1.nx), J1 = min(J0 + R1Y, L1.ny);
     const int fx0 = L1.cx0[I0], fx1 = L1.cx0[I1], fy0 = L1.cy0[J0], fy1 = L1.cy0[J1];
-    const int wx = fx1 - fx0 + 2, wy = fy1 - fy0 + 2;
+    const int fw = fx1 - fx0, fh = fy1 - fy0, wx = fw + 2, wy = fh + 2;
     const T *psi = ctl->cur ? L0.r : L0.e;
-    for (int t = threadIdx.y * 32 + threadIdx.x; t < wx * wy; t += 256) {
+    for (int t = threadIdx.x; t < wx * wy; t += R0T) {
         const int lx = t % wx, ly = t / wx;
         int gx = fx0 - 1 + lx;
         gx = gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx);
@@ -150,25 +183,30 @@ __global__ void __launch_bounds__(256) resid0_restrict(Level<T> L0, Level<T> L1,
         sp[ly][lx] = psi[(long long)my * pitch + gx];   // ghost rows never read
     }
     __syncthreads();
-    const int I = I0 + threadIdx.x, J = J0 + threadIdx.y;
     double mx = 0.0;
-    if (I < L1.nx && J < L1.ny) {
-        T sum = T(0), ksum = T(0);
-        for (int j = L1.cy0[J]; j < L1.cy0[J + 1]; j++) {
-            for (int i = L1.cx0[I]; i < L1.cx0[I + 1]; i++) {
-                const int lx = i - fx0 + 1, ly = j - fy0 + 1;
-                auto kat = [&](int dx, int dy) { return sk[ly + dy][lx + dx]; };
-                auto pat = [&](int dx, int dy) { return sp[ly + dy][lx + dx]; };
-                const Node9<T> nd = node9<T>(kat, j, ny, H0c, H0s);
-                const T r = nd.b - (off9<T>(nd, pat, j, ny) - nd.diag * sp[ly][lx]);
-                sum += r;
-                ksum += sk[ly][lx];
-                const double ar = fabs((double)r);
-                mx = ar <= mx ? mx : (ar == ar ? ar : INFINITY);  // NaN counts as infinite
-            }
+    for (int t = threadIdx.x; t < fw * fh; t += R0T) {
+        const int qx = t % fw, qy = t / fw, lx = qx + 1, ly = qy + 1, j = fy0 + qy;
+        auto kat = [&](int dx, int dy) { return sk[ly + dy][lx + dx]; };
+        auto pat = [&](int dx, int dy) { return sp[ly + dy][lx + dx]; };
+        const Node9<T> nd = node9<T>(kat, j, ny, H0c, H0s);
+        const T r = nd.b - (off9<T>(nd, pat, j, ny) - nd.diag * sp[ly][lx]);
+        sr[qy][qx] = r;
+        const double ar = fabs((double)r);
+        mx = ar <= mx ? mx : (ar == ar ? ar : INFINITY);  // NaN counts as infinite
+    }
+    __syncthreads();
+    if (threadIdx.x < R1X * R1Y) {
+        const int I = I0 + threadIdx.x % R1X, J = J0 + threadIdx.x / R1X;
+        if (I < L1.nx && J < L1.ny) {
+            T sum = T(0), ksum = T(0);
+            for (int j = L1.cy0[J]; j < L1.cy0[J + 1]; j++)
+                for (int i = L1.cx0[I]; i < L1.cx0[I + 1]; i++) {
+                    sum += sr[j - fy0][i - fx0];
+                    ksum += sk[j - fy0 + 1][i - fx0 + 1];
+                }
+            L1.b[(long long)J * L1.pitch + I] = sum;
+            L1.k[(long long)J * L1.pitch + I] = ksum / (L1.wx[I] * L1.wy[J]);  // unit lattice cells
         }
-        L1.b[(long long)J * L1.pitch + I] = sum;
-        L1.k[(long long)J * L1.pitch + I] = ksum / (L1.wx[I] * L1.wy[J]);  // unit lattice cells
     }
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0 && mx > 0.0) atomic_max_nonneg(&ctl->norm_bits, mx);
@@ -198,21 +236,26 @@ __global__ void __launch_bounds__(SX *SY) smooth0(Level<T> L0, Level<T> L1, int 
     const int x0 = blockIdx.x * SX, y0 = blockIdx.y * SY;
     const T *src = ctl->cur ? L0.r : L0.e;
     T *dst = ctl->cur ? L0.e : L0.r;
+    __shared__ ProlongTile<T, SX + 2, SY + 2> pt;
+    if (add_coarse) prolong_tile_load(pt, L0, x0 - 1, y0 - 1);
     for (int t = threadIdx.y * SX + threadIdx.x; t < (SX + 2) * (SY + 2); t += SX * SY) {
         const int lx = t % (SX + 2), ly = t / (SX + 2);
         int gx = x0 - 1 + lx;
-        gx = ((gx % nx) + nx) % nx;
+        if (gx < 0) gx += nx;
+        while (gx >= nx) gx -= nx;
         const int gy = y0 - 1 + ly;
         const int my = gy < 0 ? 0 : (gy >= ny ? ny - 1 : gy);
         sk[ly][lx] = L0.k[(long long)my * pitch + gx];
-        T v = T(0);
-        if (gy >= 0 && gy < ny) {
-            v = src[(long long)gy * pitch + gx];
-            if (add_coarse) v += interp_coarse(L0, L1, gx, gy);
-        }
-        sp[ly][lx] = v;  // ghost rows are never read: the mirror is used instead
+        sp[ly][lx] = (gy >= 0 && gy < ny) ? src[(long long)gy * pitch + gx] : T(0);
     }
     __syncthreads();
+    if (add_coarse) {  // ghost rows are never read: the mirror is used instead
+        for (int t = threadIdx.y * SX + threadIdx.x; t < (SX + 2) * (SY + 2); t += SX * SY) {
+            const int lx = t % (SX + 2), ly = t / (SX + 2), gy = y0 - 1 + ly;
+            if (gy >= 0 && gy < ny) sp[ly][lx] += prolong_at(pt, L1, lx, ly);
+        }
+        __syncthreads();
+    }
     const int lx = threadIdx.x + 1, ly = threadIdx.y + 1;
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
     const bool own = x < nx && y < ny;
@@ -302,20 +345,30 @@ __global__ void __launch_bounds__(SX *SY) fv_smooth(Level<T> L, Level<T> C, int 
     __shared__ T sk[SY + 2][SX + 2];
     const int nx = L.nx, ny = L.ny, p = L.pitch;
     const int x0 = blockIdx.x * SX, y0 = blockIdx.y * SY;
+    __shared__ ProlongTile<T, SX + 2, SY + 2> pt;
+    if (POST) prolong_tile_load(pt, L, x0 - 1, y0 - 1);
     for (int t = threadIdx.y * SX + threadIdx.x; t < (SX + 2) * (SY + 2); t += SX * SY) {
         const int lx = t % (SX + 2), ly = t / (SX + 2);
         int gx = x0 - 1 + lx;
-        gx = ((gx % nx) + nx) % nx;
+        if (gx < 0) gx += nx;
+        while (gx >= nx) gx -= nx;
         const int gy = y0 - 1 + ly;
         T kv = T(0), ev = T(0);
         if (gy >= 0 && gy < ny) {
             kv = L.k[(long long)gy * p + gx];
-            if (POST) ev = L.r[(long long)gy * p + gx] + interp_coarse(L, C, gx, gy);
+            if (POST) ev = L.r[(long long)gy * p + gx];
         }
         sk[ly][lx] = kv;
         se[ly][lx] = ev;
     }
     __syncthreads();
+    if (POST) {
+        for (int t = threadIdx.y * SX + threadIdx.x; t < (SX + 2) * (SY + 2); t += SX * SY) {
+            const int lx = t % (SX + 2), ly = t / (SX + 2), gy = y0 - 1 + ly;
+            if (gy >= 0 && gy < ny) se[ly][lx] += prolong_at(pt, C, lx, ly);
+        }
+        __syncthreads();
+    }
     const int lx = threadIdx.x + 1, ly = threadIdx.y + 1;
     const int I = x0 + threadIdx.x, J = y0 + threadIdx.y;
     const bool own = I < nx && J < ny;
@@ -740,10 +793,9 @@ static dim3 g2(int nx, int ny, dim3 b) { return dim3((nx + b.x - 1) / b.x, (ny +
 template <typename T>
 void mg_cycle_head(MgHost<T> *m, T H0c, T H0s, cudaGraphConditionalHandle hw,
                    cudaGraphConditionalHandle hi, int in_graph, cudaStream_t s) {
-    dim3 b(32, 8);
     const std::vector<Level<T>> &lv = m->lv;
-    resid0_restrict<T><<<g2(lv[1].nx, lv[1].ny, b), b, 0, s>>>(lv[0], lv[1], H0c, H0s, m->ctl,
-                                                               hw, hi, in_graph);
+    resid0_restrict<T><<<g2(lv[1].nx, lv[1].ny, dim3(R1X, R1Y)), R0T, 0, s>>>(
+        lv[0], lv[1], H0c, H0s, m->ctl, hw, hi, in_graph);
 }
 
 template <typename T>
