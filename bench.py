@@ -210,6 +210,7 @@ def run_ours(args):
     clk.start()
     time.sleep(0.3)
     n0 = ch.kernel_launches()
+    st0 = ch.solver_stats()
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     stage = {"phase": 0.0, "solve": 0.0, "collide": 0.0}
@@ -226,6 +227,7 @@ def run_ours(args):
     barrier()
     step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
     n1 = ch.kernel_launches()
+    st1 = ch.solver_stats()
     obs = ch.observe(allow=(fcd.FCD_ENOCONV,))
     clocks = clk.stop()
     total_ms = sum(step_ms)
@@ -280,6 +282,7 @@ def run_ours(args):
         "e2e": e2e,
         "gpu_launches": int(n1 - n0),
         "mag_cycles_last_solve": obs["mag_iters"], "mag_resid_last_solve": obs["mag_resid"],
+        "solver_per_step": {k: (st1[k] - st0[k]) / args.steps for k in st0},
         "clocks": clocks,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

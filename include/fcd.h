@@ -159,6 +159,11 @@ fcd_status fcd_get_derived(const fcd_ctx *ctx, double *out15);
  * synchronises to read the device-side cycle count). */
 long fcd_kernel_launches(const fcd_ctx *ctx);
 
+/* Cumulative potential-solver counters since create: [cycle heads (lattice
+ * residual evaluations), V-cycles, two-grid cycles, lattice-sweep cycles,
+ * solves stopped at the cycle cap] (synchronises). */
+fcd_status fcd_solver_stats(fcd_ctx *ctx, long long *out5);
+
 /* Timing of the stages of a step with CUDA events recorded on the context's
  * stream (inside the step graph): enable, run fcd_step, then read
  * ms4 = [phase recovery + coarse permeabilities, potential solve,

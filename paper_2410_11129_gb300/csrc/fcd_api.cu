@@ -152,6 +152,7 @@ struct fcd_ctx {
     virtual fcd_status get_state(void *dst, size_t bytes) = 0;
     virtual fcd_status set_state(const void *src, size_t bytes) = 0;
     virtual long launches() const = 0;
+    virtual fcd_status solver_stats(long long *out5) = 0;
     virtual fcd_status set_profiling(int on) = 0;
     virtual fcd_status profile(double *ms) = 0;
     fcd_status fail(fcd_status s, const char *fmt, ...) {
@@ -348,6 +349,7 @@ struct Engine : fcd_ctx {
             CK(cudaStreamSynchronize(s));
             if (!h_ctl->keep_going) break;
             if (h_ctl->mode == 1) mg_cycle_smooth<T>(mg, P.H0c, P.H0s, s);
+            else if (h_ctl->mode == 2) mg_cycle_twogrid<T>(mg, P.H0c, P.H0s, s);
             else mg_cycle_rest<T>(mg, P.H0c, P.H0s, s);
             CK(cudaGetLastError());
         }
@@ -375,8 +377,9 @@ struct Engine : fcd_ctx {
             cudaGraphNode_t wnode;
             CK(cudaGraphAddNode(&wnode, gcap, deps, nullptr, nd, &cp));
             // while body: lattice residual, then a switch node holding the rest
-            // of the V-cycle (case 0) or lattice sweeps only (case 1); both
-            // conditions are set by the residual kernel
+            // of the V-cycle (case 0), lattice sweeps only (case 1) or a
+            // two-grid cycle (case 2); both conditions are set by the residual
+            // kernel
             cudaGraph_t body = cp.conditional.phGraph_out[0];
             cudaGraphConditionalHandle hi;
             CK(cudaGraphConditionalHandleCreate(&hi, body, 0, cudaGraphCondAssignDefault));
@@ -395,7 +398,7 @@ struct Engine : fcd_ctx {
                 cudaGraphNodeParams ip = {cudaGraphNodeTypeConditional};
                 ip.conditional.handle = hi;
                 ip.conditional.type = cudaGraphCondTypeSwitch;
-                ip.conditional.size = 2;
+                ip.conditional.size = 3;
                 cudaGraphNode_t inode;
                 if (e1 == cudaSuccess) e1 = cudaGraphAddNode(&inode, body, bd, nullptr, bn, &ip);
                 if (e1 == cudaSuccess)
@@ -415,6 +418,13 @@ struct Engine : fcd_ctx {
                                                        nullptr, 0, cudaStreamCaptureModeThreadLocal);
                 if (e1 == cudaSuccess) {
                     mg_cycle_smooth<T>(mg, P.H0c, P.H0s, bs);
+                    e1 = cudaStreamEndCapture(bs, &out2);
+                }
+                if (e1 == cudaSuccess)
+                    e1 = cudaStreamBeginCaptureToGraph(bs, ip.conditional.phGraph_out[2], nullptr,
+                                                       nullptr, 0, cudaStreamCaptureModeThreadLocal);
+                if (e1 == cudaSuccess) {
+                    mg_cycle_twogrid<T>(mg, P.H0c, P.H0s, bs);
                     e1 = cudaStreamEndCapture(bs, &out2);
                 }
             }
@@ -722,11 +732,21 @@ struct Engine : fcd_ctx {
         return FCD_OK;
     }
 
+    fcd_status solver_stats(long long *o) override {
+        if (sync_ctl() != FCD_OK) return FCD_ECUDA;
+        o[0] = h_ctl->cycles_launched;
+        o[1] = h_ctl->total_cycles;
+        o[2] = h_ctl->twogrid_cycles;
+        o[3] = h_ctl->smooth_cycles;
+        o[4] = h_ctl->nonconv_count;
+        return FCD_OK;
+    }
+
     long launches() const override {
         MgCtl c;
         if (cudaMemcpy(&c, ctl, sizeof c, cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
         return host_kernels + (long)c.cycles_launched + (long)c.total_cycles * mg_kernels_per_cycle(mg) +
-               (long)c.smooth_cycles;
+               (long)c.smooth_cycles + 2 * (long)c.twogrid_cycles;
     }
 };
 
@@ -819,6 +839,11 @@ fcd_status fcd_get_derived(const fcd_ctx *c, double *o) {
 }
 
 long fcd_kernel_launches(const fcd_ctx *c) { return c ? c->launches() : -1; }
+
+fcd_status fcd_solver_stats(fcd_ctx *c, long long *out5) {
+    if (!c || !out5) return FCD_EINVAL;
+    return c->solver_stats(out5);
+}
 
 fcd_status fcd_set_profiling(fcd_ctx *c, int enable) { return c ? c->set_profiling(enable) : FCD_EINVAL; }
 

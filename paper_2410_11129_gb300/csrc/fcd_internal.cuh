@@ -102,9 +102,12 @@ struct MgCtl {
     double H0;
     unsigned int blocks_done;      // blocks of the last kernel of a cycle that finished
     long long step_cur;            // step index of the step in flight (breakup key)
-    int mode;                      // decision of the cycle head: 0 V-cycle, 1 fine smoothing, 2 stop
-    int smooth_left;               // fine-smoothing-only cycles still allowed in this solve
-    long long smooth_cycles;       // cumulative fine-smoothing-only cycles (launch accounting)
+    int mode;                      // decision of the cycle head: 0 V-cycle, 1 lattice sweeps,
+                                   // 2 two-grid cycle, 3 stop
+    int smooth_left;               // lattice-sweep cycles still allowed in this solve
+    int twogrid_left;              // two-grid cycles still allowed in this solve
+    long long smooth_cycles;       // cumulative lattice-sweep cycles (launch accounting)
+    long long twogrid_cycles;      // cumulative two-grid cycles (launch accounting)
 };
 
 // What the phase kernel does besides Eq. 32: reset the solve's control block
@@ -189,6 +192,8 @@ template <typename T>
 void mg_cycle_rest(MgHost<T> *m, T H0c, T H0s, cudaStream_t s);
 template <typename T>
 void mg_cycle_smooth(MgHost<T> *m, T H0c, T H0s, cudaStream_t s);
+template <typename T>
+void mg_cycle_twogrid(MgHost<T> *m, T H0c, T H0s, cudaStream_t s);
 template <typename T>
 int mg_kernels_per_cycle(const MgHost<T> *m);
 template <typename T>

@@ -38,6 +38,7 @@ __global__ void __launch_bounds__(256) phase_kernel(Phys<T> P, const void *gv, T
             c->blocks_done = 0u;
             c->mode = 0;
             c->smooth_left = 1;
+            c->twogrid_left = 2;
         }
         if (pc.step) {
             c->step_cur = *pc.step;

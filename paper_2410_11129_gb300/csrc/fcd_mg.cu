@@ -38,10 +38,14 @@ constexpr int CTA_THREADS = 1024;
 constexpr int NU_PRE = 2, NU_POST = 2, NU_FINE = 2;  // grid-wide levels: V(2,2); lattice: V(0,2)
 constexpr int NU_CTA = 1, NU_COARSEST = 8;           // single-block levels: V(1,1)
 constexpr int MIN_COARSE = 100;                      // coarsening stops at this many cells
-// A cycle whose starting residual is within SMOOTH_RATIO of the tolerance may
-// run NU_SMOOTH_ONLY lattice sweeps instead of a V-cycle (once per solve).
+// Cheaper cycles tried before a V-cycle: NU_SMOOTH_ONLY lattice sweeps when the
+// starting residual is within SMOOTH_RATIO of the tolerance (once per solve),
+// else a two-grid cycle (NU_TWOGRID sweeps on level 1, at most twice per solve).
+// The residual changes between time steps are local, so both usually suffice
+// after the extrapolated initial guess (numpy prototype: the two-grid cycle
+// reduces such residuals as much as a V-cycle).
 constexpr double SMOOTH_RATIO = 2.5;
-constexpr int NU_SMOOTH_ONLY = 3;
+constexpr int NU_SMOOTH_ONLY = 3, NU_TWOGRID = 4;
 constexpr size_t CTA_SMEM_MAX = 200 * 1024;  // shared memory of the single-block levels
 constexpr size_t CTA_CELLS = 2048;            // cells of the single-block levels
 
@@ -145,35 +149,33 @@ __device__ __forceinline__ T prolong_at(const ProlongTile<T, NXT, NYT> &pt, cons
     return (T(1) - wy) * a + wy * b;
 }
 
-// Residual of level 0 on the children of each level-1 cell, summed onto it,
-// and the level-1 permeability (mean of the children); the max-norm over the
-// lattice goes to the control block. A block covers 16 x 8 level-1 cells: it
-// stages their lattice footprint (at most 33 x 17 nodes plus a one-node ring)
-// of k and psi' in shared memory, computes one lattice residual per thread,
-// then sums the children per coarse cell.
 __device__ void cycle_decide(MgCtl *ctl, cudaGraphConditionalHandle hw,
                              cudaGraphConditionalHandle hi, int in_graph);
 
-constexpr int R1X = 16, R1Y = 8, R0T = 512;
-constexpr int RX = 2 * R1X + 1 + 2, RY = 2 * R1Y + 1 + 2;
+// Residual of level 0 on the children of each level-1 cell, summed onto it,
+// and the level-1 permeability (mean of the children); the max-norm over the
+// lattice goes to the control block. A 32 x 8 block of level-1 cells stages
+// its lattice footprint (at most 65 x 17 cells plus a one-cell ring) of k and
+// psi' in shared memory.
+constexpr int RX = 2 * 32 + 1 + 2, RY = 2 * 8 + 1 + 2;
 
 template <typename T>
-__global__ void __launch_bounds__(R0T) resid0_restrict(Level<T> L0, Level<T> L1, T H0c, T H0s,
+__global__ void __launch_bounds__(256) resid0_restrict(Level<T> L0, Level<T> L1, T H0c, T H0s,
                                                        MgCtl *ctl, cudaGraphConditionalHandle hw,
                                                        cudaGraphConditionalHandle hi, int in_graph) {
-    const bool lead = threadIdx.x == 0;
+    const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
     if (ctl->done) {
         if (lead && blockIdx.x == 0 && blockIdx.y == 0) cycle_decide(ctl, hw, hi, in_graph);
         return;
     }
-    __shared__ T sk[RY][RX], sp[RY][RX], sr[RY - 2][RX - 2];
+    __shared__ T sk[RY][RX], sp[RY][RX];
     const int nx = L0.nx, ny = L0.ny, pitch = L0.pitch;
-    const int I0 = blockIdx.x * R1X, J0 = blockIdx.y * R1Y;
-    const int I1 = min(I0 + R1X, L1.nx), J1 = min(J0 + R1Y, L1.ny);
+    const int I0 = blockIdx.x * 32, J0 = blockIdx.y * 8;
+    const int I1 = min(I0 + 32, L1.nx), J1 = min(J0 + 8, L1.ny);
     const int fx0 = L1.cx0[I0], fx1 = L1.cx0[I1], fy0 = L1.cy0[J0], fy1 = L1.cy0[J1];
-    const int fw = fx1 - fx0, fh = fy1 - fy0, wx = fw + 2, wy = fh + 2;
+    const int wx = fx1 - fx0 + 2, wy = fy1 - fy0 + 2;
     const T *psi = ctl->cur ? L0.r : L0.e;
-    for (int t = threadIdx.x; t < wx * wy; t += R0T) {
+    for (int t = threadIdx.y * 32 + threadIdx.x; t < wx * wy; t += 256) {
         const int lx = t % wx, ly = t / wx;
         int gx = fx0 - 1 + lx;
         gx = gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx);
@@ -183,30 +185,25 @@ __global__ void __launch_bounds__(R0T) resid0_restrict(Level<T> L0, Level<T> L1,
         sp[ly][lx] = psi[(long long)my * pitch + gx];   // ghost rows never read
     }
     __syncthreads();
+    const int I = I0 + threadIdx.x, J = J0 + threadIdx.y;
     double mx = 0.0;
-    for (int t = threadIdx.x; t < fw * fh; t += R0T) {
-        const int qx = t % fw, qy = t / fw, lx = qx + 1, ly = qy + 1, j = fy0 + qy;
-        auto kat = [&](int dx, int dy) { return sk[ly + dy][lx + dx]; };
-        auto pat = [&](int dx, int dy) { return sp[ly + dy][lx + dx]; };
-        const Node9<T> nd = node9<T>(kat, j, ny, H0c, H0s);
-        const T r = nd.b - (off9<T>(nd, pat, j, ny) - nd.diag * sp[ly][lx]);
-        sr[qy][qx] = r;
-        const double ar = fabs((double)r);
-        mx = ar <= mx ? mx : (ar == ar ? ar : INFINITY);  // NaN counts as infinite
-    }
-    __syncthreads();
-    if (threadIdx.x < R1X * R1Y) {
-        const int I = I0 + threadIdx.x % R1X, J = J0 + threadIdx.x / R1X;
-        if (I < L1.nx && J < L1.ny) {
-            T sum = T(0), ksum = T(0);
-            for (int j = L1.cy0[J]; j < L1.cy0[J + 1]; j++)
-                for (int i = L1.cx0[I]; i < L1.cx0[I + 1]; i++) {
-                    sum += sr[j - fy0][i - fx0];
-                    ksum += sk[j - fy0 + 1][i - fx0 + 1];
-                }
-            L1.b[(long long)J * L1.pitch + I] = sum;
-            L1.k[(long long)J * L1.pitch + I] = ksum / (L1.wx[I] * L1.wy[J]);  // unit lattice cells
+    if (I < L1.nx && J < L1.ny) {
+        T sum = T(0), ksum = T(0);
+        for (int j = L1.cy0[J]; j < L1.cy0[J + 1]; j++) {
+            for (int i = L1.cx0[I]; i < L1.cx0[I + 1]; i++) {
+                const int lx = i - fx0 + 1, ly = j - fy0 + 1;
+                auto kat = [&](int dx, int dy) { return sk[ly + dy][lx + dx]; };
+                auto pat = [&](int dx, int dy) { return sp[ly + dy][lx + dx]; };
+                const Node9<T> nd = node9<T>(kat, j, ny, H0c, H0s);
+                const T r = nd.b - (off9<T>(nd, pat, j, ny) - nd.diag * sp[ly][lx]);
+                sum += r;
+                ksum += sk[ly][lx];
+                const double ar = fabs((double)r);
+                mx = ar <= mx ? mx : (ar == ar ? ar : INFINITY);  // NaN counts as infinite
+            }
         }
+        L1.b[(long long)J * L1.pitch + I] = sum;
+        L1.k[(long long)J * L1.pitch + I] = ksum / (L1.wx[I] * L1.wy[J]);  // unit lattice cells
     }
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0 && mx > 0.0) atomic_max_nonneg(&ctl->norm_bits, mx);
@@ -335,11 +332,14 @@ __device__ __forceinline__ T fv_resid_global(const Level<T> &L, const T *e, int 
     return L.b[(long long)J * p + I] - (s - (f.te + f.tw + f.tn + f.ts) * e0);
 }
 
-// Tiled block Gauss-Seidel on a grid-wide coarse level. PRE: zero initial
-// guess, output to L.r. POST: L.r plus the coarse correction, output to L.e.
-template <typename T, bool POST>
+// Tiled block Gauss-Seidel on a grid-wide coarse level. KIND 0 (pre-smoothing):
+// zero initial guess, output to L.r. KIND 1 (post-smoothing): L.r plus the
+// coarse correction, output to L.e. KIND 2 (two-grid solve): zero initial
+// guess, output to L.e.
+template <typename T, int KIND>
 __global__ void __launch_bounds__(SX *SY) fv_smooth(Level<T> L, Level<T> C, int sweeps,
                                                     MgCtl *ctl) {
+    constexpr bool POST = KIND == 1;
     if (cycle_skip(ctl)) return;
     __shared__ T se[SY + 2][SX + 2];
     __shared__ T sk[SY + 2][SX + 2];
@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(SX *SY) fv_smooth(Level<T> L, Level<T> C, int 
             }
             __syncthreads();
         }
-    if (own) (POST ? L.e : L.r)[(long long)J * p + I] = se[ly][lx];
+    if (own) (KIND == 0 ? L.r : L.e)[(long long)J * p + I] = se[ly][lx];
 }
 
 // Residual of a grid-wide level (pre-smoothed iterate in F.r) summed onto the
@@ -577,15 +577,20 @@ __device__ void cycle_decide(MgCtl *ctl, cudaGraphConditionalHandle hw,
     }
     ctl->keep_going = !ctl->done;
     if (ctl->done) {
-        ctl->mode = 2;
+        ctl->mode = 3;
     } else if (ctl->smooth_left > 0 && norm_of(ctl) <= SMOOTH_RATIO * ctl->tolH0) {
         ctl->mode = 1;  // close to the tolerance: lattice sweeps only
         ctl->smooth_left--;
+    } else if (ctl->twogrid_left > 0) {
+        ctl->mode = 2;  // two-grid cycle
+        ctl->twogrid_left--;
+        ctl->smooth_left = 0;
     } else {
         ctl->mode = 0;  // full V-cycle
     }
     if (in_graph) {
-        cudaGraphSetConditional(hi, (unsigned)ctl->mode);  // switch: 0 V-cycle, 1 sweeps, 2 none
+        // switch node: 0 V-cycle, 1 lattice sweeps, 2 two-grid, 3 no body
+        cudaGraphSetConditional(hi, (unsigned)ctl->mode);
         cudaGraphSetConditional(hw, ctl->keep_going ? 1u : 0u);
     }
 }
@@ -595,6 +600,7 @@ __device__ void cycle_decide(MgCtl *ctl, cudaGraphConditionalHandle hw,
 __device__ void cycle_close(MgCtl *ctl) {
     ctl->iter++;
     if (ctl->mode == 1) ctl->smooth_cycles++;
+    else if (ctl->mode == 2) ctl->twogrid_cycles++;
     else ctl->total_cycles++;
     ctl->cur ^= 1;
     ctl->norm_bits = 0ull;
@@ -793,9 +799,10 @@ static dim3 g2(int nx, int ny, dim3 b) { return dim3((nx + b.x - 1) / b.x, (ny +
 template <typename T>
 void mg_cycle_head(MgHost<T> *m, T H0c, T H0s, cudaGraphConditionalHandle hw,
                    cudaGraphConditionalHandle hi, int in_graph, cudaStream_t s) {
+    dim3 b(32, 8);
     const std::vector<Level<T>> &lv = m->lv;
-    resid0_restrict<T><<<g2(lv[1].nx, lv[1].ny, dim3(R1X, R1Y)), R0T, 0, s>>>(
-        lv[0], lv[1], H0c, H0s, m->ctl, hw, hi, in_graph);
+    resid0_restrict<T><<<g2(lv[1].nx, lv[1].ny, b), b, 0, s>>>(lv[0], lv[1], H0c, H0s, m->ctl,
+                                                               hw, hi, in_graph);
 }
 
 template <typename T>
@@ -803,12 +810,12 @@ void mg_cycle_rest(MgHost<T> *m, T H0c, T H0s, cudaStream_t s) {
     dim3 b(32, 8), bs(SX, SY);
     const std::vector<Level<T>> &lv = m->lv;
     for (int l = 1; l < m->lc; l++) {
-        fv_smooth<T, false><<<g2(lv[l].nx, lv[l].ny, bs), bs, 0, s>>>(lv[l], lv[l + 1], NU_PRE, m->ctl);
+        fv_smooth<T, 0><<<g2(lv[l].nx, lv[l].ny, bs), bs, 0, s>>>(lv[l], lv[l + 1], NU_PRE, m->ctl);
         fv_resid_restrict<T><<<g2(lv[l + 1].nx, lv[l + 1].ny, b), b, 0, s>>>(lv[l], lv[l + 1], m->ctl);
     }
     coarse_cta<T><<<1, CTA_THREADS, m->cta_smem, s>>>(m->d_lv, m->lc, m->nl, m->ctl);
     for (int l = m->lc - 1; l >= 1; l--)
-        fv_smooth<T, true><<<g2(lv[l].nx, lv[l].ny, bs), bs, 0, s>>>(lv[l], lv[l + 1], NU_POST, m->ctl);
+        fv_smooth<T, 1><<<g2(lv[l].nx, lv[l].ny, bs), bs, 0, s>>>(lv[l], lv[l + 1], NU_POST, m->ctl);
     smooth0<T><<<g2(lv[0].nx, lv[0].ny, bs), bs, 0, s>>>(lv[0], lv[1], 1, NU_FINE, H0c, H0s, m->ctl);
 }
 
@@ -818,6 +825,14 @@ void mg_cycle_smooth(MgHost<T> *m, T H0c, T H0s, cudaStream_t s) {
     const std::vector<Level<T>> &lv = m->lv;
     smooth0<T><<<g2(lv[0].nx, lv[0].ny, bs), bs, 0, s>>>(lv[0], lv[1], 0, NU_SMOOTH_ONLY, H0c, H0s,
                                                           m->ctl);
+}
+
+template <typename T>
+void mg_cycle_twogrid(MgHost<T> *m, T H0c, T H0s, cudaStream_t s) {
+    dim3 bs(SX, SY);
+    const std::vector<Level<T>> &lv = m->lv;
+    fv_smooth<T, 2><<<g2(lv[1].nx, lv[1].ny, bs), bs, 0, s>>>(lv[1], lv[1], NU_TWOGRID, m->ctl);
+    smooth0<T><<<g2(lv[0].nx, lv[0].ny, bs), bs, 0, s>>>(lv[0], lv[1], 1, NU_FINE, H0c, H0s, m->ctl);
 }
 
 template <typename T>
@@ -835,6 +850,7 @@ int mg_levels(const MgHost<T> *m) { return m->nl; }
                                    cudaGraphConditionalHandle, int, cudaStream_t);              \
     template void mg_cycle_rest<T>(MgHost<T> *, T, T, cudaStream_t);                             \
     template void mg_cycle_smooth<T>(MgHost<T> *, T, T, cudaStream_t);                           \
+    template void mg_cycle_twogrid<T>(MgHost<T> *, T, T, cudaStream_t);                          \
     template int mg_kernels_per_cycle<T>(const MgHost<T> *);                                    \
     template int mg_levels<T>(const MgHost<T> *);
 FCD_MG_INST(float)

@@ -74,6 +74,7 @@ _SIGS = {
     "fcd_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "fcd_get_derived": (C.c_int, [C.c_void_p, DP]),
     "fcd_kernel_launches": (C.c_long, [C.c_void_p]),
+    "fcd_solver_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong)]),
     "fcd_set_profiling": (C.c_int, [C.c_void_p, C.c_int]),
     "fcd_last_step_profile": (C.c_int, [C.c_void_p, DP]),
     "fcd_last_error": (C.c_char_p, [C.c_void_p]),
@@ -235,6 +236,11 @@ class Channel:
         names = ["u_avg", "sigma12", "sigma13", "sigma23", "gamma1", "gamma2", "gamma3", "gammaT",
                  "tau1", "tau2", "tau3", "tau_phi", "mu0H0sq", "H0", "G"]
         return dict(zip(names, list(out)))
+
+    def solver_stats(self):
+        out = (C.c_longlong * 5)()
+        self.check(load().fcd_solver_stats(self.h, out))
+        return dict(zip(["heads", "vcycles", "twogrid", "sweeps", "capped"], list(out)))
 
     def set_profiling(self, on=True):
         self.check(load().fcd_set_profiling(self.h, 1 if on else 0))
