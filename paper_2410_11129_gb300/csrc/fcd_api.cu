@@ -342,6 +342,7 @@ struct Engine : fcd_ctx {
     int pre_kernels() const { return 1; }
 
     fcd_status host_mg_loop(cudaStream_t s) {
+        mg_presmooth<T>(mg, P.H0c, P.H0s, s);
         for (int guard = 0; guard < 1000000; guard++) {
             mg_cycle_head<T>(mg, P.H0c, P.H0s, 0, 0, 0, s);
             CK(cudaGetLastError());
@@ -363,6 +364,7 @@ struct Engine : fcd_ctx {
         enqueue_pre(c, s);
         if (profiling) CK(cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal));
         if (magnetic()) {
+            mg_presmooth<T>(mg, P.H0c, P.H0s, s);
             cudaStreamCaptureStatus cs;
             cudaGraph_t gcap;
             const cudaGraphNode_t *deps = nullptr;
@@ -494,7 +496,7 @@ struct Engine : fcd_ctx {
         }
         launch_phase<T>(mode, P, g[cur], phi1, phi2, k,
                         PhaseCtl{ctl, 1, tol * D.H0, max_iter, nullptr, 0, nullptr, nullptr, nullptr}, s);
-        host_kernels += 1;
+        host_kernels += 1;  // the opening sweeps are counted with the sweep cycles
         CK(cudaGetLastError());
         fcd_status st = host_mg_loop(s);
         if (st != FCD_OK) return st;

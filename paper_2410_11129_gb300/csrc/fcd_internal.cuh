@@ -195,6 +195,8 @@ void mg_cycle_smooth(MgHost<T> *m, T H0c, T H0s, cudaStream_t s);
 template <typename T>
 void mg_cycle_twogrid(MgHost<T> *m, T H0c, T H0s, cudaStream_t s);
 template <typename T>
+void mg_presmooth(MgHost<T> *m, T H0c, T H0s, cudaStream_t s);  // opens every solve
+template <typename T>
 int mg_kernels_per_cycle(const MgHost<T> *m);
 template <typename T>
 int mg_levels(const MgHost<T> *m);

@@ -36,8 +36,8 @@ __global__ void __launch_bounds__(256) phase_kernel(Phys<T> P, const void *gv, T
             c->max_iter = pc.max_iter;
             c->keep_going = 1;
             c->blocks_done = 0u;
-            c->mode = 0;
-            c->smooth_left = 1;
+            c->mode = 1;         // the opening sweeps count as a lattice-sweep cycle
+            c->smooth_left = 0;  // ... and use up the sweep allowance
             c->twogrid_left = 2;
         }
         if (pc.step) {

@@ -38,7 +38,8 @@ constexpr int CTA_THREADS = 1024;
 constexpr int NU_PRE = 2, NU_POST = 2, NU_FINE = 2;  // grid-wide levels: V(2,2); lattice: V(0,2)
 constexpr int NU_CTA = 1, NU_COARSEST = 8;           // single-block levels: V(1,1)
 constexpr int MIN_COARSE = 100;                      // coarsening stops at this many cells
-// Cheaper cycles tried before a V-cycle: NU_SMOOTH_ONLY lattice sweeps when the
+// Every solve opens with NU_SMOOTH_ONLY lattice sweeps (no residual check
+// before them). Cheaper cycles tried before a V-cycle: lattice sweeps when the
 // starting residual is within SMOOTH_RATIO of the tolerance (once per solve),
 // else a two-grid cycle (NU_TWOGRID sweeps on level 1, at most twice per solve).
 // The residual changes between time steps are local, so both usually suffice
@@ -224,9 +225,11 @@ __device__ void cycle_close(MgCtl *ctl);
 // block to finish closes the cycle.
 template <typename T>
 __global__ void __launch_bounds__(SX *SY) smooth0(Level<T> L0, Level<T> L1, int add_coarse,
-                                                  int sweeps, T H0c, T H0s, MgCtl *ctl) {
+                                                  int sweeps, T H0c, T H0s, MgCtl *ctl,
+                                                  int first) {
     const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
-    if (cycle_skip(ctl)) return;
+    // first: the sweeps that open a solve (no residual known yet)
+    if (first ? (ctl->done || ctl->iter >= ctl->max_iter) : cycle_skip(ctl)) return;
     __shared__ T sp[SY + 2][SX + 2];
     __shared__ T sk[SY + 2][SX + 2];
     const int nx = L0.nx, ny = L0.ny, pitch = L0.pitch;
@@ -816,7 +819,8 @@ void mg_cycle_rest(MgHost<T> *m, T H0c, T H0s, cudaStream_t s) {
     coarse_cta<T><<<1, CTA_THREADS, m->cta_smem, s>>>(m->d_lv, m->lc, m->nl, m->ctl);
     for (int l = m->lc - 1; l >= 1; l--)
         fv_smooth<T, 1><<<g2(lv[l].nx, lv[l].ny, bs), bs, 0, s>>>(lv[l], lv[l + 1], NU_POST, m->ctl);
-    smooth0<T><<<g2(lv[0].nx, lv[0].ny, bs), bs, 0, s>>>(lv[0], lv[1], 1, NU_FINE, H0c, H0s, m->ctl);
+    smooth0<T><<<g2(lv[0].nx, lv[0].ny, bs), bs, 0, s>>>(lv[0], lv[1], 1, NU_FINE, H0c, H0s, m->ctl,
+                                                          0);
 }
 
 template <typename T>
@@ -824,7 +828,15 @@ void mg_cycle_smooth(MgHost<T> *m, T H0c, T H0s, cudaStream_t s) {
     dim3 bs(SX, SY);
     const std::vector<Level<T>> &lv = m->lv;
     smooth0<T><<<g2(lv[0].nx, lv[0].ny, bs), bs, 0, s>>>(lv[0], lv[1], 0, NU_SMOOTH_ONLY, H0c, H0s,
-                                                          m->ctl);
+                                                          m->ctl, 0);
+}
+
+template <typename T>
+void mg_presmooth(MgHost<T> *m, T H0c, T H0s, cudaStream_t s) {
+    dim3 bs(SX, SY);
+    const std::vector<Level<T>> &lv = m->lv;
+    smooth0<T><<<g2(lv[0].nx, lv[0].ny, bs), bs, 0, s>>>(lv[0], lv[1], 0, NU_SMOOTH_ONLY, H0c, H0s,
+                                                          m->ctl, 1);
 }
 
 template <typename T>
@@ -832,7 +844,8 @@ void mg_cycle_twogrid(MgHost<T> *m, T H0c, T H0s, cudaStream_t s) {
     dim3 bs(SX, SY);
     const std::vector<Level<T>> &lv = m->lv;
     fv_smooth<T, 2><<<g2(lv[1].nx, lv[1].ny, bs), bs, 0, s>>>(lv[1], lv[1], NU_TWOGRID, m->ctl);
-    smooth0<T><<<g2(lv[0].nx, lv[0].ny, bs), bs, 0, s>>>(lv[0], lv[1], 1, NU_FINE, H0c, H0s, m->ctl);
+    smooth0<T><<<g2(lv[0].nx, lv[0].ny, bs), bs, 0, s>>>(lv[0], lv[1], 1, NU_FINE, H0c, H0s, m->ctl,
+                                                          0);
 }
 
 template <typename T>
@@ -851,6 +864,7 @@ int mg_levels(const MgHost<T> *m) { return m->nl; }
     template void mg_cycle_rest<T>(MgHost<T> *, T, T, cudaStream_t);                             \
     template void mg_cycle_smooth<T>(MgHost<T> *, T, T, cudaStream_t);                           \
     template void mg_cycle_twogrid<T>(MgHost<T> *, T, T, cudaStream_t);                          \
+    template void mg_presmooth<T>(MgHost<T> *, T, T, cudaStream_t);                              \
     template int mg_kernels_per_cycle<T>(const MgHost<T> *);                                    \
     template int mg_levels<T>(const MgHost<T> *);
 FCD_MG_INST(float)
