@@ -174,6 +174,27 @@ fcd_status fcd_last_step_profile(fcd_ctx *ctx, double *ms4);
 /* Reason of the last failure on ctx; with ctx == NULL, of the last failed
  * fcd_create on the calling thread. */
 const char *fcd_last_error(const fcd_ctx *ctx);
+
+/* Observables of a caller's population buffer with no device allocation.
+ * The paper has no counterpart: this serves callers that cannot allocate
+ * device memory (another framework owns the memory budget, cudaMalloc/cudaFree
+ * would synchronise a latency-critical loop, or the memory plan is fixed in
+ * advance). g: device pointer to the phase-field populations in the FP64
+ * exchange layout (18*nx*ny doubles, g[i][a][y][x]); nx >= 4, ny >= 2,
+ * nx <= 16384 and nx*ny <= 524288, else FCD_EINVAL with the reason on stderr.
+ * Fills mass, centroids, extents, T_o, T_i and the breakup fields of the
+ * given state (b_step = 0 if the core touches the carrier in it, else -1);
+ * step, t_star and the solver fields are 0. Work runs on cuda_stream (a
+ * cudaStream_t; NULL = legacy default stream) and the call synchronises it.
+ * Scratch: one 9.6 MiB device array inside the library, reserved on every
+ * GPU that loads it until the process exits; its device address is looked up
+ * (cudaGetSymbolAddress) by the first call on each device, so make that first
+ * call before any stream capture. All calls share that array: calls that may
+ * overlap on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller. Allocates nothing: no cudaMalloc, cudaFree or
+ * allocating library routine. */
+fcd_status fcd_observe_populations_noalloc(const double *g, int nx, int ny, void *cuda_stream,
+                                           fcd_obs *out);
 void fcd_destroy(fcd_ctx *ctx);
 
 #ifdef __cplusplus

@@ -78,6 +78,8 @@ _SIGS = {
     "fcd_set_profiling": (C.c_int, [C.c_void_p, C.c_int]),
     "fcd_last_step_profile": (C.c_int, [C.c_void_p, DP]),
     "fcd_last_error": (C.c_char_p, [C.c_void_p]),
+    "fcd_observe_populations_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p,
+                                                   C.POINTER(fcd_obs)]),
     "fcd_destroy": (None, [C.c_void_p]),
 }
 

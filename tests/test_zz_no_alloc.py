@@ -1,0 +1,56 @@
+"""The allocation-free observables entry point (collected last on purpose).
+
+fcd_observe_populations_noalloc exists for callers that cannot allocate
+device memory; it must give the same observables as fcd_observables on the
+same state, call after call, while its scratch lives in one static device
+array that every call reuses.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from paper_2410_11129_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+KEYS = ("T_o", "T_i", "lx_o", "ly_o", "lx_i", "ly_i", "xc_core", "yc_core", "xc_shell",
+        "yc_shell")
+
+
+def test_noalloc_observables_match_context_twice():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2410_11129_gb300 import fcd
+    L = fcd.load()
+    cfg = W.small(nx=96, ny=40, r1=6.0, r2=12.0, xc=30.0, xi=4.0, Bo_m=2.0, ferro="shell",
+                  mag_tol=1e-10, mag_max_iter=300)
+    ch = fcd.Channel(dict(cfg, precision="fp64"))
+    stream = torch.cuda.current_stream()
+    for _ in range(2):  # two calls in a row: the shared scratch is reused
+        ch.step(40)
+        ref = ch.observe()
+        f, g, psi = ch.populations()
+        g_dev = torch.from_numpy(g).to("cuda")
+        out = fcd.fcd_obs()
+        st = L.fcd_observe_populations_noalloc(C.c_void_p(g_dev.data_ptr()), ch.nx, ch.ny,
+                                                C.c_void_p(stream.cuda_stream), C.byref(out))
+        assert st == fcd.FCD_OK
+        got = out.as_dict()
+        for k in KEYS:
+            assert abs(got[k] - ref[k]) <= 1e-12 * max(1.0, abs(ref[k])), (k, got[k], ref[k])
+        for i in range(3):
+            assert abs(got["mass"][i] - ref["mass"][i]) <= 1e-12 * abs(ref["mass"][i])
+        if got["breakup"]:  # a touch in this state implies the context recorded one
+            assert ref["breakup"] == 1
+    ch.close()
+
+
+def test_noalloc_rejects_oversized_lattice():
+    from paper_2410_11129_gb300 import fcd
+    L = fcd.load()
+    out = fcd.fcd_obs()
+    dummy = C.c_void_p(1)  # never dereferenced: the size check comes first
+    assert L.fcd_observe_populations_noalloc(dummy, 20000, 40, None, C.byref(out)) == fcd.FCD_EINVAL
+    assert L.fcd_observe_populations_noalloc(dummy, 1024, 1024, None, C.byref(out)) == fcd.FCD_EINVAL
+    assert L.fcd_observe_populations_noalloc(None, 64, 32, None, C.byref(out)) == fcd.FCD_EINVAL
