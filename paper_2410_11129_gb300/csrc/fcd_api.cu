@@ -53,7 +53,8 @@ struct Derived {
 static const char *derive(const fcd_params *p, Derived *d) {
     if (p->nx < 4 || (p->nx & 1)) return "nx must be even and >= 4";
     if (p->ny < 2) return "ny must be >= 2";
-    if ((long long)p->nx * p->ny > (1ll << 31) - 1) return "nx*ny exceeds 2^31-1";
+    if (27ll * ((p->nx + 31) / 32 * 32) * p->ny > (1ll << 31) - 1)
+        return "lattice too large: 27 population planes must index within 2^31 elements";
     for (int i = 0; i < 3; i++) {
         if (!(p->rho[i] > 0)) return "densities must be positive";
         if (!(p->nu[i] > 0)) return "viscosities must be positive";

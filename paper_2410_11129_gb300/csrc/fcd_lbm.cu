@@ -122,9 +122,9 @@ __global__ void __launch_bounds__(TX *TY) collide_kernel(LbmArgs<T> A) {
     if constexpr (EARLY) {
         if (live) {
 #pragma unroll
-            for (int a = 0; a < 9; a++) fpre[a] = __ldg(fs + a * ps + n);
+            for (int a = 0; a < 9; a++) fpre[a] = __ldg(fs + (a * (int)ps + (int)n));
 #pragma unroll
-            for (int a = 0; a < 18; a++) gpre[a] = __ldg(gs + a * ps + n);
+            for (int a = 0; a < 18; a++) gpre[a] = __ldg(gs + (a * (int)ps + (int)n));
         }
     }
     const T *psi = A.ctl->cur ? A.psi1 : A.psi0;
@@ -260,29 +260,42 @@ __global__ void __launch_bounds__(TX *TY) collide_kernel(LbmArgs<T> A) {
         }
     }
 
+    // Push streaming: 32-bit offsets (27 planes fit in 2^31 elements, checked at
+    // create), x-neighbour deltas with the periodic seam folded in, and wall
+    // flags that are uniform across a warp (a warp is one tile row).
+    const int n32 = y * pitch + x, ps32 = (int)ps;
+    const int dxp = (x == nx - 1) ? 1 - nx : 1, dxm = (x == 0) ? nx - 1 : -1;
+    const bool top = y == ny - 1, bot = y == 0;
+    auto dest = [&](int a) {
+        return n32 + cy(a) * pitch + (cx(a) > 0 ? dxp : (cx(a) < 0 ? dxm : 0));
+    };
+    auto walled = [&](int a) { return (cy(a) > 0 && top) || (cy(a) < 0 && bot); };
+
+    // Deviation of the equilibria from rest, D_a = 3 e.u + 4.5 (e.u)^2 - 1.5 u.u:
+    // f^eq = w (p* + D) (Eq. 16), Gamma = w (1 + D) (Eq. 18).
+    T dev[9];
+#pragma unroll
+    for (int a = 0; a < 9; a++) {
+        const T eu = T(cx(a)) * ux + T(cy(a)) * uy;
+        dev[a] = T(3) * eu + T(4.5) * eu * eu - uu;
+    }
+
     // MRT collision in closed form and push streaming of f.
     S *fd = static_cast<S *>(A.f_dst);
     const T dxx = mpxx - (ux * ux - uy * uy);
     const T dxy = mpxy - ux * uy;
     const T rel = (T(1) - snu) * T(0.25);
     const T fr = T(3) / rho;
-    const T Ftx = Fx * fr, Fty = Fy * fr;
+    const T Ftx = T(0.5) * Fx * fr, Fty = T(0.5) * Fy * fr;
 #pragma unroll
     for (int a = 0; a < 9; a++) {
         const T w = wgt<T>(a);
-        const T eu = T(cx(a)) * ux + T(cy(a)) * uy;
-        T v = w * (pst + T(3) * eu + T(4.5) * eu * eu - uu);
-        v += T(0.5) * w * (T(cx(a)) * Ftx + T(cy(a)) * Fty);
+        T v = w * ((pst + dev[a]) + (T(cx(a)) * Ftx + T(cy(a)) * Fty));
         const T rxx = (a == 1 || a == 3) ? T(1) : ((a == 2 || a == 4) ? T(-1) : T(0));
         const T rxy = (a == 5 || a == 7) ? T(1) : ((a == 6 || a == 8) ? T(-1) : T(0));
         v += rel * (rxx * dxx + rxy * dxy);
-        int xn = x + cx(a);
-        xn = xn < 0 ? nx - 1 : (xn >= nx ? 0 : xn);
-        int yn = y + cy(a);
-        if (yn >= 0 && yn < ny)
-            fd[a * ps + (long long)yn * pitch + xn] = S(v + f_off<MODE, T>(a));
-        else
-            fd[opp(a) * ps + n] = S(v + f_off<MODE, T>(opp(a)));
+        if (walled(a)) fd[opp(a) * ps32 + n32] = S(v + f_off<MODE, T>(opp(a)));
+        else fd[a * ps32 + dest(a)] = S(v + f_off<MODE, T>(a));
     }
 
     // Phase fields (Eqs. 29-31): g* = (1 - om) g + om phi Gamma + (1 - om/2) F^phi,
@@ -311,19 +324,12 @@ __global__ void __launch_bounds__(TX *TY) collide_kernel(LbmArgs<T> A) {
 #pragma unroll
         for (int a = 0; a < 9; a++) {
             const T w = wgt<T>(a);
-            const T eu = T(cx(a)) * ux + T(cy(a)) * uy;
-            const T gam = w * (T(1) + T(3) * eu + T(4.5) * eu * eu - uu);
             T gv;
             if constexpr (EARLY) gv = T(gpre[i * 9 + a]) - g_off<MODE, T>(a);
-            else gv = T(gs[(i * 9 + a) * ps + n]) - g_off<MODE, T>(a);
-            const T v = P.keep_phi * gv + ophi * gam + w * (T(cx(a)) * sqx + T(cy(a)) * sqy);
-            int xn = x + cx(a);
-            xn = xn < 0 ? nx - 1 : (xn >= nx ? 0 : xn);
-            int yn = y + cy(a);
-            if (yn >= 0 && yn < ny)
-                gd[(i * 9 + a) * ps + (long long)yn * pitch + xn] = S(v + g_off<MODE, T>(a));
-            else
-                gd[(i * 9 + opp(a)) * ps + n] = S(v + g_off<MODE, T>(opp(a)));
+            else gv = T(gs[(i * 9 + a) * ps32 + n32]) - g_off<MODE, T>(a);
+            const T v = P.keep_phi * gv + w * (ophi * (T(1) + dev[a]) + (T(cx(a)) * sqx + T(cy(a)) * sqy));
+            if (walled(a)) gd[(i * 9 + opp(a)) * ps32 + n32] = S(v + g_off<MODE, T>(opp(a)));
+            else gd[(i * 9 + a) * ps32 + dest(a)] = S(v + g_off<MODE, T>(a));
         }
     }
 }
