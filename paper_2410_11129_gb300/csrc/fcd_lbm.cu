@@ -72,6 +72,13 @@ __global__ void __launch_bounds__(256) phase_kernel(Phys<T> P, const void *gv, T
 }
 
 // ---------------------------------------------------------------- collide
+// Division inside the collide kernel: IEEE for FP64; the FP32 forms use the
+// fast single-precision divide (about 2 ulp), well inside their 1e-4 budget.
+template <typename T>
+__device__ __forceinline__ T cdiv(T a, T b) { return a / b; }
+template <>
+__device__ __forceinline__ float cdiv<float>(float a, float b) { return __fdividef(a, b); }
+
 template <typename T>
 struct Stencil {
     T c, e, w, n, s, ne, nw, sw, se;
@@ -101,7 +108,7 @@ struct Stencil {
 };
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(TX *TY) collide_kernel(LbmArgs<T> A) {
+__global__ void __launch_bounds__(TX *TY, (MODE == MODE_FP64 ? 1 : 4)) collide_kernel(LbmArgs<T> A) {
     using S = typename StoreT<MODE>::type;
     __shared__ T s1[TY + 2][TX + 2], s2[TY + 2][TX + 2], sr[TY + 2][TX + 2], sp[TY + 2][TX + 2];
     const Phys<T> &P = A.P;
@@ -188,7 +195,7 @@ __global__ void __launch_bounds__(TX *TY) collide_kernel(LbmArgs<T> A) {
     // Kelvin force F_m = -(1/2) |H|^2 grad chi (Eq. 7); grad chi by Eq. 9 with
     // grad phi_3 = -(grad phi_1 + grad phi_2); H = H0 e_alpha - grad psi' (Eq. 5).
     {
-        const T kk = T(1) / (P.ik[0] * h1 + P.ik[1] * h2 + P.ik[2] * h3);
+        const T kk = cdiv(T(1), P.ik[0] * h1 + P.ik[1] * h2 + P.ik[2] * h3);
         const T gcx = -kk * kk * (P.dk1 * g1x + P.dk2 * g2x);
         const T gcy = -kk * kk * (P.dk1 * g1y + P.dk2 * g2y);
         const T Hx = P.H0c - dpx, Hy = P.H0s - dpy;
@@ -215,10 +222,10 @@ __global__ void __launch_bounds__(TX *TY) collide_kernel(LbmArgs<T> A) {
     // Pressure (F_p = -(p/rho) grad rho with p = rho c_s^2 p*) and driving force.
     Fx += -pst * T(1.0 / 3.0) * grx + P.G;
     Fy += -pst * T(1.0 / 3.0) * gry;
-    const T half_inv_rho = T(0.5) / rho;
+    const T inv_rho = cdiv(T(1), rho), half_inv_rho = T(0.5) * inv_rho;
     const T upx = jx + Fx * half_inv_rho, upy = jy + Fy * half_inv_rho;
     const T tau = P.tau[0] * h1 + P.tau[1] * h2 + P.tau[2] * h3;
-    const T snu = T(1) / (T(0.5) + tau);
+    const T snu = cdiv(T(1), T(0.5) + tau);
     // Viscous force from the non-equilibrium stress (moments of f - f^eq(p*, u')):
     // Pi = (1/6) m_e + (1/2) s_nu m_pxx on the diagonal, s_nu m_pxy off it.
     {
@@ -285,7 +292,7 @@ __global__ void __launch_bounds__(TX *TY) collide_kernel(LbmArgs<T> A) {
     const T dxx = mpxx - (ux * ux - uy * uy);
     const T dxy = mpxy - ux * uy;
     const T rel = (T(1) - snu) * T(0.25);
-    const T fr = T(3) / rho;
+    const T fr = T(3) * inv_rho;
     const T Ftx = T(0.5) * Fx * fr, Fty = T(0.5) * Fy * fr;
 #pragma unroll
     for (int a = 0; a < 9; a++) {
@@ -305,9 +312,9 @@ __global__ void __launch_bounds__(TX *TY) collide_kernel(LbmArgs<T> A) {
         const T t1 = P.four_over_xi * h1 * (T(1) - h1);
         const T t2 = P.four_over_xi * h2 * (T(1) - h2);
         const T t3 = P.four_over_xi * h3 * (T(1) - h3);
-        const T i1 = t1 / (sqrt(g1x * g1x + g1y * g1y) + P.eps_n);
-        const T i2 = t2 / (sqrt(g2x * g2x + g2y * g2y) + P.eps_n);
-        const T i3 = t3 / (sqrt(g3x * g3x + g3y * g3y) + P.eps_n);
+        const T i1 = cdiv(t1, sqrt(g1x * g1x + g1y * g1y) + P.eps_n);
+        const T i2 = cdiv(t2, sqrt(g2x * g2x + g2y * g2y) + P.eps_n);
+        const T i3 = cdiv(t3, sqrt(g3x * g3x + g3y * g3y) + P.eps_n);
         const T mx = (i1 * g1x + i2 * g2x + i3 * g3x) * T(1.0 / 3.0);
         const T my = (i1 * g1y + i2 * g2y + i3 * g3y) * T(1.0 / 3.0);
         qx[0] = i1 * g1x - mx;
