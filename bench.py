@@ -27,6 +27,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "coupled-step MLUPS vs HBM roofline; plain vs batched/adjoint at stated error"
+DEFAULT_WORKLOAD = "1600x200"
 UNIT = "MLUPS"
 FALLBACK_HBM_GBS = 6800.0
 # Algorithmic bytes per node of one collide-stream launch in FP32: f read+write
@@ -36,6 +37,15 @@ COLLIDE_BYTES_PER_NODE_F32 = 240
 # DRAM bytes per collide launch measured by ncu on this workload, keyed by the
 # hash of the kernel source it was taken on (null once the source changes).
 NCU_TRAFFIC = {}
+
+
+def _workloads():
+    from paper_2410_11129_gb300 import workloads as W
+    return {"1600x200": W.C2, "200x40": W.C1, "2400x300": W.C3, "800x100": W.C5,
+            "9600x1200": W.ROOF}
+
+
+WORKLOADS = _workloads()
 
 
 def kernel_source_hash():
@@ -185,7 +195,7 @@ def run_ours(args):
     from paper_2410_11129_gb300 import fcd
     from paper_2410_11129_gb300 import workloads as W
 
-    cfg = dict(W.C2)
+    cfg = dict(WORKLOADS[args.workload])
     N = cfg["nx"] * cfg["ny"]
     ch = fcd.Channel(cfg)
     ch.set_profiling(True)
@@ -261,21 +271,23 @@ def run_ours(args):
 
     peak, peak_kind = measured_peak()
     coll_ms = stage["collide"] / args.steps
-    achieved = COLLIDE_BYTES_PER_NODE_F32 * N / (coll_ms * 1e-3) / 1e9
+    bpn = COLLIDE_BYTES_PER_NODE_F32 * (2 if cfg["precision"] == "fp64" else 1)
+    achieved = bpn * N / (coll_ms * 1e-3) / 1e9
     h = kernel_source_hash()
     traffic = NCU_TRAFFIC.get(h)
-    roofline = {"bound": "hbm", "kernel": "collide_kernel<float, offset-free FP32>",
+    roofline = {"bound": "hbm", "kernel": "collide_kernel (%s)" % cfg["precision"],
                 "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "algorithmic_bytes_per_launch": COLLIDE_BYTES_PER_NODE_F32 * N,
-                "launch_ms": coll_ms}
+                "frac": achieved / peak,
+                "traffic": traffic if args.workload == DEFAULT_WORKLOAD else None,
+                "algorithmic_bytes_per_launch": bpn * N, "launch_ms": coll_ms}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if cfg["precision"] == "fp64" else "f32", "data": "synthetic",
         "config": {"workload": cfg["name"], "nx": cfg["nx"], "ny": cfg["ny"],
                    "precision": cfg["precision"], "mag_tol": cfg["mag_tol"],
-                   "l2": "256 MiB buffer written between timed steps (state is 69 MB < L2)",
+                   "l2": "256 MiB buffer written between timed steps",
                    "parallelism": "replicas x%d" % ws},
         "stage_ms_per_step": {k: v / args.steps for k, v in stage.items()},
         "roofline": roofline,
@@ -285,7 +297,7 @@ def run_ours(args):
         "solver_per_step": {k: (st1[k] - st0[k]) / args.steps for k in st0},
         "clocks": clocks,
     }
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.workload == DEFAULT_WORKLOAD:
         v, n, dt = oracle_rate(cfg, min_seconds=10.0, max_steps=30)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": "%s, %d whole-grid FP64 oracle steps (%.1f s) after "
@@ -305,6 +317,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS),
+                    help="the default is the benchmark workload; the others are extra data points")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

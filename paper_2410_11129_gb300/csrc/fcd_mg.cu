@@ -230,28 +230,24 @@ __global__ void __launch_bounds__(256) resid0_restrict(Level<T> L0, Level<T> L1,
 __device__ void cycle_close(MgCtl *ctl);
 
 // Level-0 block Gauss-Seidel after adding the coarse correction; the last
-// block to finish closes the cycle. A 256-thread block smooths a 64 x 16
-// lattice tile: each thread owns a 2 x 2 cell block, i.e. one cell of each of
-// the four colours, so every thread updates one cell in every colour pass.
-constexpr int QX = 64, QY = 16;
-
+// block to finish closes the cycle.
 template <typename T>
-__global__ void __launch_bounds__(256) smooth0(Level<T> L0, Level<T> L1, int add_coarse,
-                                               int sweeps, T H0c, T H0s, MgCtl *ctl, int first) {
+__global__ void __launch_bounds__(SX *SY) smooth0(Level<T> L0, Level<T> L1, int add_coarse,
+                                                  int sweeps, T H0c, T H0s, MgCtl *ctl,
+                                                  int first) {
     const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
     // first: the sweeps that open a solve (no residual known yet)
     if (first ? (ctl->done || ctl->iter >= ctl->max_iter) : cycle_skip(ctl)) return;
-    __shared__ T sp[QY + 2][QX + 2];
-    __shared__ T sk[QY + 2][QX + 2];
-    __shared__ ProlongTile<T, QX + 2, QY + 2> pt;
+    __shared__ T sp[SY + 2][SX + 2];
+    __shared__ T sk[SY + 2][SX + 2];
     const int nx = L0.nx, ny = L0.ny, pitch = L0.pitch;
-    const int x0 = blockIdx.x * QX, y0 = blockIdx.y * QY;
-    const int tid = threadIdx.y * 32 + threadIdx.x;
+    const int x0 = blockIdx.x * SX, y0 = blockIdx.y * SY;
     const T *src = ctl->cur ? L0.r : L0.e;
     T *dst = ctl->cur ? L0.e : L0.r;
+    __shared__ ProlongTile<T, SX + 2, SY + 2> pt;
     if (add_coarse) prolong_tile_load(pt, L0, x0 - 1, y0 - 1);
-    for (int t = tid; t < (QX + 2) * (QY + 2); t += 256) {
-        const int lx = t % (QX + 2), ly = t / (QX + 2);
+    for (int t = threadIdx.y * SX + threadIdx.x; t < (SX + 2) * (SY + 2); t += SX * SY) {
+        const int lx = t % (SX + 2), ly = t / (SX + 2);
         int gx = x0 - 1 + lx;
         if (gx < 0) gx += nx;
         while (gx >= nx) gx -= nx;
@@ -262,41 +258,29 @@ __global__ void __launch_bounds__(256) smooth0(Level<T> L0, Level<T> L1, int add
     }
     __syncthreads();
     if (add_coarse) {  // ghost rows are never read: the mirror is used instead
-        for (int t = tid; t < (QX + 2) * (QY + 2); t += 256) {
-            const int lx = t % (QX + 2), ly = t / (QX + 2), gy = y0 - 1 + ly;
+        for (int t = threadIdx.y * SX + threadIdx.x; t < (SX + 2) * (SY + 2); t += SX * SY) {
+            const int lx = t % (SX + 2), ly = t / (SX + 2), gy = y0 - 1 + ly;
             if (gy >= 0 && gy < ny) sp[ly][lx] += prolong_at(pt, L1, lx, ly);
         }
         __syncthreads();
     }
-    // owned cells: colour c = i + 2 j at local (2 tx + 1 + i, 2 ty + 1 + j)
-    Node9<T> nd[4];
-    bool own[4];
-#pragma unroll
-    for (int c = 0; c < 4; c++) {
-        const int i = c & 1, j = c >> 1;
-        const int lx = 2 * threadIdx.x + 1 + i, ly = 2 * threadIdx.y + 1 + j;
-        const int x = x0 + lx - 1, y = y0 + ly - 1;
-        own[c] = x < nx && y < ny;
+    const int lx = threadIdx.x + 1, ly = threadIdx.y + 1;
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    const bool own = x < nx && y < ny;
+    Node9<T> nd;
+    if (own) {
         auto kat = [&](int dx, int dy) { return sk[ly + dy][lx + dx]; };
-        if (own[c]) nd[c] = node9<T>(kat, y, ny, H0c, H0s);
+        nd = node9<T>(kat, y, ny, H0c, H0s);
     }
+    const int colour = (x & 1) + 2 * (y & 1);
+    auto pat = [&](int dx, int dy) { return sp[ly + dy][lx + dx]; };
     for (int s = 0; s < sweeps; s++) {
-#pragma unroll
         for (int c = 0; c < 4; c++) {
-            const int i = c & 1, j = c >> 1;
-            const int lx = 2 * threadIdx.x + 1 + i, ly = 2 * threadIdx.y + 1 + j;
-            const int y = y0 + ly - 1;
-            auto pat = [&](int dx, int dy) { return sp[ly + dy][lx + dx]; };
-            if (own[c]) sp[ly][lx] = (off9<T>(nd[c], pat, y, ny) - nd[c].b) / nd[c].diag;
+            if (own && colour == c) sp[ly][lx] = (off9<T>(nd, pat, y, ny) - nd.b) / nd.diag;
             __syncthreads();
         }
     }
-#pragma unroll
-    for (int c = 0; c < 4; c++) {
-        const int i = c & 1, j = c >> 1;
-        const int lx = 2 * threadIdx.x + 1 + i, ly = 2 * threadIdx.y + 1 + j;
-        if (own[c]) dst[(long long)(y0 + ly - 1) * pitch + x0 + lx - 1] = sp[ly][lx];
-    }
+    if (own) dst[(long long)y * pitch + x] = sp[ly][lx];
     __syncthreads();
     if (lead) {
         __threadfence();
@@ -843,7 +827,7 @@ void mg_cycle_rest(MgHost<T> *m, T H0c, T H0s, cudaStream_t s) {
     coarse_cta<T><<<1, CTA_THREADS, m->cta_smem, s>>>(m->d_lv, m->lc, m->nl, m->ctl);
     for (int l = m->lc - 1; l >= 1; l--)
         fv_smooth<T, 1><<<g2(lv[l].nx, lv[l].ny, bs), bs, 0, s>>>(lv[l], lv[l + 1], NU_POST, m->ctl);
-    smooth0<T><<<g2(lv[0].nx, lv[0].ny, dim3(QX, QY)), bs, 0, s>>>(lv[0], lv[1], 1, NU_FINE, H0c, H0s, m->ctl,
+    smooth0<T><<<g2(lv[0].nx, lv[0].ny, bs), bs, 0, s>>>(lv[0], lv[1], 1, NU_FINE, H0c, H0s, m->ctl,
                                                           0);
 }
 
@@ -851,7 +835,7 @@ template <typename T>
 void mg_cycle_smooth(MgHost<T> *m, T H0c, T H0s, cudaStream_t s) {
     dim3 bs(SX, SY);
     const std::vector<Level<T>> &lv = m->lv;
-    smooth0<T><<<g2(lv[0].nx, lv[0].ny, dim3(QX, QY)), bs, 0, s>>>(lv[0], lv[1], 0, NU_SMOOTH_ONLY, H0c, H0s,
+    smooth0<T><<<g2(lv[0].nx, lv[0].ny, bs), bs, 0, s>>>(lv[0], lv[1], 0, NU_SMOOTH_ONLY, H0c, H0s,
                                                           m->ctl, 0);
 }
 
@@ -859,7 +843,7 @@ template <typename T>
 void mg_presmooth(MgHost<T> *m, T H0c, T H0s, cudaStream_t s) {
     dim3 bs(SX, SY);
     const std::vector<Level<T>> &lv = m->lv;
-    smooth0<T><<<g2(lv[0].nx, lv[0].ny, dim3(QX, QY)), bs, 0, s>>>(lv[0], lv[1], 0, NU_SMOOTH_ONLY, H0c, H0s,
+    smooth0<T><<<g2(lv[0].nx, lv[0].ny, bs), bs, 0, s>>>(lv[0], lv[1], 0, NU_SMOOTH_ONLY, H0c, H0s,
                                                           m->ctl, 1);
 }
 
@@ -868,7 +852,7 @@ void mg_cycle_twogrid(MgHost<T> *m, T H0c, T H0s, cudaStream_t s) {
     dim3 bs(SX, SY);
     const std::vector<Level<T>> &lv = m->lv;
     fv_smooth<T, 2><<<g2(lv[1].nx, lv[1].ny, bs), bs, 0, s>>>(lv[1], lv[1], NU_TWOGRID, m->ctl);
-    smooth0<T><<<g2(lv[0].nx, lv[0].ny, dim3(QX, QY)), bs, 0, s>>>(lv[0], lv[1], 1, NU_FINE, H0c, H0s, m->ctl,
+    smooth0<T><<<g2(lv[0].nx, lv[0].ny, bs), bs, 0, s>>>(lv[0], lv[1], 1, NU_FINE, H0c, H0s, m->ctl,
                                                           0);
 }
 
