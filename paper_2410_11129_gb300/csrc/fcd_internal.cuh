@@ -78,6 +78,8 @@ struct Level {
     T *r;                     // scratch (level 0: second psi' buffer)
     const int *cx0, *cy0;     // children of cell I: parent columns cx0[I] .. cx0[I+1]-1
     const T *xc, *yc, *wx, *wy;
+    const T *ixe;             // 1 / (distance to the east centre), periodic
+    const T *iyn, *iys;       // 1 / (distance to the north / south centre or wall)
     T Lx, ylo, yhi;
     // prolongation of the next coarser level onto this one
     const int *px0, *px1, *py0, *py1;  // -1 in py* stands for the wall (value 0)

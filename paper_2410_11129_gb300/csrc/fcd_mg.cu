@@ -268,15 +268,17 @@ __global__ void __launch_bounds__(SX *SY) smooth0(Level<T> L0, Level<T> L1, int 
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
     const bool own = x < nx && y < ny;
     Node9<T> nd;
+    T inv_diag = T(0);
     if (own) {
         auto kat = [&](int dx, int dy) { return sk[ly + dy][lx + dx]; };
         nd = node9<T>(kat, y, ny, H0c, H0s);
+        inv_diag = T(1) / nd.diag;
     }
     const int colour = (x & 1) + 2 * (y & 1);
     auto pat = [&](int dx, int dy) { return sp[ly + dy][lx + dx]; };
     for (int s = 0; s < sweeps; s++) {
         for (int c = 0; c < 4; c++) {
-            if (own && colour == c) sp[ly][lx] = (off9<T>(nd, pat, y, ny) - nd.b) / nd.diag;
+            if (own && colour == c) sp[ly][lx] = (off9<T>(nd, pat, y, ny) - nd.b) * inv_diag;
             __syncthreads();
         }
     }
@@ -308,16 +310,12 @@ __device__ __forceinline__ FV<T> fv_coef(const Level<T> &L, int I, int J, KF kat
     const T k0 = kat(0, 0);
     f.ie = I + 1 == nx ? 0 : I + 1;
     f.iw = I == 0 ? nx - 1 : I - 1;
-    const T dxe = I + 1 == nx ? L.xc[0] + L.Lx - L.xc[I] : L.xc[I + 1] - L.xc[I];
-    const T dxw = I == 0 ? L.xc[0] + L.Lx - L.xc[nx - 1] : L.xc[I] - L.xc[I - 1];
-    f.te = T(0.5) * (k0 + kat(1, 0)) * L.wy[J] / dxe;
-    f.tw = T(0.5) * (k0 + kat(-1, 0)) * L.wy[J] / dxw;
+    f.te = T(0.5) * (k0 + kat(1, 0)) * L.wy[J] * L.ixe[I];
+    f.tw = T(0.5) * (k0 + kat(-1, 0)) * L.wy[J] * L.ixe[f.iw];
     f.hasn = J + 1 < ny;
     f.hass = J > 0;
-    f.tn = f.hasn ? T(0.5) * (k0 + kat(0, 1)) * L.wx[I] / (L.yc[J + 1] - L.yc[J])
-                  : k0 * L.wx[I] / (L.yhi - L.yc[J]);
-    f.ts = f.hass ? T(0.5) * (k0 + kat(0, -1)) * L.wx[I] / (L.yc[J] - L.yc[J - 1])
-                  : k0 * L.wx[I] / (L.yc[J] - L.ylo);
+    f.tn = (f.hasn ? T(0.5) * (k0 + kat(0, 1)) : k0) * L.wx[I] * L.iyn[J];
+    f.ts = (f.hass ? T(0.5) * (k0 + kat(0, -1)) : k0) * L.wx[I] * L.iys[J];
     return f;
 }
 
@@ -384,11 +382,11 @@ __global__ void __launch_bounds__(SX *SY) fv_smooth(Level<T> L, Level<T> C, int 
     const int I = x0 + threadIdx.x, J = y0 + threadIdx.y;
     const bool own = I < nx && J < ny;
     FV<T> f;
-    T dg = T(1), b = T(0);
+    T idg = T(0), b = T(0);
     if (own) {
         auto kat = [&](int dx, int dy) { return sk[ly + dy][lx + dx]; };
         f = fv_coef(L, I, J, kat);
-        dg = f.te + f.tw + f.tn + f.ts;
+        idg = T(1) / (f.te + f.tw + f.tn + f.ts);
         b = L.b[(long long)J * p + I];
     }
     const int colour = own ? fv_colour(I, J, nx) : -1;
@@ -399,7 +397,7 @@ __global__ void __launch_bounds__(SX *SY) fv_smooth(Level<T> L, Level<T> C, int 
                 T v = f.te * se[ly][lx + 1] + f.tw * se[ly][lx - 1];
                 if (f.hasn) v += f.tn * se[ly + 1][lx];
                 if (f.hass) v += f.ts * se[ly - 1][lx];
-                se[ly][lx] = (v - b) / dg;
+                se[ly][lx] = (v - b) * idg;
             }
             __syncthreads();
         }
@@ -424,7 +422,8 @@ __global__ void __launch_bounds__(256) fv_resid_restrict(Level<T> F, Level<T> C,
 }
 
 // ---- levels lc .. nl-1 inside one block, resident in shared memory.
-// Per level: e, b, k, te (east face), tn (north face, wall at the top), dg.
+// Per level: e, b, k, te (east face), tn (north face, wall at the top), and dg,
+// the reciprocal of the diagonal.
 constexpr int MAX_LEVELS = 24;
 constexpr int CTA_ARRAYS = 6;
 
@@ -453,7 +452,7 @@ __device__ __forceinline__ void cta_gs(const Level<T> &L, const CtaView<T> &V, i
                 T v = V.te[t] * V.e[J * nx + ie] + V.te[J * nx + iw] * V.e[J * nx + iw];
                 if (J + 1 < ny) v += V.tn[t] * V.e[t + nx];
                 if (J > 0) v += V.tn[t - nx] * V.e[t - nx];
-                V.e[t] = (v - V.b[t]) / V.dg[t];
+                V.e[t] = (v - V.b[t]) * V.dg[t];
             }
             if (warp_only) __syncwarp();
             else __syncthreads();
@@ -514,7 +513,7 @@ __global__ void __launch_bounds__(CTA_THREADS) coarse_cta(const Level<T> *lv, in
             const FV<T> f = fv_coef(C, I, J, kat);
             V.te[t] = f.te;
             V.tn[t] = f.tn;
-            V.dg[t] = f.te + f.tw + f.tn + f.ts;
+            V.dg[t] = T(1) / (f.te + f.tw + f.tn + f.ts);  // reciprocal of the diagonal
         }
     }
     __syncthreads();
@@ -534,7 +533,7 @@ __global__ void __launch_bounds__(CTA_THREADS) coarse_cta(const Level<T> *lv, in
                     T v = F.te[q] * F.e[j * fnx + ie] + F.te[j * fnx + iw] * F.e[j * fnx + iw];
                     if (j + 1 < fny) v += F.tn[q] * F.e[q + fnx];
                     if (j > 0) v += F.tn[q - fnx] * F.e[q - fnx];
-                    s += F.b[q] - (v - F.dg[q] * F.e[q]);
+                    s += F.b[q] - (v - F.e[q] / F.dg[q]);
                 }
             V.b[t] = s;
             V.e[t] = T(0);
@@ -776,6 +775,22 @@ MgHost<T> *mg_create(int nx, int ny, int pitch, T *k0, T *psiA, T *psiB, MgCtl *
         L.wx = up.put<T>(wx.data(), wx.size() * sizeof(T));
         L.yc = up.put<T>(yc.data(), yc.size() * sizeof(T));
         L.wy = up.put<T>(wy.data(), wy.size() * sizeof(T));
+        {  // inverse centre distances (periodic in x; walls at 0 and ny in y)
+            std::vector<T> ixe(L.nx), iyn(L.ny), iys(L.ny);
+            for (int i = 0; i < L.nx; i++) {
+                const double d = i + 1 == L.nx ? xcs[l][0] + nx - xcs[l][i] : xcs[l][i + 1] - xcs[l][i];
+                ixe[i] = T(1.0 / d);
+            }
+            for (int j = 0; j < L.ny; j++) {
+                const double dn = j + 1 < L.ny ? ycs[l][j + 1] - ycs[l][j] : double(ny) - ycs[l][j];
+                const double ds = j > 0 ? ycs[l][j] - ycs[l][j - 1] : ycs[l][j];
+                iyn[j] = T(1.0 / dn);
+                iys[j] = T(1.0 / ds);
+            }
+            L.ixe = up.put<T>(ixe.data(), ixe.size() * sizeof(T));
+            L.iyn = up.put<T>(iyn.data(), iyn.size() * sizeof(T));
+            L.iys = up.put<T>(iys.data(), iys.size() * sizeof(T));
+        }
         if (l + 1 < m->nl) {
             std::vector<int> a0, a1, b0, b1;
             std::vector<T> wa, wb;

@@ -65,8 +65,9 @@ C5 = dict(channel(800, 100, 15, 30, Ca=0.15, Bo_m=2.0, alpha_deg=0.0, ferro="she
           name="channel-800x100", steps=20000, precision="fp64")
 
 # L2-busting roofline channel: the 1600x200 physics on 9600x1200 (droplet x6).
+# The FP32 residual floor grows with the droplet (|psi'| ~ H0 r1): 1e-3 here.
 ROOF = dict(channel(9600, 1200, 180, 360, Ca=0.2, Bo_m=3.0, alpha_deg=90.0, ferro="core",
-                    chi_ferro=2.0, rho_r=2.0, nu_r=2.0, mag_tol=1e-4),
+                    chi_ferro=2.0, rho_r=2.0, nu_r=2.0, mag_tol=1e-3),
             name="channel-9600x1200-fp32", steps=200, precision="fp32")
 
 
