@@ -59,6 +59,15 @@ __device__ __forceinline__ bool cycle_skip(const MgCtl *c) {
     return c->done || norm_of(c) <= c->tolH0 || c->iter >= c->max_iter;
 }
 
+// cycle_skip evaluated once per block (the FP64 compare is costly on this GPU).
+__device__ __forceinline__ bool block_skip(const MgCtl *c, bool first = false) {
+    __shared__ int flag;
+    if (threadIdx.x == 0 && threadIdx.y == 0)
+        flag = first ? (c->done || c->iter >= c->max_iter) : cycle_skip(c);
+    __syncthreads();
+    return flag != 0;
+}
+
 __device__ __forceinline__ void atomic_max_nonneg(unsigned long long *p, double v) {
     atomicMax(p, (unsigned long long)__double_as_longlong(v));
 }
@@ -187,7 +196,7 @@ __global__ void __launch_bounds__(256) resid0_restrict(Level<T> L0, Level<T> L1,
     }
     __syncthreads();
     const int I = I0 + threadIdx.x, J = J0 + threadIdx.y;
-    double mx = 0.0;
+    T mxt = T(0);  // a max is exact in the compute type; only the reduction is FP64
     if (I < L1.nx && J < L1.ny) {
         T sum = T(0), ksum = T(0);
         auto child = [&](int i, int j) {
@@ -198,8 +207,8 @@ __global__ void __launch_bounds__(256) resid0_restrict(Level<T> L0, Level<T> L1,
             const T r = nd.b - (off9<T>(nd, pat, j, ny) - nd.diag * sp[ly][lx]);
             sum += r;
             ksum += sk[ly][lx];
-            const double ar = fabs((double)r);
-            mx = ar <= mx ? mx : (ar == ar ? ar : INFINITY);  // NaN counts as infinite
+            const T ar = fabs(r);
+            mxt = ar <= mxt ? mxt : (ar == ar ? ar : T(INFINITY));  // NaN counts as infinite
         };
         const int ia = L1.cx0[I], ib = L1.cx0[I + 1], ja = L1.cy0[J], jb = L1.cy0[J + 1];
         if (ib - ia == 2 && jb - ja == 2) {  // the common 2 x 2 merge, unrolled
@@ -214,7 +223,8 @@ __global__ void __launch_bounds__(256) resid0_restrict(Level<T> L0, Level<T> L1,
         L1.b[(long long)J * L1.pitch + I] = sum;
         L1.k[(long long)J * L1.pitch + I] = ksum / (L1.wx[I] * L1.wy[J]);  // unit lattice cells
     }
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    for (int o = 16; o > 0; o >>= 1) mxt = fmax(mxt, __shfl_xor_sync(0xffffffffu, mxt, o));
+    const double mx = (double)mxt;
     if ((threadIdx.x & 31) == 0 && mx > 0.0) atomic_max_nonneg(&ctl->norm_bits, mx);
     __syncthreads();
     if (lead) {  // the last block to finish sees the whole norm and decides the cycle
@@ -237,7 +247,7 @@ __global__ void __launch_bounds__(SX *SY) smooth0(Level<T> L0, Level<T> L1, int 
                                                   int first) {
     const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
     // first: the sweeps that open a solve (no residual known yet)
-    if (first ? (ctl->done || ctl->iter >= ctl->max_iter) : cycle_skip(ctl)) return;
+    if (block_skip(ctl, first != 0)) return;
     __shared__ T sp[SY + 2][SX + 2];
     __shared__ T sk[SY + 2][SX + 2];
     const int nx = L0.nx, ny = L0.ny, pitch = L0.pitch;
@@ -349,7 +359,7 @@ template <typename T, int KIND>
 __global__ void __launch_bounds__(SX *SY) fv_smooth(Level<T> L, Level<T> C, int sweeps,
                                                     MgCtl *ctl) {
     constexpr bool POST = KIND == 1;
-    if (cycle_skip(ctl)) return;
+    if (block_skip(ctl)) return;
     __shared__ T se[SY + 2][SX + 2];
     __shared__ T sk[SY + 2][SX + 2];
     const int nx = L.nx, ny = L.ny, p = L.pitch;
