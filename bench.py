@@ -128,6 +128,18 @@ def dist_env():
     return ws, rank, local
 
 
+def replica_throughput(total_ms, nodes, steps, ws, device=None):
+    """Whole-job throughput of independent replicas: every rank advanced its own
+    channel by `steps` steps; the job takes as long as the slowest rank."""
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return nodes * steps * ws / (total_ms * 1e-3) / 1e6, total_ms
+
+
 def oracle_rate(cfg, min_seconds, max_steps, warmup=1):
     """MLUPS of the FP64 C oracle (single thread) over a bounded sample."""
     import oracle
@@ -240,12 +252,7 @@ def run_ours(args):
     st1 = ch.solver_stats()
     obs = ch.observe(allow=(fcd.FCD_ENOCONV,))
     clocks = clk.stop()
-    total_ms = sum(step_ms)
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = N * args.steps * ws / (total_ms * 1e-3) / 1e6
+    value, total_ms = replica_throughput(sum(step_ms), N, args.steps, ws, dev)
 
     # End to end through the C ABI with host buffers: state in (h2d), one step,
     # state out (d2h), every step.
