@@ -25,6 +25,8 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# more hardware work queues, so that the streams of a batch run concurrently
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 METRIC = "coupled-step MLUPS vs HBM roofline; plain vs batched/adjoint at stated error"
 DEFAULT_WORKLOAD = "1600x200"
@@ -138,6 +140,49 @@ def replica_throughput(total_ms, nodes, steps, ws, device=None):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     return nodes * steps * ws / (total_ms * 1e-3) / 1e6, total_ms
+
+
+def measure_batched(steps, warmup):
+    """The 96-instance regime sweep (FP32, Bo_m x Ca x {core, shell}, lengths
+    800-2400 x 200): all instances advanced by fcd_batch_step (one stream and
+    graph set per instance) against looping the plain method over the same
+    instances on one stream, at the same tolerance. The 8 GB state exceeds L2."""
+    import torch
+    from paper_2410_11129_gb300 import fcd
+    from paper_2410_11129_gb300 import workloads as W
+    cfgs = [dict(c, precision="fp32") for c in W.regime_sweep()]
+    nodes = sum(c["nx"] * c["ny"] for c in cfgs)
+    stream = torch.cuda.current_stream()
+    batch = fcd.Batch(cfgs)
+    batch.step(warmup)
+    torch.cuda.synchronize()
+    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    batch.step(steps)
+    z.record(stream)
+    torch.cuda.synchronize()
+    t_batch = a.elapsed_time(z)
+    L = fcd.load()
+    for inst in batch.instances:  # the plain method: one instance after the other
+        L.fcd_set_stream(inst.h, stream.cuda_stream)
+    for inst in batch.instances:
+        inst.step(1)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(steps):
+        for inst in batch.instances:
+            inst.step(1)
+    z.record(stream)
+    torch.cuda.synchronize()
+    t_loop = a.elapsed_time(z)
+    obs = batch.observe(allow=(fcd.FCD_ENOCONV,))
+    batch.close()
+    v_b = nodes * steps / (t_batch * 1e-3) / 1e6
+    v_l = nodes * steps / (t_loop * 1e-3) / 1e6
+    return {"workload": "regime sweep, 96 channels 800-2400 x 200, fp32, seed 12345",
+            "nodes": nodes, "steps": steps, "mag_tol": cfgs[0]["mag_tol"],
+            "value": v_b, "looped_value": v_l, "unit": UNIT, "speedup": v_b / v_l,
+            "max_mag_resid": max(o["mag_resid"] for o in obs)}
 
 
 def oracle_rate(cfg, min_seconds, max_steps, warmup=1):
@@ -304,6 +349,8 @@ def run_ours(args):
         "solver_per_step": {k: (st1[k] - st0[k]) / args.steps for k in st0},
         "clocks": clocks,
     }
+    if args.batched_steps > 0 and args.workload == DEFAULT_WORKLOAD:
+        line["batched"] = measure_batched(args.batched_steps, 3)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.workload == DEFAULT_WORKLOAD:
         v, n, dt = oracle_rate(cfg, min_seconds=10.0, max_steps=30)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -324,6 +371,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batched-steps", type=int, default=10,
+                    help="steps of the batched-vs-looped regime sweep (0 skips it)")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS),
                     help="the default is the benchmark workload; the others are extra data points")
     args = ap.parse_args()

@@ -175,6 +175,30 @@ fcd_status fcd_last_step_profile(fcd_ctx *ctx, double *ms4);
  * fcd_create on the calling thread. */
 const char *fcd_last_error(const fcd_ctx *ctx);
 
+/* ---- Batched form: many independent channels (the Bo_m x Ca regime map of
+ * Sec. 3.7 is a grid of separate runs). Each instance is a full context with
+ * its own CUDA stream and captured step graphs; fcd_batch_step launches every
+ * instance's step on its own stream so that the latency-bound kernels of some
+ * instances overlap the bandwidth-bound collide-stream of others, then makes
+ * the batch's caller stream wait for all of them. Results are bit-identical
+ * to stepping each instance alone. */
+typedef struct fcd_batch fcd_batch;
+/* n parameter sets (instances may differ in every field, sizes included). */
+fcd_status fcd_batch_create(const fcd_params *params, int n, fcd_batch **out);
+/* Stream that fcd_batch_step orders itself after and joins into (default: legacy stream). */
+fcd_status fcd_batch_set_stream(fcd_batch *b, void *cuda_stream);
+/* Advance every instance by n steps (asynchronous, like fcd_step). */
+fcd_status fcd_batch_step(fcd_batch *b, long n);
+/* Observables of every instance into out[0..size-1] (synchronous); the first
+ * non-OK instance status is returned. */
+fcd_status fcd_batch_observables(fcd_batch *b, fcd_obs *out);
+int fcd_batch_size(const fcd_batch *b);
+/* Instance i (owned by the batch; use any fcd_* call on it, not fcd_destroy). */
+fcd_ctx *fcd_batch_instance(fcd_batch *b, int i);
+/* Reason of the last failure on b; with b == NULL, of the last failed create. */
+const char *fcd_batch_last_error(const fcd_batch *b);
+void fcd_batch_destroy(fcd_batch *b);
+
 /* Observables of a caller's population buffer with no device allocation.
  * The paper has no counterpart: this serves callers that cannot allocate
  * device memory (another framework owns the memory budget, cudaMalloc/cudaFree

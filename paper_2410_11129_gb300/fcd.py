@@ -80,6 +80,14 @@ _SIGS = {
     "fcd_last_error": (C.c_char_p, [C.c_void_p]),
     "fcd_observe_populations_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p,
                                                    C.POINTER(fcd_obs)]),
+    "fcd_batch_create": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),
+    "fcd_batch_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "fcd_batch_step": (C.c_int, [C.c_void_p, C.c_long]),
+    "fcd_batch_observables": (C.c_int, [C.c_void_p, C.POINTER(fcd_obs)]),
+    "fcd_batch_size": (C.c_int, [C.c_void_p]),
+    "fcd_batch_instance": (C.c_void_p, [C.c_void_p, C.c_int]),
+    "fcd_batch_last_error": (C.c_char_p, [C.c_void_p]),
+    "fcd_batch_destroy": (None, [C.c_void_p]),
     "fcd_destroy": (None, [C.c_void_p]),
 }
 
@@ -258,6 +266,63 @@ class Channel:
     def close(self):
         if getattr(self, "h", None):
             load().fcd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _Instance(Channel):
+    """A context owned by a Batch (not destroyed on its own)."""
+
+    def __init__(self, handle, cfg):
+        self.h = C.c_void_p(handle)
+        self.cfg = dict(cfg)
+        self.params = make_params(cfg)
+        self.nx, self.ny = self.params.nx, self.params.ny
+
+    def close(self):
+        self.h = None
+
+
+class Batch:
+    """Many independent channels advanced together (fcd_batch_*)."""
+
+    def __init__(self, cfgs, stream=None, torch_alloc=True):
+        L = load()
+        if torch_alloc and _torch_alloc is None:
+            use_torch_allocator()
+        self.cfgs = [dict(c) for c in cfgs]
+        arr = (fcd_params * len(cfgs))(*[make_params(c) for c in cfgs])
+        h = C.c_void_p()
+        st = L.fcd_batch_create(arr, len(cfgs), C.byref(h))
+        if st != FCD_OK:
+            raise FcdError(st, L.fcd_batch_last_error(None).decode())
+        self.h = h
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        L.fcd_batch_set_stream(self.h, C.c_void_p(stream))
+        self.instances = [_Instance(L.fcd_batch_instance(self.h, i), c) for i, c in enumerate(cfgs)]
+
+    def step(self, n=1):
+        st = load().fcd_batch_step(self.h, int(n))
+        if st != FCD_OK:
+            raise FcdError(st, load().fcd_batch_last_error(self.h).decode())
+
+    def observe(self, allow=()):
+        out = (fcd_obs * len(self.cfgs))()
+        st = load().fcd_batch_observables(self.h, out)
+        if st != FCD_OK and st not in allow:
+            raise FcdError(st, load().fcd_batch_last_error(self.h).decode())
+        return [o.as_dict() for o in out]
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().fcd_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):
