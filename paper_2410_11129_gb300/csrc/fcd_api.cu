@@ -361,6 +361,21 @@ struct Engine : fcd_ctx {
     fcd_status build_graph(int c, int sm) {
         cudaStream_t s = cap;
         CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        const fcd_status st = capture_step(c, sm, s);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(s, &g);  // always leave capture mode
+        if (st != FCD_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        CK(e);
+        graph[c][sm] = g;
+        CK(cudaGraphInstantiate(&gexec[c][sm], graph[c][sm], 0));
+        return FCD_OK;
+    }
+
+    // The captured sequence of one step (stream s is in capture mode).
+    fcd_status capture_step(int c, int sm, cudaStream_t s) {
         if (profiling) CK(cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal));
         enqueue_pre(c, s);
         if (profiling) CK(cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal));
@@ -438,8 +453,6 @@ struct Engine : fcd_ctx {
         if (profiling) CK(cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal));
         enqueue_post(c, sm != 0, s);
         if (profiling) CK(cudaEventRecordWithFlags(ev[3], s, cudaEventRecordExternal));
-        CK(cudaStreamEndCapture(s, &graph[c][sm]));
-        CK(cudaGraphInstantiate(&gexec[c][sm], graph[c][sm], 0));
         return FCD_OK;
     }
 

@@ -749,8 +749,10 @@ MgHost<T> *mg_create(int nx, int ny, int pitch, T *k0, T *psiA, T *psiB, MgCtl *
         mg_destroy(m);
         return nullptr;
     }
+    // The limit is a property of the kernel, shared by every context in the
+    // process: set it to the fixed budget, not to this hierarchy's need.
     if (cudaFuncSetAttribute(coarse_cta<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)m->cta_smem) != cudaSuccess) {
+                             (int)CTA_SMEM_MAX) != cudaSuccess) {
         snprintf(err, errlen, "multigrid: cannot reserve %zu bytes of shared memory", m->cta_smem);
         mg_destroy(m);
         return nullptr;
