@@ -36,9 +36,16 @@ FALLBACK_HBM_GBS = 6800.0
 # (18 x 4), g read+write (36 x 4), phi_1, phi_2 read (8), psi' read (4) and the
 # stored u_x, u_y, p* (12).
 COLLIDE_BYTES_PER_NODE_F32 = 240
-# DRAM bytes per collide launch measured by ncu on this workload, keyed by the
-# hash of the kernel source it was taken on (null once the source changes).
-NCU_TRAFFIC = {}
+# DRAM bytes (read + write) per collide launch measured by ncu, keyed by the hash
+# of the kernel source they were taken on and the workload (null once the source
+# changes). On 1600x200 the 37 MB of output stays in L2 when the launch ends, so
+# only the reads reach DRAM inside the launch.
+NCU_TRAFFIC = {
+    ("ad0bc2f4207122eb", "1600x200"):
+        38428416 + 420608,
+    ("ad0bc2f4207122eb", "9600x1200"):
+        1383331840 + 1204713984,
+}
 
 
 def _workloads():
@@ -185,6 +192,42 @@ def measure_batched(steps, warmup):
             "max_mag_resid": max(o["mag_resid"] for o in obs)}
 
 
+def measure_large(steps, warmup, peak, peak_kind):
+    """Whole step and collide roofline on the 9600x1200 FP32 channel (11.5 M
+    nodes, 2.5 GB of state, far larger than L2): the grid on which the HBM
+    fraction is quoted. Same per-stage events as the main measurement."""
+    import torch
+    from paper_2410_11129_gb300 import fcd
+    cfg = dict(WORKLOADS["9600x1200"])
+    N = cfg["nx"] * cfg["ny"]
+    ch = fcd.Channel(cfg)
+    ch.set_profiling(True)
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        ch.step(1)
+    torch.cuda.synchronize()
+    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    coll = 0.0
+    total = 0.0
+    for _ in range(steps):
+        a.record(stream)
+        ch.step(1)
+        z.record(stream)
+        coll += ch.last_step_profile()["collide"]
+        torch.cuda.synchronize()
+        total += a.elapsed_time(z)
+    ch.close()
+    bpn = COLLIDE_BYTES_PER_NODE_F32
+    achieved = bpn * N / (coll / steps * 1e-3) / 1e9
+    return {"workload": cfg["name"], "steps": steps, "value": N * steps / (total * 1e-3) / 1e6,
+            "unit": UNIT, "ms_per_step": total / steps,
+            "roofline": {"bound": "hbm", "kernel": "collide_kernel (fp32)", "achieved": achieved,
+                         "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                         "frac": achieved / peak,
+                         "traffic": NCU_TRAFFIC.get((kernel_source_hash(), "9600x1200")),
+                         "algorithmic_bytes_per_launch": bpn * N, "launch_ms": coll / steps}}
+
+
 def oracle_rate(cfg, min_seconds, max_steps, warmup=1):
     """MLUPS of the FP64 C oracle (single thread) over a bounded sample."""
     import oracle
@@ -326,11 +369,11 @@ def run_ours(args):
     bpn = COLLIDE_BYTES_PER_NODE_F32 * (2 if cfg["precision"] == "fp64" else 1)
     achieved = bpn * N / (coll_ms * 1e-3) / 1e9
     h = kernel_source_hash()
-    traffic = NCU_TRAFFIC.get(h)
+    traffic = NCU_TRAFFIC.get((h, args.workload))
     roofline = {"bound": "hbm", "kernel": "collide_kernel (%s)" % cfg["precision"],
                 "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                 "frac": achieved / peak,
-                "traffic": traffic if args.workload == DEFAULT_WORKLOAD else None,
+                "traffic": traffic,
                 "algorithmic_bytes_per_launch": bpn * N, "launch_ms": coll_ms}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -349,6 +392,8 @@ def run_ours(args):
         "solver_per_step": {k: (st1[k] - st0[k]) / args.steps for k in st0},
         "clocks": clocks,
     }
+    if args.large_steps > 0 and args.workload == DEFAULT_WORKLOAD and ws == 1:
+        line["large_grid"] = measure_large(args.large_steps, 3, peak, peak_kind)
     if args.batched_steps > 0 and args.workload == DEFAULT_WORKLOAD and ws == 1:
         try:
             line["batched"] = measure_batched(args.batched_steps, 3)
@@ -374,6 +419,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--large-steps", type=int, default=20,
+                    help="steps timed on the 9600x1200 channel (0: skip)")
     ap.add_argument("--batched-steps", type=int, default=10,
                     help="steps of the batched-vs-looped regime sweep (0 skips it)")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS),
