@@ -199,6 +199,39 @@ fcd_ctx *fcd_batch_instance(fcd_batch *b, int i);
 const char *fcd_batch_last_error(const fcd_batch *b);
 void fcd_batch_destroy(fcd_batch *b);
 
+/* ---- Tangent-linear form: exact discrete derivatives of the coupled step
+ * (forward mode) with respect to the four parameters of the regime study,
+ * direction order FCD_DIR_BO_M (Bo_m, Eq. 41), FCD_DIR_CA (Ca, Eq. 40),
+ * FCD_DIR_ALPHA (alpha, radians), FCD_DIR_NU_R (nu_r = nu_3 / nu_2, Eq. 39).
+ * A tangent context is an FP64 context (precision is ignored) whose state also
+ * carries the derivative of every population, phase field and potential along
+ * the four directions; each step applies the chain rule to the whole step:
+ * the collision and streaming in dual arithmetic, and four extra potential
+ * solves L(k) dpsi' = b(k, dH0) + b(dk, H0) - L(dk) psi' with the same
+ * multigrid (differentiating Eq. 6 with psi = psi0 + psi'), each to
+ * mag_tol relative to the largest |right-hand side|. Bo_m must be > 0 when a
+ * phase is ferrofluid (H0 ~ sqrt(Bo_m)); with sigma23 > 0 given directly the
+ * Ca direction is zero. The returned handle accepts fcd_step, fcd_observables
+ * (primal values), fcd_get_field (primal fields), fcd_kernel_launches,
+ * fcd_solver_stats, fcd_last_error and fcd_destroy; state snapshots and
+ * population import return FCD_ESTATE. Steps synchronise the stream once per
+ * multigrid cycle (the solve loop is driven from the host). */
+enum { FCD_DIR_BO_M = 0, FCD_DIR_CA = 1, FCD_DIR_ALPHA = 2, FCD_DIR_NU_R = 3, FCD_NDIR = 4 };
+typedef struct {
+    long step;
+    double T_o;                 /* shell deformation (Eq. 42), same value as fcd_observables */
+    double overlap;             /* sum over nodes of phi^_1 phi^_3 (core-carrier overlap) */
+    double lx_o, ly_o;          /* shell extents along and across the channel */
+    double dT_o[FCD_NDIR];      /* dT_o / d(Bo_m, Ca, alpha, nu_r) */
+    double doverlap[FCD_NDIR];  /* d overlap / d(...) */
+    double dlx_o[FCD_NDIR], dly_o[FCD_NDIR];
+} fcd_tangent_obs;
+fcd_status fcd_create_tangent(const fcd_params *params, fcd_ctx **out);
+/* Values and derivatives of the current state (synchronous). T_o is
+ * differentiated through the crossing interpolation of the 1/2 level set
+ * (l_x: the two centre-line crossings; l_y: the column of largest extent). */
+fcd_status fcd_tangent_observables(fcd_ctx *ctx, fcd_tangent_obs *out);
+
 /* Observables of a caller's population buffer with no device allocation.
  * The paper has no counterpart: this serves callers that cannot allocate
  * device memory (another framework owns the memory budget, cudaMalloc/cudaFree

@@ -211,6 +211,7 @@ struct Engine : fcd_ctx {
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     long host_kernels = 0;
     int reported_nonconv = 0;
+    int copies = 1;  // plane sets per field: 1, or 1 + NT for the tangent context
 
     T *dalloc(size_t bytes) {
         void *p = alloc(bytes, user);
@@ -246,12 +247,12 @@ struct Engine : fcd_ctx {
         const char *nog = getenv("FCD_NO_GRAPH");
         use_graph = !(nog && nog[0] == '1');
         for (int b = 0; b < 2; b++) {
-            f[b] = dalloc(9 * ps * sizeof(S));
-            g[b] = dalloc(18 * ps * sizeof(S));
+            f[b] = dalloc(9 * copies * ps * sizeof(S));
+            g[b] = dalloc(18 * copies * ps * sizeof(S));
         }
-        phi1 = dalloc(ps * sizeof(T));
-        phi2 = dalloc(ps * sizeof(T));
-        k = dalloc(ps * sizeof(T));
+        phi1 = dalloc(copies * ps * sizeof(T));
+        phi2 = dalloc(copies * ps * sizeof(T));
+        k = dalloc(copies * ps * sizeof(T));
         psiA = dalloc(ps * sizeof(T));
         psiB = dalloc(ps * sizeof(T));
         psiP = dalloc(ps * sizeof(T));
@@ -281,12 +282,12 @@ struct Engine : fcd_ctx {
         CK(cudaMemsetAsync(d_step, 0, sizeof(long long), s));
         // padding columns of every plane stay zero
         for (int b = 0; b < 2; b++) {
-            CK(cudaMemsetAsync(f[b], 0, 9 * ps * sizeof(S), s));
-            CK(cudaMemsetAsync(g[b], 0, 18 * ps * sizeof(S), s));
+            CK(cudaMemsetAsync(f[b], 0, 9 * copies * ps * sizeof(S), s));
+            CK(cudaMemsetAsync(g[b], 0, 18 * copies * ps * sizeof(S), s));
         }
-        CK(cudaMemsetAsync(phi1, 0, ps * sizeof(T), s));
-        CK(cudaMemsetAsync(phi2, 0, ps * sizeof(T), s));
-        CK(cudaMemsetAsync(k, 0, ps * sizeof(T), s));
+        CK(cudaMemsetAsync(phi1, 0, copies * ps * sizeof(T), s));
+        CK(cudaMemsetAsync(phi2, 0, copies * ps * sizeof(T), s));
+        CK(cudaMemsetAsync(k, 0, copies * ps * sizeof(T), s));
         {
             MgCtl c;
             std::memset(&c, 0, sizeof c);
@@ -766,6 +767,225 @@ struct Engine : fcd_ctx {
     }
 };
 
+
+// ---------------------------------------------------------------- tangent
+// Constants of the step in dual arithmetic: the value of every constant and its
+// derivative along Bo_m, Ca, alpha and nu_r (nu_r = nu_3 / nu_2), from the
+// lattice mapping of derive(): sigma_ij ~ 1/Ca (Eq. 40), so gamma_i and the
+// Laplacian coefficients too; mu0 H0^2 ~ Bo_m sigma (Eq. 41), H0 its root;
+// H0 (cos alpha, sin alpha); tau_2 = 3 nu_3 / nu_r (Eqs. 14, 39).
+static Phys<DualT> tangent_phys(const fcd_params *p, const Phys<double> &P) {
+    Phys<DualT> Q;
+    Q.nx = P.nx;
+    Q.ny = P.ny;
+    Q.pitch = P.pitch;
+    Q.ps = P.ps;
+    for (int i = 0; i < 3; i++) {
+        Q.rho[i] = DualT(P.rho[i]);
+        Q.tau[i] = DualT(P.tau[i]);
+        Q.ik[i] = DualT(P.ik[i]);
+        Q.gam[i] = DualT(P.gam[i]);
+        Q.lap_coef[i] = DualT(P.lap_coef[i]);
+    }
+    Q.dk1 = DualT(P.dk1);
+    Q.dk2 = DualT(P.dk2);
+    Q.s12 = DualT(P.s12);
+    Q.s13 = DualT(P.s13);
+    Q.s23 = DualT(P.s23);
+    Q.eta = DualT(P.eta);
+    Q.twelve_over_xi = DualT(P.twelve_over_xi);
+    Q.four_over_xi = DualT(P.four_over_xi);
+    Q.eps_n = DualT(P.eps_n);
+    Q.om_phi = DualT(P.om_phi);
+    Q.keep_phi = DualT(P.keep_phi);
+    Q.src_phi = DualT(P.src_phi);
+    Q.H0c = DualT(P.H0c);
+    Q.H0s = DualT(P.H0s);
+    Q.G = DualT(P.G);
+    if (p->ferro_phase != 0 && p->Bo_m > 0) {
+        Q.H0c.d[FCD_DIR_BO_M] = P.H0c / (2.0 * p->Bo_m);
+        Q.H0s.d[FCD_DIR_BO_M] = P.H0s / (2.0 * p->Bo_m);
+    }
+    if (!(p->sigma23 > 0)) {
+        const double ic = -1.0 / p->Ca;
+        Q.s12.d[FCD_DIR_CA] = P.s12 * ic;
+        Q.s13.d[FCD_DIR_CA] = P.s13 * ic;
+        Q.s23.d[FCD_DIR_CA] = P.s23 * ic;
+        for (int i = 0; i < 3; i++) {
+            Q.gam[i].d[FCD_DIR_CA] = P.gam[i] * ic;
+            Q.lap_coef[i].d[FCD_DIR_CA] = P.lap_coef[i] * ic;
+        }
+        Q.H0c.d[FCD_DIR_CA] = 0.5 * P.H0c * ic;
+        Q.H0s.d[FCD_DIR_CA] = 0.5 * P.H0s * ic;
+    }
+    Q.H0c.d[FCD_DIR_ALPHA] = -P.H0s;
+    Q.H0s.d[FCD_DIR_ALPHA] = P.H0c;
+    Q.tau[1].d[FCD_DIR_NU_R] = -P.tau[1] * p->nu[1] / p->nu[2];
+    return Q;
+}
+
+// FP64 context whose plane sets carry NT tangent copies (see fcd.h). The
+// potential solves run with the host loop of the plain context.
+struct TangentEngine : Engine<double> {
+    Phys<DualT> PT;
+    double *psiT = nullptr;   // 1 + NT planes: the step's potential, then its derivatives
+    double *dpsiP = nullptr;  // NT planes: derivatives at the previous step (extrapolation)
+    double *rhs = nullptr, *saved = nullptr;
+    unsigned long long *rmax = nullptr, *h_rmax = nullptr;
+    void *tobs = nullptr;
+    TanOut *tan_out = nullptr, *h_tan = nullptr;
+
+    ~TangentEngine() override {
+        if (h_rmax) cudaFreeHost(h_rmax);
+        if (h_tan) cudaFreeHost(h_tan);
+    }
+
+    fcd_status init() override {
+        copies = 1 + NT;
+        use_graph = false;
+        pitch = (prm.nx + 31) / 32 * 32;
+        ps = (long long)pitch * prm.ny;
+        psiT = dalloc((1 + NT) * ps * sizeof(double));
+        dpsiP = dalloc(NT * ps * sizeof(double));
+        rhs = dalloc(ps * sizeof(double));
+        saved = dalloc(ps * sizeof(double));
+        rmax = reinterpret_cast<unsigned long long *>(dalloc(sizeof(unsigned long long)));
+        tobs = dalloc(tangent_obs_scratch_bytes(prm.nx));
+        tan_out = reinterpret_cast<TanOut *>(dalloc(sizeof(TanOut)));
+        for (void *q : {(void *)psiT, (void *)dpsiP, (void *)rhs, (void *)saved, (void *)rmax, tobs,
+                        (void *)tan_out})
+            if (!q) return fail(FCD_ENOMEM, "device allocation failed");
+        CK(cudaMallocHost(&h_rmax, sizeof(unsigned long long)));
+        CK(cudaMallocHost(&h_tan, sizeof(TanOut)));
+        CK(cudaMemsetAsync(psiT, 0, (1 + NT) * ps * sizeof(double), stream));
+        CK(cudaMemsetAsync(dpsiP, 0, NT * ps * sizeof(double), stream));
+        PT = tangent_phys(&prm, make_phys<double>(&prm, D, pitch));
+        fcd_status st = Engine<double>::init();  // the initial solve runs the tangent solves too
+        if (st != FCD_OK) return st;
+        CK(cudaMemcpyAsync(dpsiP, psiT + ps, NT * ps * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+        CK(cudaStreamSynchronize(stream));
+        return FCD_OK;
+    }
+
+    // The NT tangent potentials for the current phase fields (derivative
+    // planes of k already formed). extrap: start from 2 dpsi(t) - dpsi(t-1).
+    fcd_status tangent_solves(bool extrap, double tol, int max_iter) {
+        cudaStream_t s = stream;
+        if (!magnetic()) return FCD_OK;  // no field: every derivative of psi' stays 0
+        for (int c = 0; c < NT; c++) {
+            double *dk = k + (c + 1) * ps, *dpsi = psiT + (c + 1) * ps, *prev = dpsiP + c * ps;
+            mg_tangent_rhs(mg, dk, P.H0c, P.H0s, PT.H0c.d[c], PT.H0s.d[c], rhs, rmax, s);
+            CK(cudaMemcpyAsync(h_rmax, rmax, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            host_kernels += 1;
+            if (*h_rmax == 0ull) {  // nothing drives this derivative
+                CK(cudaMemsetAsync(dpsi, 0, ps * sizeof(double), s));
+                if (extrap) CK(cudaMemsetAsync(prev, 0, ps * sizeof(double), s));
+                continue;
+            }
+            mg_psi_io(mg, 0, saved, nullptr, s);  // the primal potential
+            if (extrap) mg_psi_io(mg, 2, dpsi, prev, s);
+            else mg_psi_io(mg, 1, dpsi, nullptr, s);
+            mg_reset_scaled(ctl, rmax, tol, max_iter, s);
+            mg_set_rhs<double>(mg, rhs);
+            const fcd_status st = host_mg_loop(s);
+            mg_set_rhs<double>(mg, nullptr);
+            if (st != FCD_OK) return st;
+            mg_psi_io(mg, 0, dpsi, nullptr, s);
+            mg_psi_io(mg, 1, saved, nullptr, s);
+            host_kernels += 5;
+            CK(cudaGetLastError());
+        }
+        return FCD_OK;
+    }
+
+    fcd_status solve(double tol, int max_iter, int *iters, double *resid) override {
+        if (!(tol > 0)) tol = prm.mag_tol;
+        if (max_iter <= 0) max_iter = prm.mag_max_iter;
+        const fcd_status st = Engine<double>::solve(tol, max_iter, iters, resid);
+        if (st != FCD_OK && st != FCD_ENOCONV) return st;
+        launch_tangent_phase(P, static_cast<const double *>(g[cur]), phi1, phi2, k, stream);
+        host_kernels += 1;
+        const fcd_status st2 = tangent_solves(false, tol, max_iter);
+        return st2 != FCD_OK ? st2 : st;
+    }
+
+    fcd_status do_step(long n) override {
+        if (n < 0) return fail(FCD_EINVAL, "negative step count");
+        cudaStream_t s = stream;
+        for (long i = 0; i < n; i++) {
+            enqueue_pre(cur, s);
+            launch_tangent_phase(P, static_cast<const double *>(g[cur]), phi1, phi2, k, s);
+            if (magnetic()) {
+                fcd_status st = host_mg_loop(s);
+                if (st != FCD_OK) return st;
+                st = tangent_solves(true, prm.mag_tol, prm.mag_max_iter);
+                if (st != FCD_OK) return st;
+            }
+            mg_psi_io(mg, 0, psiT, nullptr, s);
+            LbmArgs<double, DualT> a;
+            a.P = PT;
+            a.f_src = f[cur];
+            a.g_src = g[cur];
+            a.f_dst = f[cur ^ 1];
+            a.g_dst = g[cur ^ 1];
+            a.phi1 = phi1;
+            a.phi2 = phi2;
+            a.psi0 = psiT;
+            a.psi1 = psiT;
+            a.ctl = ctl;
+            a.macro = i == n - 1 ? macro : nullptr;
+            a.brk = brk;
+            a.step = d_step;
+            launch_collide_tangent(a, s);
+            host_kernels += 4;
+            CK(cudaGetLastError());
+            cur ^= 1;
+            step++;
+        }
+        return FCD_OK;
+    }
+
+    fcd_status tangent_observe(fcd_tangent_obs *o) {
+        fcd_obs po;
+        const fcd_status st = observe(&po);  // primal observables (and the seam column)
+        if (st != FCD_OK && st != FCD_ENOCONV) return st;
+        cudaStream_t s = stream;
+        launch_tangent_obs(P, static_cast<const double *>(g[cur]), obs_out, tobs, tan_out, s);
+        host_kernels += 1;
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(h_tan, tan_out, sizeof(TanOut), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        std::memset(o, 0, sizeof *o);
+        o->step = step;
+        o->T_o = h_tan->T_o;
+        o->overlap = h_tan->overlap;
+        o->lx_o = h_tan->lx;
+        o->ly_o = h_tan->ly;
+        for (int c = 0; c < NT; c++) {
+            o->dT_o[c] = h_tan->dT_o[c];
+            o->doverlap[c] = h_tan->doverlap[c];
+            o->dlx_o[c] = h_tan->dlx[c];
+            o->dly_o[c] = h_tan->dly[c];
+        }
+        return st;
+    }
+
+    size_t state_bytes() const override { return 0; }
+    fcd_status get_state(void *, size_t) override {
+        return fail(FCD_ESTATE, "state snapshots are not available for tangent contexts");
+    }
+    fcd_status set_state(const void *, size_t) override {
+        return fail(FCD_ESTATE, "state snapshots are not available for tangent contexts");
+    }
+    fcd_status set_pops(const double *, const double *, const double *, long) override {
+        return fail(FCD_ESTATE, "population import is not available for tangent contexts");
+    }
+    fcd_status set_profiling(int) override {
+        return fail(FCD_ESTATE, "step profiling is not available for tangent contexts");
+    }
+};
+
 // ---------------------------------------------------------------- C ABI
 static thread_local char g_last[512];  // reason of the last failed fcd_create on this thread
 
@@ -803,6 +1023,47 @@ fcd_status fcd_create(const fcd_params *params, fcd_ctx **out) {
     }
     *out = c;
     return FCD_OK;
+}
+
+fcd_status fcd_create_tangent(const fcd_params *params, fcd_ctx **out) {
+    if (!out) return FCD_EINVAL;
+    *out = nullptr;
+    if (!params) return FCD_EINVAL;
+    fcd_params p = *params;
+    p.precision = FCD_FP64;
+    Derived d;
+    std::memset(&d, 0, sizeof d);
+    const char *why = derive(&p, &d);
+    if (!why && 18ll * (1 + NT) * ((p.nx + 31) / 32 * 32) * p.ny > (1ll << 31) - 1)
+        why = "lattice too large for the tangent copies (90 planes within 2^31 elements)";
+    if (!why && p.ferro_phase != 0 && !(p.Bo_m > 0))
+        why = "the Bo_m direction needs Bo_m > 0 (H0 ~ sqrt(Bo_m))";
+    if (why) {
+        snprintf(g_last, sizeof g_last, "fcd_create_tangent: %s", why);
+        return FCD_EINVAL;
+    }
+    auto *e = new (std::nothrow) TangentEngine();
+    if (!e) return FCD_ENOMEM;
+    e->alloc = g_alloc ? g_alloc : default_alloc;
+    e->release = g_free ? g_free : default_free;
+    e->user = g_alloc ? g_user : nullptr;
+    e->prm = p;
+    e->D = d;
+    const fcd_status st = e->init();
+    if (st != FCD_OK) {
+        snprintf(g_last, sizeof g_last, "%s", e->err);
+        delete e;
+        return st;
+    }
+    *out = e;
+    return FCD_OK;
+}
+
+fcd_status fcd_tangent_observables(fcd_ctx *c, fcd_tangent_obs *o) {
+    if (!c || !o) return FCD_EINVAL;
+    auto *e = dynamic_cast<TangentEngine *>(c);
+    if (!e) return c->fail(FCD_EINVAL, "not a tangent context");
+    return e->tangent_observe(o);
 }
 
 fcd_status fcd_set_stream(fcd_ctx *c, void *stream) {

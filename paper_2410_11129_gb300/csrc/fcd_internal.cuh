@@ -14,10 +14,22 @@
 #include <stdint.h>
 
 #include "fcd.h"
+#include "fcd_dual.cuh"
 
 namespace fcd {
 
-enum StoreMode { MODE_FP64 = 0, MODE_FP32 = 1, MODE_FP32_OFFSET = 2 };
+// MODE_TANGENT: FP64 storage of the primal state and of NT tangent copies
+// (forward-mode derivative along NT parameter directions), dual arithmetic.
+enum StoreMode { MODE_FP64 = 0, MODE_FP32 = 1, MODE_FP32_OFFSET = 2, MODE_TANGENT = 3 };
+
+constexpr int NT = 4;  // tangent directions: Bo_m, Ca, alpha, nu_r
+using DualT = Dual<NT>;
+
+// Arithmetic type of a kernel: the storage type, or dual numbers for tangents.
+template <typename T, int MODE>
+struct Compute { using type = T; };
+template <>
+struct Compute<double, MODE_TANGENT> { using type = DualT; };
 
 constexpr int TX = 32;  // collide tile (x)
 constexpr int TY = 8;   // collide tile (y)
@@ -84,6 +96,7 @@ struct Level {
     // prolongation of the next coarser level onto this one
     const int *px0, *px1, *py0, *py1;  // -1 in py* stands for the wall (value 0)
     const T *pwx, *pwy;
+    const T *rhs;  // level 0: explicit right-hand side (nullptr: -L psi0 formed from k)
 };
 
 // Device-side control block of one potential solve.
@@ -136,14 +149,23 @@ struct ObsOut {
     int nonfinite;
 };
 
+// Tangent observables: values and derivatives along the NT directions.
+struct TanOut {
+    double T_o, overlap, lx, ly;
+    double dT_o[NT], doverlap[NT], dlx[NT], dly[NT];
+};
+
 }  // namespace fcd
 
 // ---- host-side launchers (defined in the .cu files) ----
 namespace fcd {
 
-template <typename T>
+// T: element type of the field planes; R: arithmetic type of the constants
+// (DualT for the tangent step, whose planes hold the primal value followed by
+// NT tangent copies at a stride of one plane set).
+template <typename T, typename R = T>
 struct LbmArgs {
-    Phys<T> P;
+    Phys<R> P;
     const void *f_src, *g_src;
     void *f_dst, *g_dst;
     const T *phi1, *phi2;
@@ -159,6 +181,7 @@ void launch_phase(int mode, const Phys<T> &P, const void *g, T *phi1, T *phi2, T
                   PhaseCtl pc, cudaStream_t s);
 template <typename T>
 void launch_collide(int mode, const LbmArgs<T> &a, cudaStream_t s);
+void launch_collide_tangent(const LbmArgs<double, DualT> &a, cudaStream_t s);
 template <typename T>
 void launch_init(int mode, const Phys<T> &P, double u_max, double r1, double r2, double xc,
                  double yc, double xi, void *f, void *g, T *macro, cudaStream_t s);
@@ -200,8 +223,27 @@ template <typename T>
 void mg_presmooth(MgHost<T> *m, T H0c, T H0s, cudaStream_t s);  // opens every solve
 template <typename T>
 int mg_kernels_per_cycle(const MgHost<T> *m);
+// Tangent solves (FP64): explicit right-hand side on level 0; reset of the
+// control block with tolerance tol * max|rhs|; right-hand side along one
+// direction, L(k) dpsi' = b(k, dH0) + b(dk, H0) - L(dk) psi'; copies between
+// the current level-0 buffer (picked on the device) and a plane:
+// op 0 plane <- cur, op 1 cur <- plane, op 2 cur <- 2 plane - prev, prev <- plane.
+template <typename T>
+void mg_set_rhs(MgHost<T> *m, const T *rhs);
+void mg_reset_scaled(MgCtl *ctl, const unsigned long long *scale_bits, double tol, int max_iter,
+                     cudaStream_t s);
+void mg_tangent_rhs(MgHost<double> *m, const double *dk, double H0c, double H0s, double dH0c,
+                    double dH0s, double *rhs, unsigned long long *rmax_bits, cudaStream_t s);
+void mg_psi_io(MgHost<double> *m, int op, double *plane, double *prev, cudaStream_t s);
 template <typename T>
 int mg_levels(const MgHost<T> *m);
+
+// tangent step (FP64 primal + NT tangent copies)
+void launch_tangent_phase(const Phys<double> &P, const double *g, double *phi1, double *phi2,
+                          double *k, cudaStream_t s);
+size_t tangent_obs_scratch_bytes(int nx);
+void launch_tangent_obs(const Phys<double> &P, const double *g, const ObsOut *prim, void *scratch,
+                        TanOut *out, cudaStream_t s);
 
 // observables
 size_t observe_scratch_doubles(int nx, int ny);

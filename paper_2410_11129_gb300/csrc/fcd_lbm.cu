@@ -19,6 +19,8 @@ template <int MODE>
 struct StoreT { using type = float; };
 template <>
 struct StoreT<MODE_FP64> { using type = double; };
+template <>
+struct StoreT<MODE_TANGENT> { using type = double; };
 
 // ---------------------------------------------------------------- phase
 template <typename T, int MODE>
@@ -79,10 +81,11 @@ __device__ __forceinline__ T cdiv(T a, T b) { return a / b; }
 template <>
 __device__ __forceinline__ float cdiv<float>(float a, float b) { return __fdividef(a, b); }
 
-template <typename T>
+template <typename R, typename B>
 struct Stencil {
-    T c, e, w, n, s, ne, nw, sw, se;
-    __device__ __forceinline__ void load(const T (*a)[TX + 2], int lx, int ly) {
+    R c, e, w, n, s, ne, nw, sw, se;
+    template <int W>
+    __device__ __forceinline__ void load(const R (*a)[W], int lx, int ly) {
         c = a[ly][lx];
         e = a[ly][lx + 1];
         w = a[ly][lx - 1];
@@ -94,27 +97,76 @@ struct Stencil {
         se = a[ly - 1][lx + 1];
     }
     // Eq. 34 with c_s^2 = 1/3: 3 sum_a w_a e_a phi_a
-    __device__ __forceinline__ T gx() const {
-        return (e - w) * T(1.0 / 3.0) + ((ne - nw) + (se - sw)) * T(1.0 / 12.0);
+    __device__ __forceinline__ R gx() const {
+        return (e - w) * B(1.0 / 3.0) + ((ne - nw) + (se - sw)) * B(1.0 / 12.0);
     }
-    __device__ __forceinline__ T gy() const {
-        return (n - s) * T(1.0 / 3.0) + ((ne + nw) - (se + sw)) * T(1.0 / 12.0);
+    __device__ __forceinline__ R gy() const {
+        return (n - s) * B(1.0 / 3.0) + ((ne + nw) - (se + sw)) * B(1.0 / 12.0);
     }
     // Eq. 35: 6 sum_a w_a (phi_a - phi_0)
-    __device__ __forceinline__ T lap() const {
-        return (T(4) * ((e + w) + (n + s)) + ((ne + nw) + (se + sw)) - T(20) * c) *
-               T(1.0 / 6.0);
+    __device__ __forceinline__ R lap() const {
+        return (B(4) * ((e + w) + (n + s)) + ((ne + nw) + (se + sw)) - B(20) * c) *
+               B(1.0 / 6.0);
     }
 };
 
+// Field and population access. Plain modes: one plane per quantity. Tangent
+// mode: the primal plane set is followed by NT tangent copies, copy c of plane
+// q of an np-plane set at (np * c + q) planes from the base.
+template <typename R, typename T>
+__device__ __forceinline__ R ld_field(const T *p, long long i, long long ps) {
+    if constexpr (sizeof(R) == sizeof(T)) {
+        (void)ps;
+        return R(p[i]);
+    } else {
+        R r(p[i]);
+#pragma unroll
+        for (int c = 0; c < NT; c++) r.d[c] = p[i + (c + 1) * ps];
+        return r;
+    }
+}
+template <typename R, typename S>
+__device__ __forceinline__ R ld_pop(const S *p, int q, int np, int ps, int n) {
+    if constexpr (sizeof(R) == sizeof(S)) {
+        (void)np;
+        return R(p[q * ps + n]);
+    } else {
+        R r(p[q * ps + n]);
+#pragma unroll
+        for (int c = 0; c < NT; c++) r.d[c] = p[(np * (c + 1) + q) * ps + n];
+        return r;
+    }
+}
+template <typename S, typename R>
+__device__ __forceinline__ void st_pop(S *p, int q, int np, int ps, int n, const R &v) {
+    if constexpr (sizeof(R) == sizeof(S)) {
+        (void)np;
+        p[q * ps + n] = S(v);
+    } else {
+        p[q * ps + n] = v.v;
+#pragma unroll
+        for (int c = 0; c < NT; c++) p[(np * (c + 1) + q) * ps + n] = v.d[c];
+    }
+}
+
+// Tile height: the dual tiles of the tangent step are five times larger.
+template <int MODE>
+__host__ __device__ constexpr int tile_y() { return MODE == MODE_TANGENT ? 4 : TY; }
+template <int MODE>
+__host__ __device__ constexpr int collide_min_blocks() { return MODE == MODE_FP32 || MODE == MODE_FP32_OFFSET ? 4 : 1; }
+
 template <typename T, int MODE>
-__global__ void __launch_bounds__(TX *TY, (MODE == MODE_FP64 ? 1 : 4)) collide_kernel(LbmArgs<T> A) {
+__global__ void __launch_bounds__(TX *tile_y<MODE>(), collide_min_blocks<MODE>())
+    collide_kernel(LbmArgs<T, typename Compute<T, MODE>::type> A) {
     using S = typename StoreT<MODE>::type;
-    __shared__ T s1[TY + 2][TX + 2], s2[TY + 2][TX + 2], sr[TY + 2][TX + 2], sp[TY + 2][TX + 2];
-    const Phys<T> &P = A.P;
+    using R = typename Compute<T, MODE>::type;  // arithmetic type
+    using B = T;                                // type of the constants
+    constexpr int TYM = tile_y<MODE>();
+    __shared__ R s1[TYM + 2][TX + 2], s2[TYM + 2][TX + 2], sr[TYM + 2][TX + 2], sp[TYM + 2][TX + 2];
+    const Phys<R> &P = A.P;
     const int nx = P.nx, ny = P.ny, pitch = P.pitch;
     const long long ps = P.ps;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TYM;
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
     const bool live = x < nx && y < ny;
     const long long n = (long long)y * pitch + x;
@@ -122,7 +174,7 @@ __global__ void __launch_bounds__(TX *TY, (MODE == MODE_FP64 ? 1 : 4)) collide_k
     // FP32 forms: issue the 27 population loads first so that their latency
     // overlaps the halo fill and the force evaluation (FP64 keeps them late:
     // its register budget is already large).
-    constexpr bool EARLY = MODE != MODE_FP64;
+    constexpr bool EARLY = MODE == MODE_FP32 || MODE == MODE_FP32_OFFSET;
     const S *fs = static_cast<const S *>(A.f_src);
     const S *gs = static_cast<const S *>(A.g_src);
     S fpre[EARLY ? 9 : 1], gpre[EARLY ? 18 : 1];
@@ -136,7 +188,7 @@ __global__ void __launch_bounds__(TX *TY, (MODE == MODE_FP64 ? 1 : 4)) collide_k
     }
     const T *psi = A.ctl->cur ? A.psi1 : A.psi0;
 
-    for (int i = threadIdx.y * TX + threadIdx.x; i < (TX + 2) * (TY + 2); i += TX * TY) {
+    for (int i = threadIdx.y * TX + threadIdx.x; i < (TX + 2) * (TYM + 2); i += TX * TYM) {
         int lx = i % (TX + 2), ly = i / (TX + 2);
         int gx = x0 - 1 + lx;
         if (gx < 0) gx += nx;
@@ -145,12 +197,12 @@ __global__ void __launch_bounds__(TX *TY, (MODE == MODE_FP64 ? 1 : 4)) collide_k
         bool ghost = gy < 0 || gy >= ny;
         int my = gy < 0 ? 0 : (gy >= ny ? ny - 1 : gy);
         long long m = (long long)my * pitch + gx;
-        T p1 = A.phi1[m], p2 = A.phi2[m];
+        const R p1 = ld_field<R>(A.phi1, m, ps), p2 = ld_field<R>(A.phi2, m, ps);
         s1[ly][lx] = p1;  // mirrored ghost rows: zero normal gradient
         s2[ly][lx] = p2;
         sr[ly][lx] = P.rho[0] * clamp01(p1) + P.rho[1] * clamp01(p2) +
-                     P.rho[2] * clamp01(T(1) - p1 - p2);
-        T q = psi[m];
+                     P.rho[2] * clamp01(B(1) - p1 - p2);
+        const R q = ld_field<R>(psi, m, ps);
         sp[ly][lx] = ghost ? -q : q;  // psi' = 0 on the wall faces
     }
     __syncthreads();
@@ -158,107 +210,107 @@ __global__ void __launch_bounds__(TX *TY, (MODE == MODE_FP64 ? 1 : 4)) collide_k
     if (!live) return;
     const int lx = threadIdx.x + 1, ly = threadIdx.y + 1;
 
-    Stencil<T> st;
+    Stencil<R, B> st;
     st.load(s1, lx, ly);
-    const T ph1 = st.c, g1x = st.gx(), g1y = st.gy(), l1 = st.lap();
+    const R ph1 = st.c, g1x = st.gx(), g1y = st.gy(), l1 = st.lap();
     st.load(s2, lx, ly);
-    const T ph2 = st.c, g2x = st.gx(), g2y = st.gy(), l2 = st.lap();
-    const T ph3 = T(1) - ph1 - ph2;
-    const T g3x = -(g1x + g2x), g3y = -(g1y + g2y), l3 = -(l1 + l2);
+    const R ph2 = st.c, g2x = st.gx(), g2y = st.gy(), l2 = st.lap();
+    const R ph3 = B(1) - ph1 - ph2;
+    const R g3x = -(g1x + g2x), g3y = -(g1y + g2y), l3 = -(l1 + l2);
     st.load(sr, lx, ly);
-    const T rho = st.c, grx = st.gx(), gry = st.gy();
+    const R rho = st.c, grx = st.gx(), gry = st.gy();
     st.load(sp, lx, ly);
-    const T dpx = st.gx(), dpy = st.gy();
+    const R dpx = st.gx(), dpy = st.gy();
 
-    const T h1 = clamp01(ph1), h2 = clamp01(ph2), h3 = clamp01(ph3);
+    const R h1 = clamp01(ph1), h2 = clamp01(ph2), h3 = clamp01(ph3);
 
     // Surface tension (Eqs. 25, 28, 36). With phi_3 = 1 - phi_1 - phi_2 the
     // gradients sum to zero, so the part of mu_i common to all phases drops out:
     // F_s = sum_i [ (12/xi) dH/dphi_i - (3/4) xi gamma_i lap phi_i ] grad phi_i.
-    T Fx, Fy;
+    R Fx, Fy;
     {
-        const T gp = P.gam[0] * ph1 + P.gam[1] * ph2 + P.gam[2] * ph3;
-        const T q3 = ph1 * ph2 * ph3;
-        const T a1 = ph1 * ph1, a2 = ph2 * ph2, a3 = ph3 * ph3;
-        const T d1 = T(2) * ph1 * (P.s12 * a2 + P.s13 * a3) + ph2 * ph3 * gp + P.gam[0] * q3 +
-                     T(2) * P.eta * ph1 * a2 * a3;
-        const T d2 = T(2) * ph2 * (P.s12 * a1 + P.s23 * a3) + ph1 * ph3 * gp + P.gam[1] * q3 +
-                     T(2) * P.eta * a1 * ph2 * a3;
-        const T d3 = T(2) * ph3 * (P.s13 * a1 + P.s23 * a2) + ph1 * ph2 * gp + P.gam[2] * q3 +
-                     T(2) * P.eta * a1 * a2 * ph3;
-        const T m1 = P.twelve_over_xi * d1 - P.lap_coef[0] * l1;
-        const T m2 = P.twelve_over_xi * d2 - P.lap_coef[1] * l2;
-        const T m3 = P.twelve_over_xi * d3 - P.lap_coef[2] * l3;
+        const R gp = P.gam[0] * ph1 + P.gam[1] * ph2 + P.gam[2] * ph3;
+        const R q3 = ph1 * ph2 * ph3;
+        const R a1 = ph1 * ph1, a2 = ph2 * ph2, a3 = ph3 * ph3;
+        const R d1 = B(2) * ph1 * (P.s12 * a2 + P.s13 * a3) + ph2 * ph3 * gp + P.gam[0] * q3 +
+                     B(2) * P.eta * ph1 * a2 * a3;
+        const R d2 = B(2) * ph2 * (P.s12 * a1 + P.s23 * a3) + ph1 * ph3 * gp + P.gam[1] * q3 +
+                     B(2) * P.eta * a1 * ph2 * a3;
+        const R d3 = B(2) * ph3 * (P.s13 * a1 + P.s23 * a2) + ph1 * ph2 * gp + P.gam[2] * q3 +
+                     B(2) * P.eta * a1 * a2 * ph3;
+        const R m1 = P.twelve_over_xi * d1 - P.lap_coef[0] * l1;
+        const R m2 = P.twelve_over_xi * d2 - P.lap_coef[1] * l2;
+        const R m3 = P.twelve_over_xi * d3 - P.lap_coef[2] * l3;
         Fx = m1 * g1x + m2 * g2x + m3 * g3x;
         Fy = m1 * g1y + m2 * g2y + m3 * g3y;
     }
     // Kelvin force F_m = -(1/2) |H|^2 grad chi (Eq. 7); grad chi by Eq. 9 with
     // grad phi_3 = -(grad phi_1 + grad phi_2); H = H0 e_alpha - grad psi' (Eq. 5).
     {
-        const T kk = cdiv(T(1), P.ik[0] * h1 + P.ik[1] * h2 + P.ik[2] * h3);
-        const T gcx = -kk * kk * (P.dk1 * g1x + P.dk2 * g2x);
-        const T gcy = -kk * kk * (P.dk1 * g1y + P.dk2 * g2y);
-        const T Hx = P.H0c - dpx, Hy = P.H0s - dpy;
-        const T hh = T(0.5) * (Hx * Hx + Hy * Hy);
+        const R kk = cdiv(R(B(1)), P.ik[0] * h1 + P.ik[1] * h2 + P.ik[2] * h3);
+        const R gcx = -kk * kk * (P.dk1 * g1x + P.dk2 * g2x);
+        const R gcy = -kk * kk * (P.dk1 * g1y + P.dk2 * g2y);
+        const R Hx = P.H0c - dpx, Hy = P.H0s - dpy;
+        const R hh = B(0.5) * (Hx * Hx + Hy * Hy);
         Fx -= hh * gcx;
         Fy -= hh * gcy;
     }
 
     // Populations.
-    T f[9];
+    R f[9];
 #pragma unroll
     for (int a = 0; a < 9; a++) {
-        if constexpr (EARLY) f[a] = T(fpre[a]) - f_off<MODE, T>(a);
-        else f[a] = T(fs[a * ps + n]) - f_off<MODE, T>(a);
+        if constexpr (EARLY) f[a] = R(fpre[a]) - f_off<MODE, B>(a);
+        else f[a] = ld_pop<R>(fs, a, 9, (int)ps, (int)n) - f_off<MODE, B>(a);
     }
-    const T pst = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
-    const T jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-    const T jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
-    const T mpxx = (f[1] + f[3]) - (f[2] + f[4]);
-    const T mpxy = (f[5] + f[7]) - (f[6] + f[8]);
-    const T me = T(2) * ((f[5] + f[6]) + (f[7] + f[8])) - ((f[1] + f[2]) + (f[3] + f[4])) -
-                 T(4) * f[0];
+    const R pst = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+    const R jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+    const R jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+    const R mpxx = (f[1] + f[3]) - (f[2] + f[4]);
+    const R mpxy = (f[5] + f[7]) - (f[6] + f[8]);
+    const R me = B(2) * ((f[5] + f[6]) + (f[7] + f[8])) - ((f[1] + f[2]) + (f[3] + f[4])) -
+                 B(4) * f[0];
 
     // Pressure (F_p = -(p/rho) grad rho with p = rho c_s^2 p*) and driving force.
-    Fx += -pst * T(1.0 / 3.0) * grx + P.G;
-    Fy += -pst * T(1.0 / 3.0) * gry;
-    const T inv_rho = cdiv(T(1), rho), half_inv_rho = T(0.5) * inv_rho;
-    const T upx = jx + Fx * half_inv_rho, upy = jy + Fy * half_inv_rho;
-    const T tau = P.tau[0] * h1 + P.tau[1] * h2 + P.tau[2] * h3;
-    const T snu = cdiv(T(1), T(0.5) + tau);
+    Fx += -pst * B(1.0 / 3.0) * grx + P.G;
+    Fy += -pst * B(1.0 / 3.0) * gry;
+    const R inv_rho = cdiv(R(B(1)), rho), half_inv_rho = B(0.5) * inv_rho;
+    const R upx = jx + Fx * half_inv_rho, upy = jy + Fy * half_inv_rho;
+    const R tau = P.tau[0] * h1 + P.tau[1] * h2 + P.tau[2] * h3;
+    const R snu = cdiv(R(B(1)), B(0.5) + tau);
     // Viscous force from the non-equilibrium stress (moments of f - f^eq(p*, u')):
     // Pi = (1/6) m_e + (1/2) s_nu m_pxx on the diagonal, s_nu m_pxy off it.
     {
-        const T he = me - (T(3) * (upx * upx + upy * upy) - T(2) * pst);
-        const T hxx = mpxx - (upx * upx - upy * upy);
-        const T hxy = mpxy - upx * upy;
-        const T Pxx = he * T(1.0 / 6.0) + T(0.5) * snu * hxx;
-        const T Pyy = he * T(1.0 / 6.0) - T(0.5) * snu * hxx;
-        const T Pxy = snu * hxy;
-        const T Fmx = -tau * (Pxx * grx + Pxy * gry);
-        const T Fmy = -tau * (Pxy * grx + Pyy * gry);
+        const R he = me - (B(3) * (upx * upx + upy * upy) - B(2) * pst);
+        const R hxx = mpxx - (upx * upx - upy * upy);
+        const R hxy = mpxy - upx * upy;
+        const R Pxx = he * B(1.0 / 6.0) + B(0.5) * snu * hxx;
+        const R Pyy = he * B(1.0 / 6.0) - B(0.5) * snu * hxx;
+        const R Pxy = snu * hxy;
+        const R Fmx = -tau * (Pxx * grx + Pxy * gry);
+        const R Fmy = -tau * (Pxy * grx + Pyy * gry);
         Fx += Fmx;
         Fy += Fmy;
     }
-    const T ux = jx + Fx * half_inv_rho, uy = jy + Fy * half_inv_rho;
-    const T uu = T(1.5) * (ux * ux + uy * uy);
+    const R ux = jx + Fx * half_inv_rho, uy = jy + Fy * half_inv_rho;
+    const R uu = B(1.5) * (ux * ux + uy * uy);
 
     if (A.macro) {
-        A.macro[n] = ux;
-        A.macro[ps + n] = uy;
-        A.macro[2 * ps + n] = pst;
+        A.macro[n] = value(ux);
+        A.macro[ps + n] = value(uy);
+        A.macro[2 * ps + n] = value(pst);
     }
 
     // Breakup: the core (phi_1 >= 1/2) touches the carrier (phi_3 >= 1/2) at a
     // D2Q9 neighbour inside the channel; keep the first (step, y, x).
-    if (A.brk && h1 >= T(0.5) && *((volatile unsigned long long *)A.brk) == ~0ull) {
+    if (A.brk && h1 >= B(0.5) && *((volatile unsigned long long *)A.brk) == ~0ull) {
         bool touch = false;
 #pragma unroll
         for (int a = 1; a < 9; a++) {
             int yy = y + cy(a);
             if (yy < 0 || yy >= ny) continue;
-            T q1 = s1[ly + cy(a)][lx + cx(a)], q2 = s2[ly + cy(a)][lx + cx(a)];
-            touch |= clamp01(T(1) - q1 - q2) >= T(0.5);
+            const R q1 = s1[ly + cy(a)][lx + cx(a)], q2 = s2[ly + cy(a)][lx + cx(a)];
+            touch |= clamp01(B(1) - q1 - q2) >= B(0.5);
         }
         if (touch) {
             unsigned long long key = ((unsigned long long)(*A.step) << 32) |
@@ -267,8 +319,8 @@ __global__ void __launch_bounds__(TX *TY, (MODE == MODE_FP64 ? 1 : 4)) collide_k
         }
     }
 
-    // Push streaming: 32-bit offsets (27 planes fit in 2^31 elements, checked at
-    // create), x-neighbour deltas with the periodic seam folded in, and wall
+    // Push streaming: 32-bit offsets (every plane fits in 2^31 elements, checked
+    // at create), x-neighbour deltas with the periodic seam folded in, and wall
     // flags that are uniform across a warp (a warp is one tile row).
     const int n32 = y * pitch + x, ps32 = (int)ps;
     const int dxp = (x == nx - 1) ? 1 - nx : 1, dxm = (x == 0) ? nx - 1 : -1;
@@ -280,43 +332,43 @@ __global__ void __launch_bounds__(TX *TY, (MODE == MODE_FP64 ? 1 : 4)) collide_k
 
     // Deviation of the equilibria from rest, D_a = 3 e.u + 4.5 (e.u)^2 - 1.5 u.u:
     // f^eq = w (p* + D) (Eq. 16), Gamma = w (1 + D) (Eq. 18).
-    T dev[9];
+    R dev[9];
 #pragma unroll
     for (int a = 0; a < 9; a++) {
-        const T eu = T(cx(a)) * ux + T(cy(a)) * uy;
-        dev[a] = T(3) * eu + T(4.5) * eu * eu - uu;
+        const R eu = B(cx(a)) * ux + B(cy(a)) * uy;
+        dev[a] = B(3) * eu + B(4.5) * eu * eu - uu;
     }
 
     // MRT collision in closed form and push streaming of f.
     S *fd = static_cast<S *>(A.f_dst);
-    const T dxx = mpxx - (ux * ux - uy * uy);
-    const T dxy = mpxy - ux * uy;
-    const T rel = (T(1) - snu) * T(0.25);
-    const T fr = T(3) * inv_rho;
-    const T Ftx = T(0.5) * Fx * fr, Fty = T(0.5) * Fy * fr;
+    const R dxx = mpxx - (ux * ux - uy * uy);
+    const R dxy = mpxy - ux * uy;
+    const R rel = (B(1) - snu) * B(0.25);
+    const R fr = B(3) * inv_rho;
+    const R Ftx = B(0.5) * Fx * fr, Fty = B(0.5) * Fy * fr;
 #pragma unroll
     for (int a = 0; a < 9; a++) {
-        const T w = wgt<T>(a);
-        T v = w * ((pst + dev[a]) + (T(cx(a)) * Ftx + T(cy(a)) * Fty));
-        const T rxx = (a == 1 || a == 3) ? T(1) : ((a == 2 || a == 4) ? T(-1) : T(0));
-        const T rxy = (a == 5 || a == 7) ? T(1) : ((a == 6 || a == 8) ? T(-1) : T(0));
+        const B w = wgt<B>(a);
+        R v = w * ((pst + dev[a]) + (B(cx(a)) * Ftx + B(cy(a)) * Fty));
+        const B rxx = (a == 1 || a == 3) ? B(1) : ((a == 2 || a == 4) ? B(-1) : B(0));
+        const B rxy = (a == 5 || a == 7) ? B(1) : ((a == 6 || a == 8) ? B(-1) : B(0));
         v += rel * (rxx * dxx + rxy * dxy);
-        if (walled(a)) fd[opp(a) * ps32 + n32] = S(v + f_off<MODE, T>(opp(a)));
-        else fd[a * ps32 + dest(a)] = S(v + f_off<MODE, T>(a));
+        if (walled(a)) st_pop(fd, opp(a), 9, ps32, n32, v + f_off<MODE, B>(opp(a)));
+        else st_pop(fd, a, 9, ps32, dest(a), v + f_off<MODE, B>(a));
     }
 
     // Phase fields (Eqs. 29-31): g* = (1 - om) g + om phi Gamma + (1 - om/2) F^phi,
     // F^phi_a = w_a e_a . q_i, q_i = theta_i n_i - (1/3) sum_j theta_j n_j.
-    T qx[2], qy[2];
+    R qx[2], qy[2];
     {
-        const T t1 = P.four_over_xi * h1 * (T(1) - h1);
-        const T t2 = P.four_over_xi * h2 * (T(1) - h2);
-        const T t3 = P.four_over_xi * h3 * (T(1) - h3);
-        const T i1 = cdiv(t1, sqrt(g1x * g1x + g1y * g1y) + P.eps_n);
-        const T i2 = cdiv(t2, sqrt(g2x * g2x + g2y * g2y) + P.eps_n);
-        const T i3 = cdiv(t3, sqrt(g3x * g3x + g3y * g3y) + P.eps_n);
-        const T mx = (i1 * g1x + i2 * g2x + i3 * g3x) * T(1.0 / 3.0);
-        const T my = (i1 * g1y + i2 * g2y + i3 * g3y) * T(1.0 / 3.0);
+        const R t1 = P.four_over_xi * h1 * (B(1) - h1);
+        const R t2 = P.four_over_xi * h2 * (B(1) - h2);
+        const R t3 = P.four_over_xi * h3 * (B(1) - h3);
+        const R i1 = cdiv(t1, sqrt(g1x * g1x + g1y * g1y) + P.eps_n);
+        const R i2 = cdiv(t2, sqrt(g2x * g2x + g2y * g2y) + P.eps_n);
+        const R i3 = cdiv(t3, sqrt(g3x * g3x + g3y * g3y) + P.eps_n);
+        const R mx = (i1 * g1x + i2 * g2x + i3 * g3x) * B(1.0 / 3.0);
+        const R my = (i1 * g1y + i2 * g2y + i3 * g3y) * B(1.0 / 3.0);
         qx[0] = i1 * g1x - mx;
         qy[0] = i1 * g1y - my;
         qx[1] = i2 * g2x - mx;
@@ -325,18 +377,18 @@ __global__ void __launch_bounds__(TX *TY, (MODE == MODE_FP64 ? 1 : 4)) collide_k
     S *gd = static_cast<S *>(A.g_dst);
 #pragma unroll
     for (int i = 0; i < 2; i++) {
-        const T phi = i == 0 ? ph1 : ph2;
-        const T ophi = P.om_phi * phi;
-        const T sqx = P.src_phi * qx[i], sqy = P.src_phi * qy[i];
+        const R phi = i == 0 ? ph1 : ph2;
+        const R ophi = P.om_phi * phi;
+        const R sqx = P.src_phi * qx[i], sqy = P.src_phi * qy[i];
 #pragma unroll
         for (int a = 0; a < 9; a++) {
-            const T w = wgt<T>(a);
-            T gv;
-            if constexpr (EARLY) gv = T(gpre[i * 9 + a]) - g_off<MODE, T>(a);
-            else gv = T(gs[(i * 9 + a) * ps32 + n32]) - g_off<MODE, T>(a);
-            const T v = P.keep_phi * gv + w * (ophi * (T(1) + dev[a]) + (T(cx(a)) * sqx + T(cy(a)) * sqy));
-            if (walled(a)) gd[(i * 9 + opp(a)) * ps32 + n32] = S(v + g_off<MODE, T>(opp(a)));
-            else gd[(i * 9 + a) * ps32 + dest(a)] = S(v + g_off<MODE, T>(a));
+            const B w = wgt<B>(a);
+            R gv;
+            if constexpr (EARLY) gv = R(gpre[i * 9 + a]) - g_off<MODE, B>(a);
+            else gv = ld_pop<R>(gs, i * 9 + a, 18, ps32, n32) - g_off<MODE, B>(a);
+            const R v = P.keep_phi * gv + w * (ophi * (B(1) + dev[a]) + (B(cx(a)) * sqx + B(cy(a)) * sqy));
+            if (walled(a)) st_pop(gd, i * 9 + opp(a), 18, ps32, n32, v + g_off<MODE, B>(opp(a)));
+            else st_pop(gd, i * 9 + a, 18, ps32, dest(a), v + g_off<MODE, B>(a));
         }
     }
 }
@@ -471,6 +523,11 @@ template <typename T>
 void launch_collide(int mode, const LbmArgs<T> &a, cudaStream_t s) {
     dim3 b(TX, TY), gr = grid2(a.P.nx, a.P.ny, b);
     FCD_MODE_SWITCH(mode, T, (collide_kernel<T, M><<<gr, b, 0, s>>>(a)));
+}
+
+void launch_collide_tangent(const LbmArgs<double, DualT> &a, cudaStream_t s) {
+    dim3 b(TX, tile_y<MODE_TANGENT>()), gr = grid2(a.P.nx, a.P.ny, b);
+    collide_kernel<double, MODE_TANGENT><<<gr, b, 0, s>>>(a);
 }
 
 template <typename T>

@@ -204,7 +204,8 @@ __global__ void __launch_bounds__(256) resid0_restrict(Level<T> L0, Level<T> L1,
             auto kat = [&](int dx, int dy) { return sk[ly + dy][lx + dx]; };
             auto pat = [&](int dx, int dy) { return sp[ly + dy][lx + dx]; };
             const Node9<T> nd = node9<T>(kat, j, ny, H0c, H0s);
-            const T r = nd.b - (off9<T>(nd, pat, j, ny) - nd.diag * sp[ly][lx]);
+            const T bb = L0.rhs ? L0.rhs[(long long)j * pitch + i] : nd.b;
+            const T r = bb - (off9<T>(nd, pat, j, ny) - nd.diag * sp[ly][lx]);
             sum += r;
             ksum += sk[ly][lx];
             const T ar = fabs(r);
@@ -282,6 +283,7 @@ __global__ void __launch_bounds__(SX *SY) smooth0(Level<T> L0, Level<T> L1, int 
     if (own) {
         auto kat = [&](int dx, int dy) { return sk[ly + dy][lx + dx]; };
         nd = node9<T>(kat, y, ny, H0c, H0s);
+        if (L0.rhs) nd.b = L0.rhs[(long long)y * pitch + x];
         inv_diag = T(1) / nd.diag;
     }
     const int colour = (x & 1) + 2 * (y & 1);
@@ -889,6 +891,99 @@ int mg_kernels_per_cycle(const MgHost<T> *m) { return 2 + 3 * (m->lc - 1); }  //
 template <typename T>
 int mg_levels(const MgHost<T> *m) { return m->nl; }
 
+// ------------------------------------------------------------ tangent solves
+template <typename T>
+void mg_set_rhs(MgHost<T> *m, const T *rhs) { m->lv[0].rhs = rhs; }
+
+// The reset the phase kernel performs at the start of a solve, with the
+// tolerance scaled by max |rhs| of the tangent right-hand side.
+__global__ void mg_reset_kernel(MgCtl *c, const unsigned long long *scale_bits, double tol,
+                                int max_iter) {
+    c->norm_bits = 0ull;
+    c->iter = 0;
+    c->done = 0;
+    c->converged = 0;
+    c->tolH0 = tol * __longlong_as_double((long long)*scale_bits);
+    c->max_iter = max_iter;
+    c->keep_going = 1;
+    c->blocks_done = 0u;
+    c->mode = 1;
+    c->smooth_left = 0;
+    c->twogrid_left = 2;
+}
+
+void mg_reset_scaled(MgCtl *ctl, const unsigned long long *scale_bits, double tol, int max_iter,
+                     cudaStream_t s) {
+    mg_reset_kernel<<<1, 1, 0, s>>>(ctl, scale_bits, tol, max_iter);
+}
+
+// Differentiating L(k)(psi0 + psi') = 0 along one parameter direction:
+// L(k) dpsi' = b(k, dH0) + b(dk, H0) - L(dk) psi', where b(k, H0) = -L(k) psi0
+// is bilinear and L is linear in k, boundary rows included.
+__global__ void __launch_bounds__(256) tangent_rhs_kernel(Level<double> L0, const double *dk,
+                                                          double H0c, double H0s, double dH0c,
+                                                          double dH0s, const MgCtl *ctl, double *rhs,
+                                                          unsigned long long *rmax_bits) {
+    const int nx = L0.nx, ny = L0.ny, pitch = L0.pitch;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    double ar = 0.0;
+    if (x < nx && y < ny) {
+        const double *psi = ctl->cur ? L0.r : L0.e;
+        auto col = [&](int dx) {
+            int xx = x + dx;
+            return xx < 0 ? xx + nx : (xx >= nx ? xx - nx : xx);
+        };
+        auto row = [&](int dy) {
+            const int yy = y + dy;
+            return yy < 0 ? 0 : (yy >= ny ? ny - 1 : yy);  // mirrored ghost rows
+        };
+        auto kat = [&](int dx, int dy) { return L0.k[(long long)row(dy) * pitch + col(dx)]; };
+        auto dkat = [&](int dx, int dy) { return dk[(long long)row(dy) * pitch + col(dx)]; };
+        auto pat = [&](int dx, int dy) { return psi[(long long)(y + dy) * pitch + col(dx)]; };
+        const Node9<double> nk = node9<double>(kat, y, ny, dH0c, dH0s);
+        const Node9<double> nd = node9<double>(dkat, y, ny, H0c, H0s);
+        const long long n = (long long)y * pitch + x;
+        const double Ldk = off9<double>(nd, pat, y, ny) - nd.diag * psi[n];
+        const double r = nk.b + nd.b - Ldk;
+        rhs[n] = r;
+        ar = fabs(r);
+        ar = ar == ar ? ar : INFINITY;
+    }
+    for (int o = 16; o > 0; o >>= 1) ar = fmax(ar, __shfl_xor_sync(0xffffffffu, ar, o));
+    if ((threadIdx.x & 31) == 0 && ar > 0.0) atomic_max_nonneg(rmax_bits, ar);
+}
+
+void mg_tangent_rhs(MgHost<double> *m, const double *dk, double H0c, double H0s, double dH0c,
+                    double dH0s, double *rhs, unsigned long long *rmax_bits, cudaStream_t s) {
+    dim3 b(32, 8);
+    const Level<double> &L0 = m->lv[0];
+    cudaMemsetAsync(rmax_bits, 0, sizeof(unsigned long long), s);
+    tangent_rhs_kernel<<<g2(L0.nx, L0.ny, b), b, 0, s>>>(L0, dk, H0c, H0s, dH0c, dH0s, m->ctl, rhs,
+                                                          rmax_bits);
+}
+
+__global__ void psi_io_kernel(const MgCtl *ctl, double *A, double *B, int op, double *plane,
+                              double *prev, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double *cur = ctl->cur ? B : A;
+    if (op == 0) {
+        plane[i] = cur[i];
+    } else if (op == 1) {
+        cur[i] = plane[i];
+    } else {
+        const double v = plane[i];
+        cur[i] = 2.0 * v - prev[i];
+        prev[i] = v;
+    }
+}
+
+void mg_psi_io(MgHost<double> *m, int op, double *plane, double *prev, cudaStream_t s) {
+    const Level<double> &L0 = m->lv[0];
+    const long long n = (long long)L0.pitch * L0.ny;
+    psi_io_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(m->ctl, L0.e, L0.r, op, plane, prev, n);
+}
+
 #define FCD_MG_INST(T)                                                                          \
     template MgHost<T> *mg_create<T>(int, int, int, T *, T *, T *, MgCtl *,                     \
                                      void *(*)(size_t, void *), void (*)(void *, void *), void *, \
@@ -901,7 +996,8 @@ int mg_levels(const MgHost<T> *m) { return m->nl; }
     template void mg_cycle_twogrid<T>(MgHost<T> *, T, T, cudaStream_t);                          \
     template void mg_presmooth<T>(MgHost<T> *, T, T, cudaStream_t);                              \
     template int mg_kernels_per_cycle<T>(const MgHost<T> *);                                    \
-    template int mg_levels<T>(const MgHost<T> *);
+    template int mg_levels<T>(const MgHost<T> *);                                               \
+    template void mg_set_rhs<T>(MgHost<T> *, const T *);
 FCD_MG_INST(float)
 FCD_MG_INST(double)
 

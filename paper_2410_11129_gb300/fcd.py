@@ -53,6 +53,22 @@ class fcd_obs(C.Structure):
                 for n, _ in self._fields_}
 
 
+DIRECTIONS = ("Bo_m", "Ca", "alpha", "nu_r")  # order of the tangent directions
+
+
+class fcd_tangent_obs(C.Structure):
+    _fields_ = [
+        ("step", C.c_long), ("T_o", C.c_double), ("overlap", C.c_double),
+        ("lx_o", C.c_double), ("ly_o", C.c_double),
+        ("dT_o", C.c_double * 4), ("doverlap", C.c_double * 4),
+        ("dlx_o", C.c_double * 4), ("dly_o", C.c_double * 4),
+    ]
+
+    def as_dict(self):
+        return {n: (list(getattr(self, n)) if n[0] == "d" else getattr(self, n))
+                for n, _ in self._fields_}
+
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 
@@ -88,6 +104,8 @@ _SIGS = {
     "fcd_batch_instance": (C.c_void_p, [C.c_void_p, C.c_int]),
     "fcd_batch_last_error": (C.c_char_p, [C.c_void_p]),
     "fcd_batch_destroy": (None, [C.c_void_p]),
+    "fcd_create_tangent": (C.c_int, [C.POINTER(fcd_params), C.POINTER(C.c_void_p)]),
+    "fcd_tangent_observables": (C.c_int, [C.c_void_p, C.POINTER(fcd_tangent_obs)]),
     "fcd_destroy": (None, [C.c_void_p]),
 }
 
@@ -168,6 +186,8 @@ def use_torch_allocator():
 class Channel:
     """One context of the coupled step (owns the C handle)."""
 
+    _create = "fcd_create"
+
     def __init__(self, cfg, stream=None, torch_alloc=True):
         L = load()
         self.cfg = dict(cfg)
@@ -175,7 +195,7 @@ class Channel:
             use_torch_allocator()
         self.params = make_params(cfg)
         h = C.c_void_p()
-        st = L.fcd_create(C.byref(self.params), C.byref(h))
+        st = getattr(L, self._create)(C.byref(self.params), C.byref(h))
         if st != FCD_OK:
             raise FcdError(st, L.fcd_last_error(None).decode())
         self.h = h
@@ -273,6 +293,75 @@ class Channel:
             self.close()
         except Exception:
             pass
+
+
+class Tangent(Channel):
+    """FP64 context that also carries the derivatives of its state along
+    (Bo_m, Ca, alpha, nu_r) (fcd_create_tangent)."""
+
+    _create = "fcd_create_tangent"
+
+    def tangent_observe(self, allow=()):
+        o = fcd_tangent_obs()
+        st = load().fcd_tangent_observables(self.h, C.byref(o))
+        self.check(st, allow=allow)
+        return o.as_dict()
+
+
+def with_parameters(cfg, theta):
+    """cfg with (Bo_m, Ca, alpha [rad], nu_r) set; nu_r = nu_3 / nu_2 (Eq. 39)."""
+    bo, ca, al, nr = (float(v) for v in theta)
+    out = dict(cfg)
+    out["Bo_m"], out["Ca"], out["alpha"] = bo, ca, al
+    nu = list(cfg["nu"])
+    nu[1] = nu[2] / nr
+    out["nu"] = nu
+    return out
+
+
+def parameters_of(cfg):
+    return (cfg["Bo_m"], cfg["Ca"], cfg["alpha"], cfg["nu"][2] / cfg["nu"][1])
+
+
+def _droplet_function():
+    import torch
+
+    class DropletObservables(torch.autograd.Function):
+        """(T_o, overlap) of cfg after `steps` coupled steps, as a function of
+        theta = (Bo_m, Ca, alpha, nu_r). Forward runs the tangent-linear
+        context; backward applies the 2 x 4 Jacobian it produced."""
+
+        @staticmethod
+        def forward(ctx, theta, cfg, steps):
+            ch = Tangent(with_parameters(cfg, theta.detach().cpu().tolist()))
+            try:
+                if steps:
+                    ch.step(int(steps))
+                o = ch.tangent_observe()
+            finally:
+                ch.close()
+            J = torch.tensor([o["dT_o"], o["doverlap"]], dtype=torch.float64)
+            ctx.save_for_backward(J)
+            return torch.tensor([o["T_o"], o["overlap"]], dtype=torch.float64, device=theta.device)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            (J,) = ctx.saved_tensors
+            g = grad_out.detach().to(device="cpu", dtype=torch.float64) @ J
+            return g.to(device=grad_out.device), None, None
+
+    return DropletObservables
+
+
+_DROPLET_FN = None
+
+
+def droplet_observables(theta, cfg, steps):
+    """Differentiable (T_o, overlap): torch.autograd entry point of the tangent form."""
+    global _DROPLET_FN
+    if _DROPLET_FN is None:
+        _DROPLET_FN = _droplet_function()
+    return _DROPLET_FN.apply(theta, cfg, steps)
 
 
 class _Instance(Channel):
