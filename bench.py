@@ -394,6 +394,12 @@ def run_ours(args):
     }
     if args.large_steps > 0 and args.workload == DEFAULT_WORKLOAD and ws == 1:
         line["large_grid"] = measure_large(args.large_steps, 3, peak, peak_kind)
+    if args.gradient_steps > 0 and args.workload == DEFAULT_WORKLOAD and ws == 1:
+        try:
+            from paper_2410_11129_gb300 import gradient
+            line["gradient"] = gradient.compare(WORKLOADS["800x100"], args.gradient_steps)
+        except Exception as e:  # reported in the line; the headline numbers stand
+            line["gradient"] = {"error": "%s: %s" % (type(e).__name__, e)}
     if args.batched_steps > 0 and args.workload == DEFAULT_WORKLOAD and ws == 1:
         try:
             line["batched"] = measure_batched(args.batched_steps, 3)
@@ -419,6 +425,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--gradient-steps", type=int, default=200,
+                    help="steps of the 800x100 gradient comparison (0: skip)")
     ap.add_argument("--large-steps", type=int, default=20,
                     help="steps timed on the 9600x1200 channel (0: skip)")
     ap.add_argument("--batched-steps", type=int, default=10,

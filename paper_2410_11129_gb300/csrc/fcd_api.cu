@@ -343,17 +343,23 @@ struct Engine : fcd_ctx {
     }
     int pre_kernels() const { return 1; }
 
-    fcd_status host_mg_loop(cudaStream_t s) {
-        mg_presmooth<T>(mg, P.H0c, P.H0s, s);
+    // One solve with host checks between cycles (hierarchy m with control
+    // block c; default: the context's own).
+    fcd_status host_mg_loop(cudaStream_t s, MgHost<T> *m = nullptr, MgCtl *c = nullptr) {
+        if (!m) {
+            m = mg;
+            c = ctl;
+        }
+        mg_presmooth<T>(m, P.H0c, P.H0s, s);
         for (int guard = 0; guard < 1000000; guard++) {
-            mg_cycle_head<T>(mg, P.H0c, P.H0s, 0, 0, 0, s);
+            mg_cycle_head<T>(m, P.H0c, P.H0s, 0, 0, 0, s);
             CK(cudaGetLastError());
-            CK(cudaMemcpyAsync(h_ctl, ctl, sizeof(MgCtl), cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(h_ctl, c, sizeof(MgCtl), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
             if (!h_ctl->keep_going) break;
-            if (h_ctl->mode == 1) mg_cycle_smooth<T>(mg, P.H0c, P.H0s, s);
-            else if (h_ctl->mode == 2) mg_cycle_twogrid<T>(mg, P.H0c, P.H0s, s);
-            else mg_cycle_rest<T>(mg, P.H0c, P.H0s, s);
+            if (h_ctl->mode == 1) mg_cycle_smooth<T>(m, P.H0c, P.H0s, s);
+            else if (h_ctl->mode == 2) mg_cycle_twogrid<T>(m, P.H0c, P.H0s, s);
+            else mg_cycle_rest<T>(m, P.H0c, P.H0s, s);
             CK(cudaGetLastError());
         }
         return FCD_OK;
@@ -375,81 +381,90 @@ struct Engine : fcd_ctx {
         return FCD_OK;
     }
 
+    // The cycle loop of one potential solve as a CUDA-graph while node (stream s
+    // is capturing; the opening sweeps are already captured).
+    fcd_status capture_mg_loop(cudaStream_t s, MgHost<T> *m = nullptr) {
+        if (!m) m = mg;
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t gcap;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t nd = 0;
+        CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &gcap, &deps, nullptr, &nd));
+        cudaGraphConditionalHandle h;
+        CK(cudaGraphConditionalHandleCreate(&h, gcap, 1, cudaGraphCondAssignDefault));
+        cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t wnode;
+        CK(cudaGraphAddNode(&wnode, gcap, deps, nullptr, nd, &cp));
+        // while body: lattice residual, then a switch node holding the rest
+        // of the V-cycle (case 0), lattice sweeps only (case 1) or a
+        // two-grid cycle (case 2); both conditions are set by the residual
+        // kernel
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        cudaGraphConditionalHandle hi;
+        CK(cudaGraphConditionalHandleCreate(&hi, body, 0, cudaGraphCondAssignDefault));
+        cudaStream_t bs;
+        CK(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
+        cudaError_t e1 = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0,
+                                                       cudaStreamCaptureModeThreadLocal);
+        cudaGraph_t out1 = nullptr, out2 = nullptr;
+        if (e1 == cudaSuccess) {
+            mg_cycle_head<T>(m, P.H0c, P.H0s, h, hi, 1, bs);
+            const cudaGraphNode_t *bd = nullptr;
+            size_t bn = 0;
+            cudaStreamCaptureStatus bcs;
+            cudaGraph_t bg;
+            e1 = cudaStreamGetCaptureInfo(bs, &bcs, nullptr, &bg, &bd, nullptr, &bn);
+            cudaGraphNodeParams ip = {cudaGraphNodeTypeConditional};
+            ip.conditional.handle = hi;
+            ip.conditional.type = cudaGraphCondTypeSwitch;
+            ip.conditional.size = 3;
+            cudaGraphNode_t inode;
+            if (e1 == cudaSuccess) e1 = cudaGraphAddNode(&inode, body, bd, nullptr, bn, &ip);
+            if (e1 == cudaSuccess)
+                e1 = cudaStreamUpdateCaptureDependencies(bs, &inode, nullptr, 1,
+                                                         cudaStreamSetCaptureDependencies);
+            cudaError_t e2 = cudaStreamEndCapture(bs, &out1);
+            if (e1 == cudaSuccess) e1 = e2;
+            if (e1 == cudaSuccess)
+                e1 = cudaStreamBeginCaptureToGraph(bs, ip.conditional.phGraph_out[0], nullptr,
+                                                   nullptr, 0, cudaStreamCaptureModeThreadLocal);
+            if (e1 == cudaSuccess) {
+                mg_cycle_rest<T>(m, P.H0c, P.H0s, bs);
+                e1 = cudaStreamEndCapture(bs, &out2);
+            }
+            if (e1 == cudaSuccess)
+                e1 = cudaStreamBeginCaptureToGraph(bs, ip.conditional.phGraph_out[1], nullptr,
+                                                   nullptr, 0, cudaStreamCaptureModeThreadLocal);
+            if (e1 == cudaSuccess) {
+                mg_cycle_smooth<T>(m, P.H0c, P.H0s, bs);
+                e1 = cudaStreamEndCapture(bs, &out2);
+            }
+            if (e1 == cudaSuccess)
+                e1 = cudaStreamBeginCaptureToGraph(bs, ip.conditional.phGraph_out[2], nullptr,
+                                                   nullptr, 0, cudaStreamCaptureModeThreadLocal);
+            if (e1 == cudaSuccess) {
+                mg_cycle_twogrid<T>(m, P.H0c, P.H0s, bs);
+                e1 = cudaStreamEndCapture(bs, &out2);
+            }
+        }
+        cudaStreamDestroy(bs);
+        CK(e1);
+        CK(cudaStreamUpdateCaptureDependencies(s, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+        return FCD_OK;
+    }
+
     // The captured sequence of one step (stream s is in capture mode).
-    fcd_status capture_step(int c, int sm, cudaStream_t s) {
+    virtual fcd_status capture_step(int c, int sm, cudaStream_t s) {
         if (profiling) CK(cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal));
         enqueue_pre(c, s);
         if (profiling) CK(cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal));
         if (magnetic()) {
             mg_presmooth<T>(mg, P.H0c, P.H0s, s);
-            cudaStreamCaptureStatus cs;
-            cudaGraph_t gcap;
-            const cudaGraphNode_t *deps = nullptr;
-            size_t nd = 0;
-            CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &gcap, &deps, nullptr, &nd));
-            cudaGraphConditionalHandle h;
-            CK(cudaGraphConditionalHandleCreate(&h, gcap, 1, cudaGraphCondAssignDefault));
-            cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
-            cp.conditional.handle = h;
-            cp.conditional.type = cudaGraphCondTypeWhile;
-            cp.conditional.size = 1;
-            cudaGraphNode_t wnode;
-            CK(cudaGraphAddNode(&wnode, gcap, deps, nullptr, nd, &cp));
-            // while body: lattice residual, then a switch node holding the rest
-            // of the V-cycle (case 0), lattice sweeps only (case 1) or a
-            // two-grid cycle (case 2); both conditions are set by the residual
-            // kernel
-            cudaGraph_t body = cp.conditional.phGraph_out[0];
-            cudaGraphConditionalHandle hi;
-            CK(cudaGraphConditionalHandleCreate(&hi, body, 0, cudaGraphCondAssignDefault));
-            cudaStream_t bs;
-            CK(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
-            cudaError_t e1 = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0,
-                                                           cudaStreamCaptureModeThreadLocal);
-            cudaGraph_t out1 = nullptr, out2 = nullptr;
-            if (e1 == cudaSuccess) {
-                mg_cycle_head<T>(mg, P.H0c, P.H0s, h, hi, 1, bs);
-                const cudaGraphNode_t *bd = nullptr;
-                size_t bn = 0;
-                cudaStreamCaptureStatus bcs;
-                cudaGraph_t bg;
-                e1 = cudaStreamGetCaptureInfo(bs, &bcs, nullptr, &bg, &bd, nullptr, &bn);
-                cudaGraphNodeParams ip = {cudaGraphNodeTypeConditional};
-                ip.conditional.handle = hi;
-                ip.conditional.type = cudaGraphCondTypeSwitch;
-                ip.conditional.size = 3;
-                cudaGraphNode_t inode;
-                if (e1 == cudaSuccess) e1 = cudaGraphAddNode(&inode, body, bd, nullptr, bn, &ip);
-                if (e1 == cudaSuccess)
-                    e1 = cudaStreamUpdateCaptureDependencies(bs, &inode, nullptr, 1,
-                                                             cudaStreamSetCaptureDependencies);
-                cudaError_t e2 = cudaStreamEndCapture(bs, &out1);
-                if (e1 == cudaSuccess) e1 = e2;
-                if (e1 == cudaSuccess)
-                    e1 = cudaStreamBeginCaptureToGraph(bs, ip.conditional.phGraph_out[0], nullptr,
-                                                       nullptr, 0, cudaStreamCaptureModeThreadLocal);
-                if (e1 == cudaSuccess) {
-                    mg_cycle_rest<T>(mg, P.H0c, P.H0s, bs);
-                    e1 = cudaStreamEndCapture(bs, &out2);
-                }
-                if (e1 == cudaSuccess)
-                    e1 = cudaStreamBeginCaptureToGraph(bs, ip.conditional.phGraph_out[1], nullptr,
-                                                       nullptr, 0, cudaStreamCaptureModeThreadLocal);
-                if (e1 == cudaSuccess) {
-                    mg_cycle_smooth<T>(mg, P.H0c, P.H0s, bs);
-                    e1 = cudaStreamEndCapture(bs, &out2);
-                }
-                if (e1 == cudaSuccess)
-                    e1 = cudaStreamBeginCaptureToGraph(bs, ip.conditional.phGraph_out[2], nullptr,
-                                                       nullptr, 0, cudaStreamCaptureModeThreadLocal);
-                if (e1 == cudaSuccess) {
-                    mg_cycle_twogrid<T>(mg, P.H0c, P.H0s, bs);
-                    e1 = cudaStreamEndCapture(bs, &out2);
-                }
-            }
-            cudaStreamDestroy(bs);
-            CK(e1);
-            CK(cudaStreamUpdateCaptureDependencies(s, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+            const fcd_status st = capture_mg_loop(s);
+            if (st != FCD_OK) return st;
         }
         if (profiling) CK(cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal));
         enqueue_post(c, sm != 0, s);
@@ -830,35 +845,60 @@ struct TangentEngine : Engine<double> {
     Phys<DualT> PT;
     double *psiT = nullptr;   // 1 + NT planes: the step's potential, then its derivatives
     double *dpsiP = nullptr;  // NT planes: derivatives at the previous step (extrapolation)
-    double *rhs = nullptr, *saved = nullptr;
-    unsigned long long *rmax = nullptr, *h_rmax = nullptr;
+    // one multigrid hierarchy per direction (own potential buffers, right-hand
+    // side and control block; the permeability k is the primal one), so that
+    // the NT solves of a step run side by side
+    MgHost<double> *mgt[NT] = {};
+    MgCtl *ctlt[NT] = {};
+    double *tA[NT] = {}, *tB[NT] = {}, *rhst[NT] = {};
+    unsigned long long *rmax = nullptr;  // NT values
+    cudaStream_t side[NT] = {};
+    cudaEvent_t fork = nullptr, join[NT] = {};
     void *tobs = nullptr;
     TanOut *tan_out = nullptr, *h_tan = nullptr;
+    int reported_tangent_nonconv = 0;
 
     ~TangentEngine() override {
-        if (h_rmax) cudaFreeHost(h_rmax);
+        if (stream) cudaStreamSynchronize(stream);
+        cudaDeviceSynchronize();
+        for (int c = 0; c < NT; c++) {
+            if (mgt[c]) mg_destroy(mgt[c]);
+            if (side[c]) cudaStreamDestroy(side[c]);
+            if (join[c]) cudaEventDestroy(join[c]);
+        }
+        if (fork) cudaEventDestroy(fork);
         if (h_tan) cudaFreeHost(h_tan);
     }
 
     fcd_status init() override {
         copies = 1 + NT;
-        use_graph = false;
         pitch = (prm.nx + 31) / 32 * 32;
         ps = (long long)pitch * prm.ny;
         psiT = dalloc((1 + NT) * ps * sizeof(double));
         dpsiP = dalloc(NT * ps * sizeof(double));
-        rhs = dalloc(ps * sizeof(double));
-        saved = dalloc(ps * sizeof(double));
-        rmax = reinterpret_cast<unsigned long long *>(dalloc(sizeof(unsigned long long)));
+        rmax = reinterpret_cast<unsigned long long *>(dalloc(NT * sizeof(unsigned long long)));
         tobs = dalloc(tangent_obs_scratch_bytes(prm.nx));
         tan_out = reinterpret_cast<TanOut *>(dalloc(sizeof(TanOut)));
-        for (void *q : {(void *)psiT, (void *)dpsiP, (void *)rhs, (void *)saved, (void *)rmax, tobs,
-                        (void *)tan_out})
+        for (void *q : {(void *)psiT, (void *)dpsiP, (void *)rmax, tobs, (void *)tan_out})
             if (!q) return fail(FCD_ENOMEM, "device allocation failed");
-        CK(cudaMallocHost(&h_rmax, sizeof(unsigned long long)));
+        for (int c = 0; c < NT; c++) {
+            tA[c] = dalloc(ps * sizeof(double));
+            tB[c] = dalloc(ps * sizeof(double));
+            rhst[c] = dalloc(ps * sizeof(double));
+            ctlt[c] = reinterpret_cast<MgCtl *>(dalloc(sizeof(MgCtl)));
+            if (!tA[c] || !tB[c] || !rhst[c] || !ctlt[c]) return fail(FCD_ENOMEM, "device allocation failed");
+            CK(cudaMemsetAsync(tA[c], 0, ps * sizeof(double), stream));
+            CK(cudaMemsetAsync(tB[c], 0, ps * sizeof(double), stream));
+            CK(cudaMemsetAsync(rhst[c], 0, ps * sizeof(double), stream));
+            CK(cudaMemsetAsync(ctlt[c], 0, sizeof(MgCtl), stream));
+            CK(cudaStreamCreateWithFlags(&side[c], cudaStreamNonBlocking));
+            CK(cudaEventCreateWithFlags(&join[c], cudaEventDisableTiming));
+        }
+        CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
         CK(cudaMallocHost(&h_tan, sizeof(TanOut)));
         CK(cudaMemsetAsync(psiT, 0, (1 + NT) * ps * sizeof(double), stream));
         CK(cudaMemsetAsync(dpsiP, 0, NT * ps * sizeof(double), stream));
+        CK(cudaStreamSynchronize(stream));
         PT = tangent_phys(&prm, make_phys<double>(&prm, D, pitch));
         fcd_status st = Engine<double>::init();  // the initial solve runs the tangent solves too
         if (st != FCD_OK) return st;
@@ -867,36 +907,69 @@ struct TangentEngine : Engine<double> {
         return FCD_OK;
     }
 
-    // The NT tangent potentials for the current phase fields (derivative
-    // planes of k already formed). extrap: start from 2 dpsi(t) - dpsi(t-1).
-    fcd_status tangent_solves(bool extrap, double tol, int max_iter) {
-        cudaStream_t s = stream;
-        if (!magnetic()) return FCD_OK;  // no field: every derivative of psi' stays 0
-        for (int c = 0; c < NT; c++) {
-            double *dk = k + (c + 1) * ps, *dpsi = psiT + (c + 1) * ps, *prev = dpsiP + c * ps;
-            mg_tangent_rhs(mg, dk, P.H0c, P.H0s, PT.H0c.d[c], PT.H0s.d[c], rhs, rmax, s);
-            CK(cudaMemcpyAsync(h_rmax, rmax, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
-            host_kernels += 1;
-            if (*h_rmax == 0ull) {  // nothing drives this derivative
-                CK(cudaMemsetAsync(dpsi, 0, ps * sizeof(double), s));
-                if (extrap) CK(cudaMemsetAsync(prev, 0, ps * sizeof(double), s));
-                continue;
-            }
-            mg_psi_io(mg, 0, saved, nullptr, s);  // the primal potential
-            if (extrap) mg_psi_io(mg, 2, dpsi, prev, s);
-            else mg_psi_io(mg, 1, dpsi, nullptr, s);
-            mg_reset_scaled(ctl, rmax, tol, max_iter, s);
-            mg_set_rhs<double>(mg, rhs);
-            const fcd_status st = host_mg_loop(s);
-            mg_set_rhs<double>(mg, nullptr);
-            if (st != FCD_OK) return st;
-            mg_psi_io(mg, 0, dpsi, nullptr, s);
-            mg_psi_io(mg, 1, saved, nullptr, s);
-            host_kernels += 5;
-            CK(cudaGetLastError());
+    // Hierarchies of the tangent solves, made once the primal one exists.
+    fcd_status make_tangent_mg() {
+        for (int c = 0; c < NT && !mgt[c]; c++) {
+            mgt[c] = mg_create<double>(prm.nx, prm.ny, pitch, k, tA[c], tB[c], ctlt[c], alloc,
+                                       release, user, err, sizeof err);
+            if (!mgt[c]) return FCD_ENOMEM;
+            mg_set_rhs<double>(mgt[c], rhst[c]);
         }
         return FCD_OK;
+    }
+
+    // The NT tangent potentials for the current phase fields (derivative
+    // planes of k already formed): L(k) dpsi_c = rhs_c on hierarchy c. Graph
+    // capture: NT parallel branches forked from s; host loop: one after the
+    // other on s. extrap: start from 2 dpsi(t) - dpsi(t-1).
+    fcd_status tangent_solves(bool extrap, double tol, int max_iter, cudaStream_t s, bool capture) {
+        if (!magnetic()) return FCD_OK;  // no field: every derivative of psi' stays 0
+        if (make_tangent_mg() != FCD_OK) return FCD_ENOMEM;
+        if (capture) CK(cudaEventRecord(fork, s));
+        for (int c = 0; c < NT; c++) {
+            cudaStream_t sc = s;
+            if (capture) {
+                sc = side[c];
+                CK(cudaStreamWaitEvent(sc, fork, 0));
+            }
+            double *dk = k + (c + 1) * ps, *dpsi = psiT + (c + 1) * ps, *prev = dpsiP + c * ps;
+            mg_tangent_rhs(mg, dk, P.H0c, P.H0s, PT.H0c.d[c], PT.H0s.d[c], rhst[c], rmax + c, sc);
+            if (extrap) mg_psi_io(mgt[c], 2, dpsi, prev, sc);
+            else mg_psi_io(mgt[c], 1, dpsi, nullptr, sc);
+            mg_reset_scaled(ctlt[c], rmax + c, tol, max_iter, sc);
+            fcd_status st;
+            if (capture) {
+                mg_presmooth<double>(mgt[c], P.H0c, P.H0s, sc);
+                st = capture_mg_loop(sc, mgt[c]);
+            } else {
+                st = host_mg_loop(sc, mgt[c], ctlt[c]);
+            }
+            if (st != FCD_OK) return st;
+            mg_psi_io(mgt[c], 0, dpsi, nullptr, sc);
+            CK(cudaGetLastError());
+            if (capture) {
+                CK(cudaEventRecord(join[c], sc));
+                CK(cudaStreamWaitEvent(s, join[c], 0));
+            }
+        }
+        return FCD_OK;
+    }
+
+    // kernels of one step outside the multigrid cycles (those are counted on
+    // the device): two phase kernels, per direction the right-hand side, two
+    // copies and the reset, the potential copy and the collision
+    long step_kernels() const { return 2 + (magnetic() ? 4 * NT : 0) + 2; }
+
+    long launches() const override {
+        long n = Engine<double>::launches();
+        for (int c = 0; c < NT; c++) {
+            if (!mgt[c]) continue;
+            MgCtl q;
+            if (cudaMemcpy(&q, ctlt[c], sizeof q, cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+            n += (long)q.cycles_launched + (long)q.total_cycles * mg_kernels_per_cycle(mgt[c]) +
+                 (long)q.smooth_cycles + 2 * (long)q.twogrid_cycles;
+        }
+        return n;
     }
 
     fcd_status solve(double tol, int max_iter, int *iters, double *resid) override {
@@ -905,44 +978,71 @@ struct TangentEngine : Engine<double> {
         const fcd_status st = Engine<double>::solve(tol, max_iter, iters, resid);
         if (st != FCD_OK && st != FCD_ENOCONV) return st;
         launch_tangent_phase(P, static_cast<const double *>(g[cur]), phi1, phi2, k, stream);
-        host_kernels += 1;
-        const fcd_status st2 = tangent_solves(false, tol, max_iter);
+        host_kernels += 1 + (magnetic() ? 4 * NT : 0);
+        const fcd_status st2 = tangent_solves(false, tol, max_iter, stream, false);
         return st2 != FCD_OK ? st2 : st;
+    }
+
+    // One tangent step on s (host loop, or captured when capture is set).
+    fcd_status enqueue_tangent_step(int c, bool store_macro, cudaStream_t s, bool capture) {
+        enqueue_pre(c, s);
+        launch_tangent_phase(P, static_cast<const double *>(g[c]), phi1, phi2, k, s);
+        if (magnetic()) {
+            fcd_status st;
+            if (capture) {
+                mg_presmooth<double>(mg, P.H0c, P.H0s, s);
+                st = capture_mg_loop(s);
+            } else {
+                st = host_mg_loop(s);
+            }
+            if (st != FCD_OK) return st;
+            st = tangent_solves(true, prm.mag_tol, prm.mag_max_iter, s, capture);
+            if (st != FCD_OK) return st;
+        }
+        mg_psi_io(mg, 0, psiT, nullptr, s);
+        LbmArgs<double, DualT> a;
+        a.P = PT;
+        a.f_src = f[c];
+        a.g_src = g[c];
+        a.f_dst = f[c ^ 1];
+        a.g_dst = g[c ^ 1];
+        a.phi1 = phi1;
+        a.phi2 = phi2;
+        a.psi0 = psiT;
+        a.psi1 = psiT;
+        a.ctl = ctl;
+        a.macro = store_macro ? macro : nullptr;
+        a.brk = brk;
+        a.step = d_step;
+        launch_collide_tangent(a, s);
+        CK(cudaGetLastError());
+        return FCD_OK;
+    }
+
+    fcd_status capture_step(int c, int sm, cudaStream_t s) override {
+        return enqueue_tangent_step(c, sm != 0, s, true);
     }
 
     fcd_status do_step(long n) override {
         if (n < 0) return fail(FCD_EINVAL, "negative step count");
         cudaStream_t s = stream;
         for (long i = 0; i < n; i++) {
-            enqueue_pre(cur, s);
-            launch_tangent_phase(P, static_cast<const double *>(g[cur]), phi1, phi2, k, s);
-            if (magnetic()) {
-                fcd_status st = host_mg_loop(s);
-                if (st != FCD_OK) return st;
-                st = tangent_solves(true, prm.mag_tol, prm.mag_max_iter);
+            const int sm = i == n - 1 ? 1 : 0;
+            if (use_graph) {
+                if (!gexec[cur][sm]) {
+                    const fcd_status st = build_graph(cur, sm);
+                    if (st != FCD_OK) return st;
+                }
+                CK(cudaGraphLaunch(gexec[cur][sm], s));
+            } else {
+                const fcd_status st = enqueue_tangent_step(cur, sm != 0, s, false);
                 if (st != FCD_OK) return st;
             }
-            mg_psi_io(mg, 0, psiT, nullptr, s);
-            LbmArgs<double, DualT> a;
-            a.P = PT;
-            a.f_src = f[cur];
-            a.g_src = g[cur];
-            a.f_dst = f[cur ^ 1];
-            a.g_dst = g[cur ^ 1];
-            a.phi1 = phi1;
-            a.phi2 = phi2;
-            a.psi0 = psiT;
-            a.psi1 = psiT;
-            a.ctl = ctl;
-            a.macro = i == n - 1 ? macro : nullptr;
-            a.brk = brk;
-            a.step = d_step;
-            launch_collide_tangent(a, s);
-            host_kernels += 4;
-            CK(cudaGetLastError());
+            host_kernels += step_kernels();
             cur ^= 1;
             step++;
         }
+        CK(cudaGetLastError());
         return FCD_OK;
     }
 
@@ -956,6 +1056,12 @@ struct TangentEngine : Engine<double> {
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(h_tan, tan_out, sizeof(TanOut), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
+        int nonconv = 0;
+        for (int c = 0; c < NT; c++) {
+            if (!mgt[c]) continue;
+            CK(cudaMemcpy(h_ctl, ctlt[c], sizeof(MgCtl), cudaMemcpyDeviceToHost));
+            nonconv += h_ctl->nonconv_count;
+        }
         std::memset(o, 0, sizeof *o);
         o->step = step;
         o->T_o = h_tan->T_o;
@@ -967,6 +1073,10 @@ struct TangentEngine : Engine<double> {
             o->doverlap[c] = h_tan->doverlap[c];
             o->dlx_o[c] = h_tan->dlx[c];
             o->dly_o[c] = h_tan->dly[c];
+        }
+        if (nonconv > reported_tangent_nonconv) {
+            reported_tangent_nonconv = nonconv;
+            return fail(FCD_ENOCONV, "a tangent potential solve stopped at the cycle cap");
         }
         return st;
     }

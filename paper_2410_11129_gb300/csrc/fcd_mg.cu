@@ -896,14 +896,17 @@ template <typename T>
 void mg_set_rhs(MgHost<T> *m, const T *rhs) { m->lv[0].rhs = rhs; }
 
 // The reset the phase kernel performs at the start of a solve, with the
-// tolerance scaled by max |rhs| of the tangent right-hand side.
+// tolerance scaled by max |rhs| of the tangent right-hand side (the first
+// residual check ends a solve whose right-hand side is zero).
 __global__ void mg_reset_kernel(MgCtl *c, const unsigned long long *scale_bits, double tol,
                                 int max_iter) {
     c->norm_bits = 0ull;
     c->iter = 0;
     c->done = 0;
     c->converged = 0;
-    c->tolH0 = tol * __longlong_as_double((long long)*scale_bits);
+    // a zero right-hand side: the solution is zero and the guess is kept
+    const double scale = __longlong_as_double((long long)*scale_bits);
+    c->tolH0 = scale > 0.0 ? tol * scale : INFINITY;
     c->max_iter = max_iter;
     c->keep_going = 1;
     c->blocks_done = 0u;

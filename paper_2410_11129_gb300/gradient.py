@@ -1,0 +1,93 @@
+"""Gradient of the shell deformation: tangent-linear run against central
+differences of the plain FP64 method, on the same GPU.
+
+  python -m paper_2410_11129_gb300.gradient --steps 20000
+  python -m paper_2410_11129_gb300.gradient --steps 500 --h 1e-4
+
+The tangent context advances the state and its derivatives along
+(Bo_m, Ca, alpha, nu_r) together; central differences need two plain runs per
+direction (eight in all) with theta_j +- h * max(|theta_j|, 1). Both report
+dT_o/dtheta and d overlap/dtheta (overlap = sum phi^_1 phi^_3) at the final
+step; the wall time of each includes every run it needs.
+"""
+import argparse
+import json
+import sys
+import time
+
+import numpy as np
+
+from . import fcd
+from . import workloads as W
+
+
+def _overlap(ch):
+    p1, p2 = ch.field("phi1"), ch.field("phi2")
+    return float(np.sum(np.clip(p1, 0, 1) * np.clip(1.0 - p1 - p2, 0, 1)))
+
+
+def tangent_gradient(cfg, steps):
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ch = fcd.Tangent(cfg)
+    ch.step(steps)
+    o = ch.tangent_observe(allow=(fcd.FCD_ENOCONV,))
+    stats = ch.solver_stats()
+    ch.close()
+    torch.cuda.synchronize()
+    return o, time.perf_counter() - t0, stats
+
+
+def difference_gradient(cfg, steps, h_rel):
+    import torch
+    theta = list(fcd.parameters_of(cfg))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    dT, dO = [], []
+    for j in range(4):
+        h = h_rel * max(abs(theta[j]), 1.0)
+        vals = []
+        for s in (1.0, -1.0):
+            th = list(theta)
+            th[j] += s * h
+            ch = fcd.Channel(fcd.with_parameters(cfg, th))
+            ch.step(steps)
+            ob = ch.observe(allow=(fcd.FCD_ENOCONV,))
+            vals.append((ob["T_o"], _overlap(ch)))
+            ch.close()
+        dT.append((vals[0][0] - vals[1][0]) / (2 * h))
+        dO.append((vals[0][1] - vals[1][1]) / (2 * h))
+    torch.cuda.synchronize()
+    return {"dT_o": dT, "doverlap": dO}, time.perf_counter() - t0
+
+
+def compare(cfg, steps, h_rel=1e-4):
+    cfg = dict(cfg, precision="fp64")
+    o, t_tan, stats = tangent_gradient(cfg, steps)
+    fd, t_fd = difference_gradient(cfg, steps, h_rel)
+    out = {"workload": cfg.get("name", "%dx%d" % (cfg["nx"], cfg["ny"])), "steps": steps,
+           "directions": list(fcd.DIRECTIONS), "mag_tol": cfg["mag_tol"], "h_rel": h_rel,
+           "T_o": o["T_o"], "overlap": o["overlap"],
+           "tangent": {"dT_o": o["dT_o"], "doverlap": o["doverlap"], "seconds": t_tan,
+                       "solver": stats},
+           "central_differences": dict(fd, seconds=t_fd, runs=8),
+           "speedup": t_fd / t_tan}
+    for q in ("dT_o", "doverlap"):
+        a, b = np.array(o[q]), np.array(fd[q])
+        scale = max(np.abs(a).max(), 1e-300)
+        out["max_rel_diff_" + q] = float(np.abs(a - b).max() / scale)
+    return out
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--steps", type=int, default=W.C5["steps"])
+    ap.add_argument("--h", type=float, default=1e-4, help="relative step of the differences")
+    args = ap.parse_args(argv)
+    print(json.dumps(compare(W.C5, args.steps, args.h), indent=1), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

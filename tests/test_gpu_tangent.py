@@ -155,3 +155,21 @@ def test_tangent_rejects_bad_input(fcd):
     with pytest.raises(fcd.FcdError):
         ch.get_state(np.zeros(16, np.uint8))
     ch.close()
+
+
+def test_tangent_graph_and_host_loop_agree(fcd, monkeypatch):
+    """The captured tangent step (five solve loops as graph while nodes) and
+    the host-driven loop give the same bits."""
+    cfg = grad_cfg(mag_tol=1e-10)
+    a = fcd.Tangent(cfg)
+    a.step(20)
+    oa = a.tangent_observe()
+    monkeypatch.setenv("FCD_NO_GRAPH", "1")
+    b = fcd.Tangent(cfg)
+    b.step(20)
+    ob = b.tangent_observe()
+    for x, y in zip(a.populations(), b.populations()):
+        assert np.array_equal(x, y)
+    assert oa == ob
+    a.close()
+    b.close()
