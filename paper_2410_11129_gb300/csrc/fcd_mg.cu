@@ -185,14 +185,33 @@ __global__ void __launch_bounds__(256) resid0_restrict(Level<T> L0, Level<T> L1,
     const int fx0 = L1.cx0[I0], fx1 = L1.cx0[I1], fy0 = L1.cy0[J0], fy1 = L1.cy0[J1];
     const int wx = fx1 - fx0 + 2, wy = fy1 - fy0 + 2;
     const T *psi = ctl->cur ? L0.r : L0.e;
-    for (int t = threadIdx.y * 32 + threadIdx.x; t < wx * wy; t += 256) {
-        const int lx = t % wx, ly = t / wx;
-        int gx = fx0 - 1 + lx;
-        gx = gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx);
-        const int gy = fy0 - 1 + ly;
-        const int my = gy < 0 ? 0 : (gy >= ny ? ny - 1 : gy);
-        sk[ly][lx] = L0.k[(long long)my * pitch + gx];  // mirrored ghost rows
-        sp[ly][lx] = psi[(long long)my * pitch + gx];   // ghost rows never read
+    {  // all loads issued before the shared-memory stores
+        constexpr int NL = (RX * RY + 255) / 256;
+        T kv[NL], pv[NL];
+        const int t0 = threadIdx.y * 32 + threadIdx.x;
+#pragma unroll
+        for (int q = 0; q < NL; q++) {
+            const int t = t0 + q * 256;
+            kv[q] = T(0);
+            pv[q] = T(0);
+            if (t < wx * wy) {
+                const int lx = t % wx, ly = t / wx;
+                int gx = fx0 - 1 + lx;
+                gx = gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx);
+                const int gy = fy0 - 1 + ly;
+                const int my = gy < 0 ? 0 : (gy >= ny ? ny - 1 : gy);
+                kv[q] = L0.k[(long long)my * pitch + gx];  // mirrored ghost rows
+                pv[q] = psi[(long long)my * pitch + gx];   // ghost rows never read
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NL; q++) {
+            const int t = t0 + q * 256;
+            if (t < wx * wy) {
+                sk[t / wx][t % wx] = kv[q];
+                sp[t / wx][t % wx] = pv[q];
+            }
+        }
     }
     __syncthreads();
     const int I = I0 + threadIdx.x, J = J0 + threadIdx.y;
@@ -241,12 +260,18 @@ __global__ void __launch_bounds__(256) resid0_restrict(Level<T> L0, Level<T> L1,
 __device__ void cycle_close(MgCtl *ctl);
 
 // Level-0 block Gauss-Seidel after adding the coarse correction; the last
-// block to finish closes the cycle.
+// block to finish closes the cycle. A 32 x 8 tile runs on 64 threads, each
+// owning one 2 x 2 quad: the quad holds one node of each colour (x0 and y0
+// are even), so in every colour phase every thread updates exactly one node.
+// Same-colour nodes are not 9-point neighbours, so the result does not depend
+// on the order within a phase.
+constexpr int QT = (SX / 2) * (SY / 2);  // threads of a smoothing tile
+constexpr int TILE_LOADS = ((SX + 2) * (SY + 2) + QT - 1) / QT;
+
 template <typename T>
-__global__ void __launch_bounds__(SX *SY) smooth0(Level<T> L0, Level<T> L1, int add_coarse,
-                                                  int sweeps, T H0c, T H0s, MgCtl *ctl,
-                                                  int first) {
-    const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
+__global__ void __launch_bounds__(QT) smooth0(Level<T> L0, Level<T> L1, int add_coarse,
+                                              int sweeps, T H0c, T H0s, MgCtl *ctl, int first) {
+    const int tid = threadIdx.x;
     // first: the sweeps that open a solve (no residual known yet)
     if (block_skip(ctl, first != 0)) return;
     __shared__ T sp[SY + 2][SX + 2];
@@ -257,46 +282,74 @@ __global__ void __launch_bounds__(SX *SY) smooth0(Level<T> L0, Level<T> L1, int 
     T *dst = ctl->cur ? L0.e : L0.r;
     __shared__ ProlongTile<T, SX + 2, SY + 2> pt;
     if (add_coarse) prolong_tile_load(pt, L0, x0 - 1, y0 - 1);
-    for (int t = threadIdx.y * SX + threadIdx.x; t < (SX + 2) * (SY + 2); t += SX * SY) {
-        const int lx = t % (SX + 2), ly = t / (SX + 2);
-        int gx = x0 - 1 + lx;
-        if (gx < 0) gx += nx;
-        while (gx >= nx) gx -= nx;
-        const int gy = y0 - 1 + ly;
-        const int my = gy < 0 ? 0 : (gy >= ny ? ny - 1 : gy);
-        sk[ly][lx] = L0.k[(long long)my * pitch + gx];
-        sp[ly][lx] = (gy >= 0 && gy < ny) ? src[(long long)gy * pitch + gx] : T(0);
+    {  // tile with its frozen one-cell ring: all loads issued before the stores
+        T kv[TILE_LOADS], pv[TILE_LOADS];
+#pragma unroll
+        for (int q = 0; q < TILE_LOADS; q++) {
+            const int t = tid + q * QT;
+            kv[q] = T(0);
+            pv[q] = T(0);
+            if (t < (SX + 2) * (SY + 2)) {
+                const int lx = t % (SX + 2), ly = t / (SX + 2);
+                int gx = x0 - 1 + lx;
+                if (gx < 0) gx += nx;
+                while (gx >= nx) gx -= nx;
+                const int gy = y0 - 1 + ly;
+                const int my = gy < 0 ? 0 : (gy >= ny ? ny - 1 : gy);
+                kv[q] = L0.k[(long long)my * pitch + gx];
+                if (gy >= 0 && gy < ny) pv[q] = src[(long long)gy * pitch + gx];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < TILE_LOADS; q++) {
+            const int t = tid + q * QT;
+            if (t < (SX + 2) * (SY + 2)) {
+                sk[t / (SX + 2)][t % (SX + 2)] = kv[q];
+                sp[t / (SX + 2)][t % (SX + 2)] = pv[q];
+            }
+        }
     }
     __syncthreads();
     if (add_coarse) {  // ghost rows are never read: the mirror is used instead
-        for (int t = threadIdx.y * SX + threadIdx.x; t < (SX + 2) * (SY + 2); t += SX * SY) {
+        for (int t = tid; t < (SX + 2) * (SY + 2); t += QT) {
             const int lx = t % (SX + 2), ly = t / (SX + 2), gy = y0 - 1 + ly;
             if (gy >= 0 && gy < ny) sp[ly][lx] += prolong_at(pt, L1, lx, ly);
         }
         __syncthreads();
     }
-    const int lx = threadIdx.x + 1, ly = threadIdx.y + 1;
-    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
-    const bool own = x < nx && y < ny;
-    Node9<T> nd;
-    T inv_diag = T(0);
-    if (own) {
-        auto kat = [&](int dx, int dy) { return sk[ly + dy][lx + dx]; };
-        nd = node9<T>(kat, y, ny, H0c, H0s);
-        if (L0.rhs) nd.b = L0.rhs[(long long)y * pitch + x];
-        inv_diag = T(1) / nd.diag;
+    const int qx = 2 * (tid % (SX / 2)), qy = 2 * (tid / (SX / 2));
+    Node9<T> nd[4];
+    T inv_diag[4];
+    bool own[4];
+#pragma unroll
+    for (int c = 0; c < 4; c++) {  // colour c = (x & 1) + 2 (y & 1) is quad node (c & 1, c >> 1)
+        const int lx = qx + (c & 1) + 1, ly = qy + (c >> 1) + 1;
+        const int x = x0 + lx - 1, y = y0 + ly - 1;
+        own[c] = x < nx && y < ny;
+        inv_diag[c] = T(0);
+        if (own[c]) {
+            auto kat = [&](int dx, int dy) { return sk[ly + dy][lx + dx]; };
+            nd[c] = node9<T>(kat, y, ny, H0c, H0s);
+            if (L0.rhs) nd[c].b = L0.rhs[(long long)y * pitch + x];
+            inv_diag[c] = T(1) / nd[c].diag;
+        }
     }
-    const int colour = (x & 1) + 2 * (y & 1);
-    auto pat = [&](int dx, int dy) { return sp[ly + dy][lx + dx]; };
     for (int s = 0; s < sweeps; s++) {
+#pragma unroll
         for (int c = 0; c < 4; c++) {
-            if (own && colour == c) sp[ly][lx] = (off9<T>(nd, pat, y, ny) - nd.b) * inv_diag;
+            const int lx = qx + (c & 1) + 1, ly = qy + (c >> 1) + 1, y = y0 + ly - 1;
+            auto pat = [&](int dx, int dy) { return sp[ly + dy][lx + dx]; };
+            if (own[c]) sp[ly][lx] = (off9<T>(nd[c], pat, y, ny) - nd[c].b) * inv_diag[c];
             __syncthreads();
         }
     }
-    if (own) dst[(long long)y * pitch + x] = sp[ly][lx];
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        const int lx = qx + (c & 1) + 1, ly = qy + (c >> 1) + 1;
+        if (own[c]) dst[(long long)(y0 + ly - 1) * pitch + (x0 + lx - 1)] = sp[ly][lx];
+    }
     __syncthreads();
-    if (lead) {
+    if (tid == 0) {
         __threadfence();
         const unsigned total = gridDim.x * gridDim.y;
         if (atomicAdd(&ctl->blocks_done, 1u) == total - 1) {
@@ -856,7 +909,7 @@ void mg_cycle_rest(MgHost<T> *m, T H0c, T H0s, cudaStream_t s) {
     coarse_cta<T><<<1, CTA_THREADS, m->cta_smem, s>>>(m->d_lv, m->lc, m->nl, m->ctl);
     for (int l = m->lc - 1; l >= 1; l--)
         fv_smooth<T, 1><<<g2(lv[l].nx, lv[l].ny, bs), bs, 0, s>>>(lv[l], lv[l + 1], NU_POST, m->ctl);
-    smooth0<T><<<g2(lv[0].nx, lv[0].ny, bs), bs, 0, s>>>(lv[0], lv[1], 1, NU_FINE, H0c, H0s, m->ctl,
+    smooth0<T><<<g2(lv[0].nx, lv[0].ny, bs), QT, 0, s>>>(lv[0], lv[1], 1, NU_FINE, H0c, H0s, m->ctl,
                                                           0);
 }
 
@@ -864,7 +917,7 @@ template <typename T>
 void mg_cycle_smooth(MgHost<T> *m, T H0c, T H0s, cudaStream_t s) {
     dim3 bs(SX, SY);
     const std::vector<Level<T>> &lv = m->lv;
-    smooth0<T><<<g2(lv[0].nx, lv[0].ny, bs), bs, 0, s>>>(lv[0], lv[1], 0, NU_SMOOTH_ONLY, H0c, H0s,
+    smooth0<T><<<g2(lv[0].nx, lv[0].ny, bs), QT, 0, s>>>(lv[0], lv[1], 0, NU_SMOOTH_ONLY, H0c, H0s,
                                                           m->ctl, 0);
 }
 
@@ -872,7 +925,7 @@ template <typename T>
 void mg_presmooth(MgHost<T> *m, T H0c, T H0s, cudaStream_t s) {
     dim3 bs(SX, SY);
     const std::vector<Level<T>> &lv = m->lv;
-    smooth0<T><<<g2(lv[0].nx, lv[0].ny, bs), bs, 0, s>>>(lv[0], lv[1], 0, NU_SMOOTH_ONLY, H0c, H0s,
+    smooth0<T><<<g2(lv[0].nx, lv[0].ny, bs), QT, 0, s>>>(lv[0], lv[1], 0, NU_SMOOTH_ONLY, H0c, H0s,
                                                           m->ctl, 1);
 }
 
@@ -881,7 +934,7 @@ void mg_cycle_twogrid(MgHost<T> *m, T H0c, T H0s, cudaStream_t s) {
     dim3 bs(SX, SY);
     const std::vector<Level<T>> &lv = m->lv;
     fv_smooth<T, 2><<<g2(lv[1].nx, lv[1].ny, bs), bs, 0, s>>>(lv[1], lv[1], NU_TWOGRID, m->ctl);
-    smooth0<T><<<g2(lv[0].nx, lv[0].ny, bs), bs, 0, s>>>(lv[0], lv[1], 1, NU_FINE, H0c, H0s, m->ctl,
+    smooth0<T><<<g2(lv[0].nx, lv[0].ny, bs), QT, 0, s>>>(lv[0], lv[1], 1, NU_FINE, H0c, H0s, m->ctl,
                                                           0);
 }
 
