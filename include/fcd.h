@@ -220,7 +220,7 @@ enum { FCD_DIR_BO_M = 0, FCD_DIR_CA = 1, FCD_DIR_ALPHA = 2, FCD_DIR_NU_R = 3, FC
 typedef struct {
     long step;
     double T_o;                 /* shell deformation (Eq. 42), same value as fcd_observables */
-    double overlap;             /* sum over nodes of phi^_1 phi^_3 (core-carrier overlap) */
+    double overlap;             /* sum over nodes of phi_1 phi_3 (core-carrier overlap, unclamped) */
     double lx_o, ly_o;          /* shell extents along and across the channel */
     double dT_o[FCD_NDIR];      /* dT_o / d(Bo_m, Ca, alpha, nu_r) */
     double doverlap[FCD_NDIR];  /* d overlap / d(...) */

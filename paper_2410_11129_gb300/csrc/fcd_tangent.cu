@@ -1,8 +1,10 @@
 // fcd_tangent.cu -- kernels of the tangent-linear (forward-mode) step that are
 // not shared with the plain step: the derivative planes of Eq. 32, Eq. 8 and
 // the derivatives of the shell deformation T_o (Eq. 42) and of the core-carrier
-// overlap sum_nodes phi^_1 phi^_3 (a smooth proxy of breakup, which happens when
-// the core touches the carrier).
+// overlap sum_nodes phi_1 phi_3 (a smooth proxy of breakup, which happens when
+// the core touches the carrier; unclamped fields, so that the sum is a
+// polynomial of the state: the clamped product has a kink at every bulk node
+// where phi sits at 0 or 1 up to round-off).
 //
 // Layout: every field plane set of the tangent context holds the primal value
 // followed by NT tangent copies; copy c of plane q of an np-plane set sits
@@ -93,9 +95,8 @@ __global__ void __launch_bounds__(TOB) tangent_obs_kernel(int nx, int ny, int pi
             if (i + 1 < ny) {
                 const long long n = (long long)(i + 1) * pitch + x;
                 const DualT p1 = node_phi(g, 0, ps, n), p2 = node_phi(g, 9, ps, n);
-                const DualT h1 = clamp01(p1);
-                b = h1 + clamp01(p2);
-                ovl += h1 * clamp01(DualT(1.0) - p1 - p2);
+                b = clamp01(p1) + clamp01(p2);
+                ovl += p1 * (DualT(1.0) - p1 - p2);
                 const int y = i + 1;
                 if ((ny & 1) ? y == ny / 2 : (y == ny / 2 - 1 || y == ny / 2)) mid += b;
             }

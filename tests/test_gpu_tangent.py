@@ -1,7 +1,7 @@
 """Tangent-linear (forward-mode) derivatives of the coupled step (needs a GB300).
 
 The derivatives of the shell deformation T_o (Eq. 42) and of the core-carrier
-overlap sum phi^_1 phi^_3 along (Bo_m, Ca, alpha, nu_r) are checked against
+overlap sum phi_1 phi_3 along (Bo_m, Ca, alpha, nu_r) are checked against
 (1) Richardson-extrapolated central differences of the FP64 CPU oracle,
 (2) central differences of the plain FP64 GPU path, and (3) the exact zero of
 dT_o/dalpha at alpha = 0 for a droplet on the centre line (mirror symmetry:
@@ -38,8 +38,8 @@ def grad_cfg(**kw):
 
 
 def overlap_of(phi1, phi2):
-    """sum over nodes of clamp(phi_1) clamp(phi_3), phi_3 = 1 - phi_1 - phi_2."""
-    return float(np.sum(np.clip(phi1, 0, 1) * np.clip(1.0 - phi1 - phi2, 0, 1)))
+    """sum over nodes of phi_1 phi_3, phi_3 = 1 - phi_1 - phi_2."""
+    return float(np.sum(phi1 * (1.0 - phi1 - phi2)))
 
 
 def richardson(fun, theta, j, rel=1e-3):
