@@ -81,6 +81,26 @@ __device__ __forceinline__ T cdiv(T a, T b) { return a / b; }
 template <>
 __device__ __forceinline__ float cdiv<float>(float a, float b) { return __fdividef(a, b); }
 
+// Error-free running sum in FP32 (Knuth's TwoSum): hi + lo equals the exact sum
+// of the added values as long as lo stays far from rounding (a few dozen terms).
+struct FSum {
+    float hi = 0.0f, lo = 0.0f;
+    __device__ __forceinline__ void add(float b) {
+        const float s = __fadd_rn(hi, b);
+        const float bb = __fsub_rn(s, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+        hi = s;
+        lo = __fadd_rn(lo, err);
+    }
+    // (this - o) rounded once
+    __device__ __forceinline__ float minus(const FSum &o) const {
+        FSum d;
+        d.hi = hi;
+        d.add(-o.hi);
+        return __fadd_rn(d.hi, __fadd_rn(d.lo, __fsub_rn(lo, o.lo)));
+    }
+};
+
 template <typename R, typename B>
 struct Stencil {
     R c, e, w, n, s, ne, nw, sw, se;
@@ -375,21 +395,41 @@ __global__ void __launch_bounds__(TX *tile_y<MODE>(), collide_min_blocks<MODE>()
         qy[1] = i2 * g2y - my;
     }
     S *gd = static_cast<S *>(A.g_dst);
+    // FP32 offset form: the rest population takes the exact remainder of the
+    // node's pre-collision sum minus its eight stored outgoing populations
+    // (error-free sums), so that the collision conserves each phase's mass up
+    // to one rounding per node; the stored values are offsets by a constant,
+    // so conserving their sum conserves sum_a g.
+    constexpr bool CONSERVE = MODE == MODE_FP32_OFFSET;
 #pragma unroll
     for (int i = 0; i < 2; i++) {
         const R phi = i == 0 ? ph1 : ph2;
         const R ophi = P.om_phi * phi;
         const R sqx = P.src_phi * qx[i], sqy = P.src_phi * qy[i];
+        FSum pre, post;
+        if constexpr (CONSERVE) {
 #pragma unroll
-        for (int a = 0; a < 9; a++) {
+            for (int a = 0; a < 9; a++) pre.add(float(gpre[i * 9 + a]));
+        }
+#pragma unroll
+        for (int a = CONSERVE ? 1 : 0; a < 9; a++) {
             const B w = wgt<B>(a);
             R gv;
             if constexpr (EARLY) gv = R(gpre[i * 9 + a]) - g_off<MODE, B>(a);
             else gv = ld_pop<R>(gs, i * 9 + a, 18, ps32, n32) - g_off<MODE, B>(a);
             const R v = P.keep_phi * gv + w * (ophi * (B(1) + dev[a]) + (B(cx(a)) * sqx + B(cy(a)) * sqy));
-            if (walled(a)) st_pop(gd, i * 9 + opp(a), 18, ps32, n32, v + g_off<MODE, B>(opp(a)));
-            else st_pop(gd, i * 9 + a, 18, ps32, dest(a), v + g_off<MODE, B>(a));
+            const R out = v + g_off<MODE, B>(walled(a) ? opp(a) : a);
+            if constexpr (CONSERVE) {
+                const S sv = S(out);
+                post.add(float(sv));
+                if (walled(a)) gd[(i * 9 + opp(a)) * ps32 + n32] = sv;
+                else gd[(i * 9 + a) * ps32 + dest(a)] = sv;
+            } else {
+                if (walled(a)) st_pop(gd, i * 9 + opp(a), 18, ps32, n32, out);
+                else st_pop(gd, i * 9 + a, 18, ps32, dest(a), out);
+            }
         }
+        if constexpr (CONSERVE) gd[(i * 9) * ps32 + n32] = S(pre.minus(post));
     }
 }
 
