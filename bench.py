@@ -226,10 +226,12 @@ def measure_large(steps, warmup, peak, peak_kind):
                          "algorithmic_bytes_per_launch": bpn * N, "launch_ms": coll / steps}}
 
 
-def oracle_rate(cfg, min_seconds, max_steps, warmup=1):
-    """MLUPS of the FP64 C oracle (single thread) over a bounded sample."""
+def oracle_rate(cfg, min_seconds, max_steps, warmup=1, threads=1):
+    """MLUPS of the FP64 C oracle over a bounded sample, its node loops on
+    `threads` host threads (the results do not depend on the count)."""
     import oracle
     oracle.build()
+    oracle.set_threads(threads)
     sim = oracle.Sim(dict(cfg, mag_max_iter=100000))
     for _ in range(warmup):
         sim.step(1)
@@ -251,6 +253,8 @@ def run_reference(args):
     budget = float(os.environ.get("FCD_REF_BUDGET_S", "150"))
     import oracle
     oracle.build()
+    cores = oracle.max_threads()
+    oracle.set_threads(cores)
     sim = oracle.Sim(dict(cfg, mag_max_iter=100000))
     for _ in range(args.warmup):
         sim.step(1)
@@ -274,8 +278,8 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": cfg["name"], "nx": cfg["nx"], "ny": cfg["ny"],
-                   "mag_tol": cfg["mag_tol"], "parallelism": "host, 1 thread"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+                   "mag_tol": cfg["mag_tol"], "parallelism": "host, %d threads" % cores},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -404,10 +408,14 @@ def run_ours(args):
         except Exception as e:  # reported in the line; the headline numbers stand
             line["batched"] = {"error": "%s: %s" % (type(e).__name__, e)}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.workload == DEFAULT_WORKLOAD:
-        v, n, dt = oracle_rate(cfg, min_seconds=10.0, max_steps=30)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": "%s, %d whole-grid FP64 oracle steps (%.1f s) after "
-                                          "initialisation and one warm-up step" % (cfg["name"], n, dt)}
+        import oracle
+        cores = oracle.max_threads()
+        for threads, key in ((cores, "cpu_baseline"), (1, "cpu_baseline_1thread")):
+            v, n, dt = oracle_rate(cfg, min_seconds=10.0, max_steps=60, threads=threads)
+            line[key] = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": "%s, %d whole-grid FP64 oracle steps (%.1f s) after "
+                                   "initialisation and one warm-up step, %d thread(s)"
+                                   % (cfg["name"], n, dt, threads)}
     ch.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -11,12 +11,31 @@
  * possible (dense 9x9 moment matrices, literal stencil sums, conjugate
  * gradients for the potential). Readings of passages the paper leaves open are
  * marked "reading:" where they are used.
+ *
+ * Threads: when built with OpenMP, the loops over nodes whose iterations write
+ * disjoint outputs run row-parallel (orc_set_threads); sums stay serial, so the
+ * results are bitwise the same for any thread count. The default is 1 thread.
  */
 #include "fcd_oracle.h"
 
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+static int n_threads = 1;
+
+void orc_set_threads(int n) { n_threads = n > 0 ? n : 1; }
+
+int orc_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_num_procs();
+#else
+    return 1;
+#endif
+}
 
 #define Q 9
 #define PI 3.14159265358979323846
@@ -235,6 +254,7 @@ static double clamp01(double v) { return v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v); }
  * 1/(1+chi) = sum_i phi_i/(1+chi_i) (reading: the subscript i restored). */
 void orc_phase(const orc_params *p, const double *g, double *phi, double *k) {
     long N = (long)p->nx * p->ny;
+#pragma omp parallel for schedule(static) num_threads(n_threads)
     for (long n = 0; n < N; n++) {
         double s1 = 0.0, s2 = 0.0;
         for (int a = 0; a < Q; a++) {
@@ -259,6 +279,7 @@ void orc_phase(const orc_params *p, const double *g, double *phi, double *k) {
 void orc_mag_apply(int nx, int ny, const double *k, const double *psi, double H0,
                    double alpha, double *out) {
     double ca = cos(alpha), sa = sin(alpha);
+#pragma omp parallel for schedule(static) num_threads(n_threads)
     for (int y = 0; y < ny; y++)
         for (int x = 0; x < nx; x++) {
             long n = (long)y * nx + x;
@@ -290,6 +311,7 @@ static double dot(const double *a, const double *b, long N) {
 
 static double maxabs(const double *a, long N) {
     double m = 0.0;
+#pragma omp parallel for schedule(static) num_threads(n_threads) reduction(max : m)
     for (long n = 0; n < N; n++) if (fabs(a[n]) > m) m = fabs(a[n]);
     return m;
 }
@@ -319,10 +341,12 @@ int orc_mag_solve(int nx, int ny, const double *k, double H0, double alpha, doub
         int restart = 0;
         while (it < max_iter) {
             orc_mag_apply(nx, ny, k, pd, 0.0, alpha, Ap);
+#pragma omp parallel for schedule(static) num_threads(n_threads)
             for (long n = 0; n < N; n++) Ap[n] = -Ap[n];
             double pAp = dot(pd, Ap, N);
             if (!(pAp > 0.0)) { restart = 1; break; }
             double al = rr / pAp;
+#pragma omp parallel for schedule(static) num_threads(n_threads)
             for (long n = 0; n < N; n++) { psi[n] += al * pd[n]; r[n] -= al * Ap[n]; }
             it++;
             if (maxabs(r, N) <= target) {
@@ -333,7 +357,9 @@ int orc_mag_solve(int nx, int ny, const double *k, double H0, double alpha, doub
                 break;
             }
             double rr2 = dot(r, r, N);
-            for (long n = 0; n < N; n++) pd[n] = r[n] + (rr2 / rr) * pd[n];
+            const double beta = rr2 / rr;
+#pragma omp parallel for schedule(static) num_threads(n_threads)
+            for (long n = 0; n < N; n++) pd[n] = r[n] + beta * pd[n];
             rr = rr2;
         }
         if (!restart) break;
@@ -478,6 +504,7 @@ static void prepare(const orc_params *p, const double *g, step_ctx *c, double *p
     orc_derive(p, &c->d);
     c->N = N;
     orc_phase(p, g, phi, k);
+#pragma omp parallel for schedule(static) num_threads(n_threads)
     for (long n = 0; n < N; n++) {
         double r = 0.0;
         for (int i = 0; i < 3; i++) r += p->rho[i] * clamp01(phi[i * N + n]); /* Eq. 33 */
@@ -581,6 +608,7 @@ int orc_step(const orc_params *p, double *f, double *g, double *psi, double *mac
     double *k = malloc(N * sizeof(double));
     double *fn = malloc(Q * N * sizeof(double)), *gn = malloc(2 * Q * N * sizeof(double));
     int status = 0;
+    build_tables(); /* before the parallel loop: node_update reads them */
     for (long s = 0; s < nsteps; s++) {
         step_ctx c;
         prepare(p, g, &c, phi, rhof, k);
@@ -598,6 +626,8 @@ int orc_step(const orc_params *p, double *f, double *g, double *psi, double *mac
         if (mag_iters) *mag_iters = it;
         if (mag_resid) *mag_resid = res;
         c.psi = psi;
+        /* each node writes its own post-collision values to distinct slots */
+#pragma omp parallel for schedule(static) num_threads(n_threads)
         for (int y = 0; y < ny; y++)
             for (int x = 0; x < nx; x++) {
                 node_out o;

@@ -85,6 +85,10 @@ int orc_step(const orc_params *p, double *f, double *g, double *psi, double *mac
              long step0, long nsteps, orc_track *trk, int *mag_iters, double *mag_resid);
 void orc_observe(const orc_params *p, const double *g, const orc_track *trk,
                  long step, orc_obs *o);
+/* Threads of the row-parallel node loops (1 by default; results are bitwise
+ * the same for any count) and the host's processor count (1 without OpenMP). */
+void orc_set_threads(int n);
+int orc_max_threads(void);
 
 #ifdef __cplusplus
 }

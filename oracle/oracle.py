@@ -79,8 +79,11 @@ def build(force=False):
             return _LIB
         os.makedirs(_BUILD, exist_ok=True)
         tmp = _LIB + ".%d.tmp" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared",
-                               "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-o", tmp, _SRC]
+        try:  # row-parallel node loops when the compiler has OpenMP
+            subprocess.check_call(base + ["-fopenmp", "-lm"], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base + ["-lm"])
         os.replace(tmp, _LIB)
         return _LIB
 
@@ -112,6 +115,10 @@ def lib():
         L.orc_step.argtypes = [C.POINTER(Params), DP, DP, DP, DP, C.c_long, C.c_long,
                                C.POINTER(Track), IP, DP]
         L.orc_step.restype = C.c_int
+        L.orc_set_threads.argtypes = [C.c_int]
+        L.orc_set_threads.restype = None
+        L.orc_max_threads.argtypes = []
+        L.orc_max_threads.restype = C.c_int
         L.orc_observe.argtypes = [C.POINTER(Params), DP, C.POINTER(Track), C.c_long,
                                   C.POINTER(Obs)]
         _lib = L
@@ -317,6 +324,16 @@ class Sim:
 
     def derived(self):
         return derive(self.cfg)
+
+
+def set_threads(n):
+    """Threads of the oracle's row-parallel node loops (results do not depend on it)."""
+    lib().orc_set_threads(int(n))
+
+
+def max_threads():
+    """Host processors usable by the oracle (1 when built without OpenMP)."""
+    return lib().orc_max_threads()
 
 
 def deg(a):

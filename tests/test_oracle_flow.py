@@ -191,3 +191,19 @@ def test_kelvin_force_matches_permeability_gradient(orc):
     assert np.abs(F["Fm_y"] - ref_y).max() < 0.05 * scale
     yc, xc = int(round(cfg["yc"])), int(cfg["xc"])
     assert F["Fm_x"][yc, xc + 5] > 0 and F["Fm_x"][yc, xc - 5] < 0
+
+
+def test_oracle_threads_give_identical_bits(orc):
+    """The row-parallel loops write disjoint outputs and the sums stay serial,
+    so any thread count reproduces the single-thread run bit for bit."""
+    from paper_2410_11129_gb300 import workloads as W
+    cfg = W.small(nx=48, ny=20, r1=3.0, r2=6.0, xc=14.0, xi=4.0, Bo_m=2.0, mag_tol=1e-12)
+    runs = []
+    for n in (1, 4):
+        orc.set_threads(n)
+        sim = orc.Sim(cfg)
+        sim.step(15)
+        runs.append((sim.f.copy(), sim.g.copy(), sim.psi.copy()))
+    orc.set_threads(1)
+    for a, b in zip(*runs):
+        assert np.array_equal(a, b)
