@@ -78,8 +78,18 @@ static const char *derive(const fcd_params *p, Derived *d) {
     d->gam[0] = s12 + s13 - s23;  // Eq. 27
     d->gam[1] = s12 + s23 - s13;
     d->gam[2] = s13 + s23 - s12;
-    for (int i = 0; i < 3; i++)
-        if (!(d->gam[i] > 0)) return "a spreading coefficient gamma_i <= 0 (total spreading)";
+    // Total spreading (some gamma_i < 0, Eq. 27) needs the eta term of Eq. 28,
+    // and a gradient energy sum_i gamma_i |grad phi_i|^2 that stays positive
+    // on sum_i grad phi_i = 0 (gamma1 gamma2 + gamma1 gamma3 + gamma2 gamma3 > 0).
+    if (!(p->eta >= 0)) return "eta must be >= 0";
+    bool total = false;
+    for (int i = 0; i < 3; i++) {
+        if (d->gam[i] == 0.0) return "a spreading coefficient gamma_i is 0 (Eq. 26 undefined)";
+        if (d->gam[i] < 0.0) total = true;
+    }
+    if (total && !(p->eta > 0)) return "total spreading (a gamma_i < 0) needs eta > 0 (Eq. 28)";
+    if (!(d->gam[0] * d->gam[1] + d->gam[0] * d->gam[2] + d->gam[1] * d->gam[2] > 0))
+        return "spreading coefficients give a gradient energy that is not positive";
     d->gamT = 3.0 / (1.0 / d->gam[0] + 1.0 / d->gam[1] + 1.0 / d->gam[2]);  // Eq. 26
     for (int i = 0; i < 3; i++) d->tau[i] = 3.0 * p->nu[i];                // Eq. 14
     d->tau_phi = 3.0 * p->mobility;                                        // Eq. 30

@@ -90,6 +90,23 @@ def regime_sweep(seed=12345, n_len_align=32):
     return out
 
 
+# Table 2 surface-tension ratios (sigma23/sigma12, sigma13/sigma12); sigma23 is
+# the one set by Ca (Eq. 40), so sigma12 = sigma23 / (sigma23/sigma12).
+TABLE2 = {"non-engulfing": (0.30, 0.30), "complete engulfing-type 1": (0.50, 1.70),
+          "partial engulfing": (1.0, 1.0), "complete engulfing-type 2": (1.70, 0.50)}
+
+
+def topology(case, sigma23, eta_over_s12=1.0, **kw):
+    """A channel with the Table 2 ratios of `case` and sigma23 given directly.
+    Three of the four cases are total spreading (one gamma_i < 0), which needs
+    eta > 0 in Eq. 28; eta = eta_over_s12 * sigma12 (the paper gives no value)."""
+    r23, r13 = TABLE2[case]
+    cfg = channel(**kw)
+    cfg.update(sigma23=float(sigma23), s23_over_s12=r23, s13_over_s12=r13,
+               eta=float(eta_over_s12) * sigma23 / r23)
+    return cfg
+
+
 def small(nx=48, ny=20, **kw):
     """Small droplet channel for parity tests: spans several tiles and a ragged tail."""
     base = dict(r1=3.0, r2=6.0, xc=14.0, xi=4.0, Ca=0.1, Bo_m=1.0, ferro="shell",

@@ -35,7 +35,10 @@ def test_library_exports_every_declared_symbol():
 @pytest.mark.parametrize("bad", [
     dict(nx=7), dict(nx=2), dict(ny=1), dict(r1=9.0, r2=6.0), dict(mobility=0.0),
     dict(xi=-1.0), dict(precision=5), dict(mag_tol=0.0),
-    dict(s13_over_s12=3.0),          # gamma_2 < 0: total spreading
+    dict(s13_over_s12=3.0),          # gamma_2 < 0: total spreading without eta
+    dict(s13_over_s12=2.0, eta=0.01),  # gamma_2 = 0
+    dict(s13_over_s12=5.0, eta=0.01),  # gradient energy not positive
+    dict(eta=-0.01),
     dict(ferro="core", chi_ferro=0.0),
 ])
 def test_invalid_parameters_rejected(bad):

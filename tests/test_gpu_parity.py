@@ -140,6 +140,15 @@ def test_mass_conservation_gpu(fcd):
         ch.close()
 
 
+@pytest.mark.parametrize("case", ["non-engulfing", "complete engulfing-type 1"])
+def test_fp64_parity_total_spreading(orc, fcd, case):
+    """Table 2 topologies with a negative spreading coefficient and eta > 0
+    (Eqs. 27-28): the GPU path against the oracle, element by element."""
+    cfg = W.topology(case, 0.005, nx=48, ny=20, r1=3.0, r2=6.0, xc=14.0, xi=4.0, Bo_m=2.0,
+                     ferro="shell", chi_ferro=1.0, mag_tol=1e-13, mag_max_iter=300)
+    compare_fp64(orc, cfg, 60)
+
+
 def test_offset_form_conserves_phase_mass(fcd):
     """The FP32 offset form stores each node's rest population as the exact
     remainder of its pre-collision sum, so its phase masses drift only by one

@@ -106,6 +106,29 @@ def test_laplace_law(orc, pair):
     assert abs(dp * R / d.sigma[i][j] - 1) < 0.03
 
 
+@pytest.mark.parametrize("case,pair", [("complete engulfing-type 1", "13"),
+                                       ("complete engulfing-type 2", "23")])
+def test_laplace_law_total_spreading(orc, case, pair):
+    """Table 2 total-spreading ratios: the absent phase has gamma < 0 and eta > 0
+    (Eq. 28), yet a binary interface carries exactly sigma_ij, since the eta term
+    and the absent phase's gradient term vanish where its phi is zero."""
+    n, R, xi = 64, 16.0, 8.0
+    kw = dict(nx=n, ny=n, xc=n / 2 - 0.5, yc=n / 2 - 0.5, xi=xi, Bo_m=0.0, ferro="none",
+              u_max=0.0)
+    if pair == "13":
+        cfg = W.topology(case, 0.005, r1=R, r2=R, **kw)        # phase 1 in phase 3
+    else:
+        cfg = W.topology(case, 0.005, r1=-1000.0, r2=R, **kw)  # phase 2 in phase 3
+    s = orc.Sim(cfg)
+    d = s.derived()
+    i, j = int(pair[0]) - 1, int(pair[1]) - 1
+    assert min(d.gamma[k] for k in range(3)) < 0 and cfg["eta"] > 0
+    s.step(3000)
+    p = s.macro[2] / 3.0
+    dp = p[n // 2, n // 2] - p[2, 2]
+    assert abs(dp * R / d.sigma[i][j] - 1) < 0.03
+
+
 def _drop_cfg(**kw):
     base = dict(nx=40, ny=20, r1=3.0, r2=6.0, xc=14.0, xi=4.0, Ca=0.1, Bo_m=2.0,
                 ferro="shell", chi_ferro=1.0, mag_tol=1e-13, mag_max_iter=5000)
