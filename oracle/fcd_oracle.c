@@ -127,6 +127,7 @@ void orc_derive(const orc_params *p, orc_derived *d) {
     /* reading: body force giving the Poiseuille centre-line speed u_max
      * between half-way walls a distance ny apart */
     d->G = 8.0 * p->rho[2] * p->nu[2] * p->u_max / ((double)p->ny * p->ny);
+    if (p->open_x) d->G = 0.0; /* the open channel is driven by its inlet */
 }
 
 /* Eq. 18, with the quadratic u.u term over 2 c_s^2 (reading: the printed
@@ -199,13 +200,20 @@ void orc_chem(const orc_derived *d, double eta, double xi, const double *ph,
     }
 }
 
-/* Field access: x periodic; y mirrored about the half-way walls (reading:
- * zero normal gradient of phi at the walls, i.e. a 90 degree contact angle). */
-static double at_mirror(const double *a, int nx, int ny, int x, int y) {
-    x = ((x % nx) + nx) % nx;
+/* Field access: x periodic, or mirrored at the inlet and outlet columns of an
+ * open channel (reading: zero normal gradient there); y mirrored about the
+ * half-way walls (reading: zero normal gradient of phi at the walls, i.e. a
+ * 90 degree contact angle). */
+static double at_mirror_x(const double *a, int nx, int ny, int x, int y, int open) {
+    if (open) x = x < 0 ? 0 : (x >= nx ? nx - 1 : x);
+    else x = ((x % nx) + nx) % nx;
     if (y < 0) y = 0;
     if (y >= ny) y = ny - 1;
     return a[(long)y * nx + x];
+}
+
+static double at_mirror(const double *a, int nx, int ny, int x, int y) {
+    return at_mirror_x(a, nx, ny, x, y, 0);
 }
 
 /* psi' vanishes on the half-way walls (reading): odd reflection. */
@@ -216,13 +224,14 @@ static double at_odd(const double *a, int nx, int ny, int x, int y) {
     return a[(long)y * nx + x];
 }
 
-/* Eq. 34 (c = dx = 1). */
-static void grad_node(const double *a, int nx, int ny, int x, int y, int odd, double *gx,
-                      double *gy) {
+/* Eq. 34 (c = dx = 1). odd: psi' (periodic in x in both channel kinds,
+ * reading); else phi-like fields (mirrored at open ends). */
+static void grad_node_x(const double *a, int nx, int ny, int x, int y, int odd, int open,
+                        double *gx, double *gy) {
     double sx = 0.0, sy = 0.0;
     for (int k = 0; k < Q; k++) {
         double v = odd ? at_odd(a, nx, ny, x + EX[k], y + EY[k])
-                       : at_mirror(a, nx, ny, x + EX[k], y + EY[k]);
+                       : at_mirror_x(a, nx, ny, x + EX[k], y + EY[k], open);
         sx += W[k] * EX[k] * v;
         sy += W[k] * EY[k] * v;
     }
@@ -230,11 +239,21 @@ static void grad_node(const double *a, int nx, int ny, int x, int y, int odd, do
     *gy = sy / CS2;
 }
 
+static void grad_node(const double *a, int nx, int ny, int x, int y, int odd, double *gx,
+                      double *gy) {
+    grad_node_x(a, nx, ny, x, y, odd, 0, gx, gy);
+}
+
 /* Eq. 35. */
-static double lap_node(const double *a, int nx, int ny, int x, int y) {
+static double lap_node_x(const double *a, int nx, int ny, int x, int y, int open) {
     double c = a[(long)y * nx + x], s = 0.0;
-    for (int k = 0; k < Q; k++) s += W[k] * (at_mirror(a, nx, ny, x + EX[k], y + EY[k]) - c);
+    for (int k = 0; k < Q; k++)
+        s += W[k] * (at_mirror_x(a, nx, ny, x + EX[k], y + EY[k], open) - c);
     return 2.0 * s / CS2;
+}
+
+static double lap_node(const double *a, int nx, int ny, int x, int y) {
+    return lap_node_x(a, nx, ny, x, y, 0);
 }
 
 void orc_grad(int nx, int ny, const double *a, double *gx, double *gy) {
@@ -395,8 +414,8 @@ static void node_update(const step_ctx *c, const double *f, const double *g, int
     long N = c->N, n = (long)y * nx + x;
     double ph[3], phc[3], gph[3][2], lph[3];
     for (int i = 0; i < 2; i++) {
-        grad_node(c->phi + i * N, nx, ny, x, y, 0, &gph[i][0], &gph[i][1]);
-        lph[i] = lap_node(c->phi + i * N, nx, ny, x, y);
+        grad_node_x(c->phi + i * N, nx, ny, x, y, 0, p->open_x, &gph[i][0], &gph[i][1]);
+        lph[i] = lap_node_x(c->phi + i * N, nx, ny, x, y, p->open_x);
     }
     /* phi_3 = 1 - phi_1 - phi_2 (Eq. 24), so its derivatives follow. */
     gph[2][0] = -(gph[0][0] + gph[1][0]);
@@ -432,7 +451,7 @@ static void node_update(const step_ctx *c, const double *f, const double *g, int
     double ps = 0.0, jx = 0.0, jy = 0.0;
     for (int a = 0; a < Q; a++) { ps += fl[a]; jx += fl[a] * EX[a]; jy += fl[a] * EY[a]; }
     double rho = c->rhof[n], grx, gry;
-    grad_node(c->rhof, nx, ny, x, y, 0, &grx, &gry);
+    grad_node_x(c->rhof, nx, ny, x, y, 0, p->open_x, &grx, &gry);
     o->Fp[0] = -ps * CS2 * grx;
     o->Fp[1] = -ps * CS2 * gry;
     double Fb[2] = {d->G, 0.0};
@@ -536,7 +555,7 @@ void orc_forces(const orc_params *p, const double *f, const double *g, const dou
 /* reading of "the inner droplet touches the interface of the shell": some node
  * with clamped phi_1 >= 1/2 has a D2Q9 neighbour inside the channel with clamped
  * phi_3 >= 1/2; the reported node is the smallest (y, x). */
-static int find_touch(int nx, int ny, const double *phi, int *bx, int *by) {
+static int find_touch(int nx, int ny, int open, const double *phi, int *bx, int *by) {
     long N = (long)nx * ny;
     for (int y = 0; y < ny; y++)
         for (int x = 0; x < nx; x++) {
@@ -544,7 +563,11 @@ static int find_touch(int nx, int ny, const double *phi, int *bx, int *by) {
             for (int a = 1; a < Q; a++) {
                 int yy = y + EY[a];
                 if (yy < 0 || yy >= ny) continue;
-                int xx = ((x + EX[a]) % nx + nx) % nx;
+                int xx = x + EX[a];
+                if (xx < 0 || xx >= nx) {
+                    if (open) continue;
+                    xx = (xx + nx) % nx;
+                }
                 if (clamp01(phi[2 * N + (long)yy * nx + xx]) >= 0.5) {
                     *bx = x; *by = y;
                     return 1;
@@ -600,6 +623,74 @@ int orc_init(const orc_params *p, double *f, double *g, double *psi, double *mac
 /* One coupled step per iteration, in the order: phases (Eq. 32), permeability
  * (Eq. 8), potential (Eq. 6), forces (Eqs. 5-9, 19, 25, 33-36), velocity
  * (Eq. 22), collisions (Eqs. 12, 29), streaming with half-way bounce-back. */
+/* Open channel: the populations that would enter from outside the channel.
+ * fn, gn: this step's post-streaming values (complete except these); f, g:
+ * the previous step's (before collision). */
+static void open_boundaries(const orc_params *p, const orc_derived *d, const double *f,
+                            const double *g, double *fn, double *gn) {
+    int nx = p->nx, ny = p->ny;
+    long N = (long)nx * ny;
+    for (int y = 0; y < ny; y++) {
+        /* Inlet, Eq. 37 (reading: the Poiseuille parabola with centre-line speed u_max
+         * between the half-way walls, mean u_avg). Zou-He in the velocity-based form:
+         * the unknown populations 1, 5, 8 reflect the non-equilibrium part of their
+         * opposites, f_a = f_opp(a) + f^eq_a - f^eq_opp(a) = f_opp(a) + 6 w_a e_a.u,
+         * with the transverse correction -/+ (f2 - f4)/2 on 5 and 8 that zeroes the
+         * wall-normal momentum. At the two corner nodes the wall supplies one of 5, 8
+         * (bounce-back) and the two unknowns follow from both momentum components. */
+        double u = p->u_max * 4.0 * (y + 0.5) * (ny - 0.5 - y) / ((double)ny * ny);
+        long n = (long)y * nx;
+        double fl[Q];
+        for (int a = 0; a < Q; a++) fl[a] = fn[a * N + n];
+        if (y == 0) {            /* f5 from the wall; solve f8 (j_y = 0), then f1 (j_x = u) */
+            fl[8] = fl[2] - fl[4] + fl[5] + fl[6] - fl[7];
+        } else if (y == ny - 1) { /* f8 from the wall; solve f5, then f1 */
+            fl[5] = fl[4] - fl[2] - fl[6] + fl[7] + fl[8];
+        } else {
+            fl[5] = fl[7] + 6.0 * W[5] * u - 0.5 * (fl[2] - fl[4]);
+            fl[8] = fl[6] + 6.0 * W[8] * u + 0.5 * (fl[2] - fl[4]);
+        }
+        if (y == 0 || y == ny - 1) fl[1] = u + fl[3] - fl[5] + fl[6] + fl[7] - fl[8];
+        else fl[1] = fl[3] + 6.0 * W[1] * u;
+        fn[1 * N + n] = fl[1];
+        fn[5 * N + n] = fl[5];
+        fn[8 * N + n] = fl[8];
+        /* reading: the inflow is pure carrier (phi_1 = phi_2 = 0): zero populations */
+        for (int i = 0; i < 2; i++) {
+            gn[(i * Q + 1) * N + n] = 0.0;
+            if (y != 0) gn[(i * Q + 5) * N + n] = 0.0;
+            if (y != ny - 1) gn[(i * Q + 8) * N + n] = 0.0;
+        }
+        /* Outlet: convective condition d chi/dt + U d chi/dx = 0 (refs. [61, 62]) for
+         * the populations entering from x = nx, upwind in x and implicit in time,
+         * chi(t+1, nx-1) = (chi(t, nx-1) + U chi(t+1, nx-2)) / (1 + U), with U the mean
+         * inflow speed u_avg. reading: for f it acts on f_a - w_a p*, the part
+         * carried by the flow, while the pressure part takes the reference p* = 0
+         * at the outlet (the pressure of this incompressible form is defined up
+         * to a constant). A convective condition on all of f holds p* constant
+         * across the outlet, starves the outflow of developed channel flow and lets
+         * the pressure level drift; linear extrapolation of p* leaves the level
+         * free. g is advected as it is. */
+        long o = n + nx - 1, b = o - 1;
+        double pb = 0.0, po = 0.0;
+        for (int a = 0; a < Q; a++) {
+            pb += fn[a * N + b];
+            po += f[a * N + o];
+        }
+        const double pout = 0.0;
+        double U = d->u_avg;
+        const int in3[3] = {3, 6, 7};
+        for (int k = 0; k < 3; k++) {
+            int a = in3[k];
+            if ((a == 6 && y == 0) || (a == 7 && y == ny - 1)) continue; /* from the wall */
+            double chi = ((f[a * N + o] - W[a] * po) + U * (fn[a * N + b] - W[a] * pb)) / (1.0 + U);
+            fn[a * N + o] = chi + W[a] * pout;
+            for (int i = 0; i < 2; i++)
+                gn[(i * Q + a) * N + o] = (g[(i * Q + a) * N + o] + U * gn[(i * Q + a) * N + b]) / (1.0 + U);
+        }
+    }
+}
+
 int orc_step(const orc_params *p, double *f, double *g, double *psi, double *macro,
              long step0, long nsteps, orc_track *trk, int *mag_iters, double *mag_resid) {
     int nx = p->nx, ny = p->ny;
@@ -614,7 +705,7 @@ int orc_step(const orc_params *p, double *f, double *g, double *psi, double *mac
         prepare(p, g, &c, phi, rhof, k);
         if (trk && trk->b_step < 0) {
             int bx, by;
-            if (find_touch(nx, ny, phi, &bx, &by)) {
+            if (find_touch(nx, ny, p->open_x, phi, &bx, &by)) {
                 trk->b_step = step0 + s; trk->bx = bx; trk->by = by;
             }
         }
@@ -637,7 +728,9 @@ int orc_step(const orc_params *p, double *f, double *g, double *psi, double *mac
                 for (int a = 0; a < Q; a++) {
                     int yy = y + EY[a];
                     if (yy >= 0 && yy < ny) {
-                        int xx = ((x + EX[a]) % nx + nx) % nx;
+                        int xx = x + EX[a];
+                        if (p->open_x && (xx < 0 || xx >= nx)) continue; /* leaves the channel */
+                        xx = (xx % nx + nx) % nx;
                         long m = (long)yy * nx + xx;
                         fn[a * N + m] = o.fpost[a];
                         gn[(0 * Q + a) * N + m] = o.gpost[0][a];
@@ -649,6 +742,7 @@ int orc_step(const orc_params *p, double *f, double *g, double *psi, double *mac
                     }
                 }
             }
+        if (p->open_x) open_boundaries(p, &c.d, f, g, fn, gn);
         memcpy(f, fn, Q * N * sizeof(double));
         memcpy(g, gn, 2 * Q * N * sizeof(double));
     }
@@ -699,7 +793,7 @@ void orc_observe(const orc_params *p, const double *g, const orc_track *trk, lon
     }
     int xcut = 0;
     double best = 0.0;
-    for (int x = 0; x < nx; x++) {
+    for (int x = 0; x < nx && !p->open_x; x++) { /* open channel: the frame starts at the inlet */
         double s = 0.0;
         for (int y = 0; y < ny; y++) s += so[(long)y * nx + x];
         if (x == 0 || s < best) { best = s; xcut = x; }
@@ -735,7 +829,7 @@ void orc_observe(const orc_params *p, const double *g, const orc_track *trk, lon
     }
     long bs = trk ? trk->b_step : -1;
     int bx = trk ? trk->bx : 0, by = trk ? trk->by : 0;
-    if (bs < 0 && find_touch(nx, ny, phi, &bx, &by)) bs = step;
+    if (bs < 0 && find_touch(nx, ny, p->open_x, phi, &bx, &by)) bs = step;
     o->b_step = bs;
     if (bs >= 0) {
         o->breakup = 1;

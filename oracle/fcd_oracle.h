@@ -12,7 +12,8 @@
  *   g              g[(i*9 + a)*ny*nx + y*nx + x] (2*9*ny*nx), i = 0 core, 1 shell
  *   psi            perturbation potential psi' (total psi = psi0 + psi')
  *   macro          [ux | uy | p*] of the last step (3*ny*nx)
- * x is periodic; half-way walls sit at y = -1/2 and y = ny - 1/2.
+ * x is periodic, or (open_x) an inlet at x = 0 and an outlet at x = nx - 1;
+ * half-way walls sit at y = -1/2 and y = ny - 1/2.
  */
 #ifndef FCD_ORACLE_H
 #define FCD_ORACLE_H
@@ -34,6 +35,7 @@ typedef struct {
     double mag_tol;               /* ||L psi||_inf / H0 target per solve */
     int mag_max_iter;             /* CG iteration cap per solve */
     double eps_n;                 /* regulariser of n = grad phi / |grad phi| */
+    int open_x;                   /* 1: velocity inlet (Eq. 37) + convective outlet */
 } orc_params;
 
 typedef struct {

@@ -36,6 +36,7 @@ class Params(C.Structure):
         ("ferro_phase", C.c_int),
         ("mag_tol", C.c_double), ("mag_max_iter", C.c_int),
         ("eps_n", C.c_double),
+        ("open_x", C.c_int),
     ]
 
 
@@ -154,6 +155,7 @@ def make_params(cfg):
     p.mag_tol = cfg.get("mag_tol", 1e-10)
     p.mag_max_iter = int(cfg.get("mag_max_iter", 100000))
     p.eps_n = cfg.get("eps_n", 1e-12)
+    p.open_x = int(cfg.get("open_x", 0))
     return p
 
 

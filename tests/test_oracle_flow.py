@@ -230,3 +230,55 @@ def test_oracle_threads_give_identical_bits(orc):
     orc.set_threads(1)
     for a, b in zip(*runs):
         assert np.array_equal(a, b)
+
+
+def _open_poiseuille(orc, steps):
+    nx, ny = 48, 12
+    cfg = W.channel(nx, ny, -1000.0, -1000.0, xc=0.0, yc=0.0, xi=4.0, Bo_m=0.0, ferro="none",
+                    u_max=0.01, open_x=1)
+    cfg["nu"] = [1 / 8] * 3  # tau = 3/8: half-way bounce-back exact for the parabola
+    orc.set_threads(orc.max_threads())
+    try:
+        s = orc.Sim(cfg)
+        s.step(steps)
+    finally:
+        orc.set_threads(1)
+    return s, nx, ny
+
+
+def test_open_channel_poiseuille(orc):
+    """Velocity inlet (Eq. 37) + convective outlet: the developed flow is the
+    inlet parabola with the closed-form pressure gradient -G / c_s^2,
+    G = 8 rho nu u_max / ny^2 (the body force of the periodic channel), the
+    same flux through every column, and the outlet holds the reference p* = 0."""
+    s, nx, ny = _open_poiseuille(orc, 12000)
+    u, p = s.macro[0], s.macro[2]
+    y = np.arange(ny)
+    exact = 0.01 * 4 * (y + 0.5) * (ny - 0.5 - y) / ny**2
+    inner = range(10, nx - 10)  # away from the entrance and exit layers
+    assert max(np.abs(u[:, x] - exact).max() for x in inner) <= 1e-6 * exact.max()
+    flux = u.sum(axis=0)
+    assert np.abs(flux / exact.sum() - 1).max() <= 1e-9
+    slope = np.polyfit(np.arange(nx // 4, 3 * nx // 4), p[ny // 2, nx // 4:3 * nx // 4], 1)[0]
+    expect = -8 * (1 / 8) * 0.01 / ny**2 / (1 / 3)
+    assert abs(slope / expect - 1) <= 1e-6
+    assert abs(p[ny // 2, nx - 1]) <= 1e-6
+
+
+def test_open_channel_drop_leaves_through_outlet(orc):
+    """A drop advected through the convective outlet leaves completely (no
+    reflection), and the inflow carries no phase 1."""
+    nx, ny = 64, 16
+    cfg = W.channel(nx, ny, 4.0, 4.0, xc=44.0, yc=7.5, xi=4.0, Bo_m=0.0, ferro="none",
+                    u_max=0.05, Ca=0.1, open_x=1)
+    orc.set_threads(orc.max_threads())
+    try:
+        s = orc.Sim(cfg)
+        m0 = s.phi()[0].sum()
+        s.step(3000)
+    finally:
+        orc.set_threads(1)
+    ph = s.phi()[0]
+    assert np.isfinite(s.f).all() and np.isfinite(s.g).all()
+    assert abs(ph.sum()) <= 1e-9 * m0
+    assert np.abs(ph).max() <= 1e-8
