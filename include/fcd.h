@@ -75,6 +75,12 @@ typedef struct {
     double mag_tol;        /* potential solve target ||L psi||_inf / H0 per step */
     int mag_max_iter;      /* multigrid V-cycle cap per solve */
     double eps_n;          /* regulariser of n = grad phi / (|grad phi| + eps_n) */
+    int open_x;            /* 0: periodic channel driven by a body force (u_max).
+                            * 1: the paper's open channel (Sec. 2.5): the Eq. 37
+                            * parabola (centre-line speed u_max) enters at x = 0 as
+                            * pure carrier, a convective outlet at x = nx - 1 holds
+                            * the reference p* = 0; no body force. The potential
+                            * psi' stays periodic in x. Not for tangent contexts. */
 } fcd_params;
 
 /* Observables (Sec. 2.5, Eqs. 38 and 42). */

@@ -65,6 +65,7 @@ static const char *derive(const fcd_params *p, Derived *d) {
     if (p->precision < FCD_FP64 || p->precision > FCD_FP32_OFFSET) return "unknown precision";
     if (!(p->mag_tol > 0) || p->mag_max_iter < 0) return "mag_tol must be > 0, mag_max_iter >= 0";
     if (!(p->eps_n >= 0)) return "eps_n must be >= 0";
+    if (p->open_x != 0 && p->open_x != 1) return "open_x must be 0 or 1";
     if (!(p->s13_over_s12 > 0) || !(p->s23_over_s12 > 0)) return "surface tension ratios must be > 0";
     d->u_avg = 2.0 * p->u_max / 3.0;  // mean of the channel's parabolic profile
     double s23;
@@ -107,6 +108,7 @@ static const char *derive(const fcd_params *p, Derived *d) {
     if (!(d->mu0H0sq >= 0)) return "Bo_m must be >= 0";
     d->H0 = std::sqrt(d->mu0H0sq);
     d->G = 8.0 * p->rho[2] * p->nu[2] * p->u_max / ((double)p->ny * p->ny);
+    if (p->open_x) d->G = 0.0;  // the open channel is driven by its inlet
     return nullptr;
 }
 
@@ -349,8 +351,12 @@ struct Engine : fcd_ctx {
         a.macro = store_macro ? macro : nullptr;
         a.brk = brk;
         a.step = &ctl->step_cur;
+        a.open_x = prm.open_x;
         launch_collide<T>(mode, a, s);
+        if (prm.open_x)
+            launch_open_bc<T>(mode, P, f[c], g[c], f[c ^ 1], g[c ^ 1], prm.u_max, D.u_avg, s);
     }
+    int post_kernels() const { return prm.open_x ? 2 : 1; }
     int pre_kernels() const { return 1; }
 
     // One solve with host checks between cycles (hierarchy m with control
@@ -493,7 +499,7 @@ struct Engine : fcd_ctx {
                     if (st != FCD_OK) return st;
                 }
                 CK(cudaGraphLaunch(gexec[cur][sm], s));
-                host_kernels += pre_kernels() + 1;
+                host_kernels += pre_kernels() + post_kernels();
             } else {
                 if (profiling) CK(cudaEventRecord(ev[0], s));
                 enqueue_pre(cur, s);
@@ -505,7 +511,7 @@ struct Engine : fcd_ctx {
                 if (profiling) CK(cudaEventRecord(ev[2], s));
                 enqueue_post(cur, sm != 0, s);
                 if (profiling) CK(cudaEventRecord(ev[3], s));
-                host_kernels += pre_kernels() + 1;
+                host_kernels += pre_kernels() + post_kernels();
                 CK(cudaGetLastError());
             }
             cur ^= 1;
@@ -552,7 +558,7 @@ struct Engine : fcd_ctx {
 
     fcd_status observe(fcd_obs *o) override {
         cudaStream_t s = stream;
-        launch_observe<T>(mode, P, g[cur], obs_scratch, obs_out, s);
+        launch_observe<T>(mode, P, g[cur], obs_scratch, obs_out, s, prm.open_x);
         host_kernels += 4;
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(h_obs, obs_out, sizeof(ObsOut), cudaMemcpyDeviceToHost, s));
@@ -1158,6 +1164,7 @@ fcd_status fcd_create_tangent(const fcd_params *params, fcd_ctx **out) {
         why = "lattice too large for the tangent copies (90 planes within 2^31 elements)";
     if (!why && p.ferro_phase != 0 && !(p.Bo_m > 0))
         why = "the Bo_m direction needs Bo_m > 0 (H0 ~ sqrt(Bo_m))";
+    if (!why && p.open_x) why = "the open channel is not available for tangent contexts";
     if (why) {
         snprintf(g_last, sizeof g_last, "fcd_create_tangent: %s", why);
         return FCD_EINVAL;

@@ -174,6 +174,7 @@ struct LbmArgs {
     T *macro;                    // nullptr: do not store the macroscopic fields
     unsigned long long *brk;     // sticky breakup key (nullptr: no check)
     const long long *step;       // device step counter (breakup key)
+    int open_x = 0;              // open channel: no wrap in x (see launch_open_bc)
 };
 
 template <typename T>
@@ -182,6 +183,12 @@ void launch_phase(int mode, const Phys<T> &P, const void *g, T *phi1, T *phi2, T
 template <typename T>
 void launch_collide(int mode, const LbmArgs<T> &a, cudaStream_t s);
 void launch_collide_tangent(const LbmArgs<double, DualT> &a, cudaStream_t s);
+// Open channel: the populations entering through the inlet (x = 0) and the
+// outlet (x = nx - 1) after a collide-stream from (f_src, g_src) into
+// (f_dst, g_dst); one thread per row.
+template <typename T>
+void launch_open_bc(int mode, const Phys<T> &P, const void *f_src, const void *g_src,
+                    void *f_dst, void *g_dst, double u_max, double u_avg, cudaStream_t s);
 template <typename T>
 void launch_init(int mode, const Phys<T> &P, double u_max, double r1, double r2, double xc,
                  double yc, double xi, void *f, void *g, T *macro, cudaStream_t s);
@@ -249,6 +256,6 @@ void launch_tangent_obs(const Phys<double> &P, const double *g, const ObsOut *pr
 size_t observe_scratch_doubles(int nx, int ny);
 template <typename T>
 void launch_observe(int mode, const Phys<T> &P, const void *g, double *scratch, ObsOut *out,
-                    cudaStream_t s);
+                    cudaStream_t s, int open_x = 0);
 
 }  // namespace fcd

@@ -175,7 +175,10 @@ __host__ __device__ constexpr int tile_y() { return MODE == MODE_TANGENT ? 4 : T
 template <int MODE>
 __host__ __device__ constexpr int collide_min_blocks() { return MODE == MODE_FP32 || MODE == MODE_FP32_OFFSET ? 4 : 1; }
 
-template <typename T, int MODE>
+// OPEN: the channel's x ends are an inlet and an outlet (phi-like fields
+// mirrored there, populations leaving through them dropped; psi' stays
+// periodic); otherwise x is periodic.
+template <typename T, int MODE, bool OPEN>
 __global__ void __launch_bounds__(TX *tile_y<MODE>(), collide_min_blocks<MODE>())
     collide_kernel(LbmArgs<T, typename Compute<T, MODE>::type> A) {
     using S = typename StoreT<MODE>::type;
@@ -211,13 +214,15 @@ __global__ void __launch_bounds__(TX *tile_y<MODE>(), collide_min_blocks<MODE>()
     for (int i = threadIdx.y * TX + threadIdx.x; i < (TX + 2) * (TYM + 2); i += TX * TYM) {
         int lx = i % (TX + 2), ly = i / (TX + 2);
         int gx = x0 - 1 + lx;
+        const int gm = gx < 0 ? 0 : (gx >= nx ? nx - 1 : gx);  // mirrored column (open ends)
         if (gx < 0) gx += nx;
         while (gx >= nx) gx -= nx;
         int gy = y0 - 1 + ly;
         bool ghost = gy < 0 || gy >= ny;
         int my = gy < 0 ? 0 : (gy >= ny ? ny - 1 : gy);
         long long m = (long long)my * pitch + gx;
-        const R p1 = ld_field<R>(A.phi1, m, ps), p2 = ld_field<R>(A.phi2, m, ps);
+        const long long mp = OPEN ? (long long)my * pitch + gm : m;
+        const R p1 = ld_field<R>(A.phi1, mp, ps), p2 = ld_field<R>(A.phi2, mp, ps);
         s1[ly][lx] = p1;  // mirrored ghost rows: zero normal gradient
         s2[ly][lx] = p2;
         sr[ly][lx] = P.rho[0] * clamp01(p1) + P.rho[1] * clamp01(p2) +
@@ -329,6 +334,7 @@ __global__ void __launch_bounds__(TX *tile_y<MODE>(), collide_min_blocks<MODE>()
         for (int a = 1; a < 9; a++) {
             int yy = y + cy(a);
             if (yy < 0 || yy >= ny) continue;
+            if (OPEN && (x + cx(a) < 0 || x + cx(a) >= nx)) continue;
             const R q1 = s1[ly + cy(a)][lx + cx(a)], q2 = s2[ly + cy(a)][lx + cx(a)];
             touch |= clamp01(B(1) - q1 - q2) >= B(0.5);
         }
@@ -349,6 +355,10 @@ __global__ void __launch_bounds__(TX *tile_y<MODE>(), collide_min_blocks<MODE>()
         return n32 + cy(a) * pitch + (cx(a) > 0 ? dxp : (cx(a) < 0 ? dxm : 0));
     };
     auto walled = [&](int a) { return (cy(a) > 0 && top) || (cy(a) < 0 && bot); };
+    // open channel: populations leaving through the inlet or the outlet
+    auto leaves = [&](int a) {
+        return OPEN && ((cx(a) > 0 && x == nx - 1) || (cx(a) < 0 && x == 0));
+    };
 
     // Deviation of the equilibria from rest, D_a = 3 e.u + 4.5 (e.u)^2 - 1.5 u.u:
     // f^eq = w (p* + D) (Eq. 16), Gamma = w (1 + D) (Eq. 18).
@@ -374,7 +384,7 @@ __global__ void __launch_bounds__(TX *tile_y<MODE>(), collide_min_blocks<MODE>()
         const B rxy = (a == 5 || a == 7) ? B(1) : ((a == 6 || a == 8) ? B(-1) : B(0));
         v += rel * (rxx * dxx + rxy * dxy);
         if (walled(a)) st_pop(fd, opp(a), 9, ps32, n32, v + f_off<MODE, B>(opp(a)));
-        else st_pop(fd, a, 9, ps32, dest(a), v + f_off<MODE, B>(a));
+        else if (!leaves(a)) st_pop(fd, a, 9, ps32, dest(a), v + f_off<MODE, B>(a));
     }
 
     // Phase fields (Eqs. 29-31): g* = (1 - om) g + om phi Gamma + (1 - om/2) F^phi,
@@ -423,13 +433,83 @@ __global__ void __launch_bounds__(TX *tile_y<MODE>(), collide_min_blocks<MODE>()
                 const S sv = S(out);
                 post.add(float(sv));
                 if (walled(a)) gd[(i * 9 + opp(a)) * ps32 + n32] = sv;
-                else gd[(i * 9 + a) * ps32 + dest(a)] = sv;
+                else if (!leaves(a)) gd[(i * 9 + a) * ps32 + dest(a)] = sv;
             } else {
                 if (walled(a)) st_pop(gd, i * 9 + opp(a), 18, ps32, n32, out);
-                else st_pop(gd, i * 9 + a, 18, ps32, dest(a), out);
+                else if (!leaves(a)) st_pop(gd, i * 9 + a, 18, ps32, dest(a), out);
             }
         }
         if constexpr (CONSERVE) gd[(i * 9) * ps32 + n32] = S(pre.minus(post));
+    }
+}
+
+// ---------------------------------------------------------------- open ends
+// Inlet (x = 0), Eq. 37: the Poiseuille parabola with centre-line speed u_max
+// between the half-way walls. Zou-He in the velocity-based form: the unknown
+// populations 1, 5, 8 reflect the non-equilibrium part of their opposites,
+// f_a = f_opp(a) + 6 w_a e_a.u, with -/+ (f2 - f4)/2 on 5 and 8 zeroing the
+// wall-normal momentum; at the two corner nodes the wall supplies one of 5, 8
+// and the two unknowns follow from both momentum components. The inflow is pure
+// carrier: its phase-field populations are zero.
+// Outlet (x = nx - 1): convective condition chi(t+1) = (chi(t) + U chi_{nx-2}(t+1))
+// / (1 + U), U = u_avg, on f_a - w_a p* with the outlet holding the reference
+// p* = 0, and on g as it is.
+template <typename T, int MODE>
+__global__ void open_bc_kernel(Phys<T> P, const void *fsv, const void *gsv, void *fdv, void *gdv,
+                               T u_max, T u_avg) {
+    using S = typename StoreT<MODE>::type;
+    const int y = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nx = P.nx, ny = P.ny;
+    if (y >= ny) return;
+    const long long ps = P.ps, n = (long long)y * P.pitch, o = n + nx - 1, b = o - 1;
+    const S *fs = static_cast<const S *>(fsv);
+    const S *gs = static_cast<const S *>(gsv);
+    S *fd = static_cast<S *>(fdv);
+    S *gd = static_cast<S *>(gdv);
+    auto F = [&](const S *p, int a, long long m) { return T(p[a * ps + m]) - f_off<MODE, T>(a); };
+    auto G = [&](const S *p, int q, int a, long long m) {
+        return T(p[(q * 9 + a) * ps + m]) - g_off<MODE, T>(a);
+    };
+    // inlet
+    const T u = u_max * T(4) * (T(y) + T(0.5)) * (T(ny) - T(0.5) - T(y)) / (T(ny) * T(ny));
+    T fl[9];
+#pragma unroll
+    for (int a = 0; a < 9; a++) fl[a] = F(fd, a, n);
+    if (y == 0) {
+        fl[8] = fl[2] - fl[4] + fl[5] + fl[6] - fl[7];
+    } else if (y == ny - 1) {
+        fl[5] = fl[4] - fl[2] - fl[6] + fl[7] + fl[8];
+    } else {
+        fl[5] = fl[7] + T(6) * wgt<T>(5) * u - T(0.5) * (fl[2] - fl[4]);
+        fl[8] = fl[6] + T(6) * wgt<T>(8) * u + T(0.5) * (fl[2] - fl[4]);
+    }
+    if (y == 0 || y == ny - 1) fl[1] = u + fl[3] - fl[5] + fl[6] + fl[7] - fl[8];
+    else fl[1] = fl[3] + T(6) * wgt<T>(1) * u;
+    fd[1 * ps + n] = S(fl[1] + f_off<MODE, T>(1));
+    fd[5 * ps + n] = S(fl[5] + f_off<MODE, T>(5));
+    fd[8 * ps + n] = S(fl[8] + f_off<MODE, T>(8));
+    for (int q = 0; q < 2; q++) {
+        gd[(q * 9 + 1) * ps + n] = S(g_off<MODE, T>(1));
+        if (y != 0) gd[(q * 9 + 5) * ps + n] = S(g_off<MODE, T>(5));
+        if (y != ny - 1) gd[(q * 9 + 8) * ps + n] = S(g_off<MODE, T>(8));
+    }
+    // outlet
+    T pb = T(0), po = T(0);
+    for (int a = 0; a < 9; a++) {
+        pb += F(fd, a, b);
+        po += F(fs, a, o);
+    }
+    const T pout = T(0);
+    const int in3[3] = {3, 6, 7};
+    for (int k = 0; k < 3; k++) {
+        const int a = in3[k];
+        if ((a == 6 && y == 0) || (a == 7 && y == ny - 1)) continue;  // from the wall
+        const T chi = ((F(fs, a, o) - wgt<T>(a) * po) + u_avg * (F(fd, a, b) - wgt<T>(a) * pb)) /
+                      (T(1) + u_avg);
+        fd[a * ps + o] = S(chi + wgt<T>(a) * pout + f_off<MODE, T>(a));
+        for (int q = 0; q < 2; q++)
+            gd[(q * 9 + a) * ps + o] =
+                S((G(gs, q, a, o) + u_avg * G(gd, q, a, b)) / (T(1) + u_avg) + g_off<MODE, T>(a));
     }
 }
 
@@ -562,12 +642,21 @@ void launch_phase(int mode, const Phys<T> &P, const void *g, T *phi1, T *phi2, T
 template <typename T>
 void launch_collide(int mode, const LbmArgs<T> &a, cudaStream_t s) {
     dim3 b(TX, TY), gr = grid2(a.P.nx, a.P.ny, b);
-    FCD_MODE_SWITCH(mode, T, (collide_kernel<T, M><<<gr, b, 0, s>>>(a)));
+    if (a.open_x) FCD_MODE_SWITCH(mode, T, (collide_kernel<T, M, true><<<gr, b, 0, s>>>(a)));
+    else FCD_MODE_SWITCH(mode, T, (collide_kernel<T, M, false><<<gr, b, 0, s>>>(a)));
 }
 
 void launch_collide_tangent(const LbmArgs<double, DualT> &a, cudaStream_t s) {
     dim3 b(TX, tile_y<MODE_TANGENT>()), gr = grid2(a.P.nx, a.P.ny, b);
-    collide_kernel<double, MODE_TANGENT><<<gr, b, 0, s>>>(a);
+    collide_kernel<double, MODE_TANGENT, false><<<gr, b, 0, s>>>(a);
+}
+
+template <typename T>
+void launch_open_bc(int mode, const Phys<T> &P, const void *f_src, const void *g_src,
+                    void *f_dst, void *g_dst, double u_max, double u_avg, cudaStream_t s) {
+    const int b = 64, gr = (P.ny + b - 1) / b;
+    FCD_MODE_SWITCH(mode, T, (open_bc_kernel<T, M><<<gr, b, 0, s>>>(P, f_src, g_src, f_dst, g_dst,
+                                                                   T(u_max), T(u_avg))));
 }
 
 template <typename T>
@@ -615,6 +704,8 @@ void launch_phi3_to_f64(const T *p1, const T *p2, int nx, int ny, int pitch, dou
     template void launch_phase<T>(int, const Phys<T> &, const void *, T *, T *, T *,          \
                                   PhaseCtl, cudaStream_t);                                    \
     template void launch_collide<T>(int, const LbmArgs<T> &, cudaStream_t);                    \
+    template void launch_open_bc<T>(int, const Phys<T> &, const void *, const void *, void *,    \
+                                    void *, double, double, cudaStream_t);                      \
     template void launch_init<T>(int, const Phys<T> &, double, double, double, double, double, \
                                  double, void *, void *, T *, cudaStream_t);                   \
     template void launch_export<T>(int, const Phys<T> &, const void *, const void *, double *, \

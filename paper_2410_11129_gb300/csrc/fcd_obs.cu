@@ -38,7 +38,8 @@ __device__ __forceinline__ double c01(double v) { return v < 0.0 ? 0.0 : (v > 1.
 
 // Core at a node with phi_1 >= 1/2 next to a carrier node (phi_3 >= 1/2)
 // inside the channel; smallest y*nx + x wins.
-__global__ void obs_touch(int nx, int ny, const double *phi1, const double *phi2, ObsOut *out) {
+__global__ void obs_touch(int nx, int ny, const double *phi1, const double *phi2, ObsOut *out,
+                          int open) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= nx || y >= ny) return;
     if (c01(phi1[(long long)y * nx + x]) < 0.5) return;
@@ -46,6 +47,7 @@ __global__ void obs_touch(int nx, int ny, const double *phi1, const double *phi2
         const int yy = y + cy(a);
         if (yy < 0 || yy >= ny) continue;
         int xx = x + cx(a);
+        if (open && (xx < 0 || xx >= nx)) continue;  // outside an open channel
         xx = xx < 0 ? nx - 1 : (xx >= nx ? 0 : xx);
         const long long m = (long long)yy * nx + xx;
         if (c01(1.0 - phi1[m] - phi2[m]) >= 0.5) {
@@ -130,7 +132,8 @@ __device__ double block_max(double v, double *sh) {
     return r;
 }
 
-__global__ void __launch_bounds__(FIN) obs_final(int nx, const double *col, ObsOut *out) {
+// open: the frame starts at the inlet (no periodic seam to cut)
+__global__ void __launch_bounds__(FIN) obs_final(int nx, const double *col, ObsOut *out, int open) {
     __shared__ double sh[FIN];
     __shared__ int ish[FIN];
     const int t = threadIdx.x;
@@ -161,7 +164,7 @@ __global__ void __launch_bounds__(FIN) obs_final(int nx, const double *col, ObsO
             __syncthreads();
         }
     }
-    const int xcut = ish[0];
+    const int xcut = open ? 0 : ish[0];
     __syncthreads();
     if (t == 0) out->xcut = xcut;
     for (int w = 0; w < 2; w++) {  // 0: shell indicator, 1: core indicator
@@ -225,7 +228,7 @@ __global__ void __launch_bounds__(FIN) obs_final(int nx, const double *col, ObsO
 
 template <typename T>
 void launch_observe(int mode, const Phys<T> &P, const void *g, double *scratch, ObsOut *out,
-                    cudaStream_t s) {
+                    cudaStream_t s, int open_x) {
     const long long N = (long long)P.nx * P.ny;
     double *phi1 = scratch, *phi2 = scratch + N, *col = scratch + 2 * N;
     cudaMemsetAsync(out, 0, sizeof(ObsOut), s);
@@ -237,16 +240,16 @@ void launch_observe(int mode, const Phys<T> &P, const void *g, double *scratch, 
         if (mode == MODE_FP32) obs_phi<T, MODE_FP32><<<gr, b, 0, s>>>(P, g, phi1, phi2, out);
         else obs_phi<T, MODE_FP32_OFFSET><<<gr, b, 0, s>>>(P, g, phi1, phi2, out);
     }
-    obs_touch<<<gr, b, 0, s>>>(P.nx, P.ny, phi1, phi2, out);
+    obs_touch<<<gr, b, 0, s>>>(P.nx, P.ny, phi1, phi2, out, open_x);
     obs_columns<<<(P.nx + 127) / 128, 128, 0, s>>>(P.nx, P.ny, phi1, phi2, col);
-    obs_final<<<1, FIN, 0, s>>>(P.nx, col, out);
+    obs_final<<<1, FIN, 0, s>>>(P.nx, col, out, open_x);
 }
 
 size_t observe_scratch_doubles(int nx, int ny) { return 2ull * nx * ny + (size_t)COLS * nx; }
 
 template void launch_observe<float>(int, const Phys<float> &, const void *, double *, ObsOut *,
-                                    cudaStream_t);
+                                    cudaStream_t, int);
 template void launch_observe<double>(int, const Phys<double> &, const void *, double *,
-                                     ObsOut *, cudaStream_t);
+                                     ObsOut *, cudaStream_t, int);
 
 }  // namespace fcd

@@ -32,6 +32,7 @@ class fcd_params(C.Structure):
         ("s13_over_s12", C.c_double), ("s23_over_s12", C.c_double), ("sigma23", C.c_double),
         ("u_max", C.c_double), ("ferro_phase", C.c_int), ("precision", C.c_int),
         ("mag_tol", C.c_double), ("mag_max_iter", C.c_int), ("eps_n", C.c_double),
+        ("open_x", C.c_int),
     ]
 
 
@@ -159,6 +160,7 @@ def make_params(cfg):
     p.mag_tol = cfg.get("mag_tol", 1e-10)
     p.mag_max_iter = int(cfg.get("mag_max_iter", 200))
     p.eps_n = cfg.get("eps_n", 1e-12 if p.precision == FCD_FP64 else 1e-6)
+    p.open_x = int(cfg.get("open_x", 0))
     return p
 
 

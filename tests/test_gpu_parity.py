@@ -105,9 +105,38 @@ def test_solver_matches_oracle_and_layered_exact(orc, fcd):
     ch.close()
 
 
+@pytest.mark.parametrize("kw", [
+    dict(),                                                             # shell ferro
+    dict(ferro="core", chi_ferro=2.0, alpha=0.7, rho_r=2.0, nu_r=2.0, Bo_m=3.0, xc=10.0),
+])
+def test_fp64_parity_open_channel(orc, fcd, kw):
+    """Open channel: Eq. 37 inlet and convective outlet, droplet and field."""
+    compare_fp64(orc, parity_cfg(open_x=1, **kw), 120)
+
+
+def test_open_channel_poiseuille_gpu(fcd):
+    """The open channel's developed flow on the GPU: the inlet parabola and the
+    closed-form pressure gradient, as pinned on the oracle."""
+    from paper_2410_11129_gb300 import fcd as F
+    nx, ny = 48, 12
+    cfg = W.channel(nx, ny, -1000.0, -1000.0, xc=0.0, yc=0.0, xi=4.0, Bo_m=0.0, ferro="none",
+                    u_max=0.01, open_x=1)
+    cfg["nu"] = [1 / 8] * 3
+    ch = F.Channel(dict(cfg, precision="fp64"))
+    ch.step(12000)
+    u, p = ch.field("ux"), ch.field("pstar")
+    ch.close()
+    y = np.arange(ny)
+    exact = 0.01 * 4 * (y + 0.5) * (ny - 0.5 - y) / ny**2
+    assert max(np.abs(u[:, x] - exact).max() for x in range(10, nx - 10)) <= 1e-6 * exact.max()
+    slope = np.polyfit(np.arange(nx // 4, 3 * nx // 4), p[ny // 2, nx // 4:3 * nx // 4], 1)[0]
+    assert abs(slope / (-8 * (1 / 8) * 0.01 / ny**2 / (1 / 3)) - 1) <= 1e-6
+
+
 @pytest.mark.parametrize("prec", ["fp32", "fp32_offset"])
-def test_fp32_forms_against_fp64_oracle(orc, fcd, prec):
-    cfg = parity_cfg(mag_tol=1e-5)
+@pytest.mark.parametrize("open_x", [0, 1])
+def test_fp32_forms_against_fp64_oracle(orc, fcd, prec, open_x):
+    cfg = parity_cfg(mag_tol=1e-5, open_x=open_x)
     sim = orc.Sim(dict(cfg, mag_tol=1e-13))
     from paper_2410_11129_gb300 import fcd as F
     ch = F.Channel(dict(cfg, precision=prec))
