@@ -49,7 +49,7 @@ NCU_TRAFFIC = {
 def _workloads():
     from paper_2410_11129_gb300 import workloads as W
     return {"1600x200": W.C2, "200x40": W.C1, "2400x300": W.C3, "800x100": W.C5,
-            "9600x1200": W.ROOF}
+            "9600x1200": W.ROOF, "900x150-open": W.PAPER}
 
 
 WORKLOADS = _workloads()

@@ -2,7 +2,8 @@
 
   python -m paper_2410_11129_gb300.run --workload 1600x200 --steps 100 [--precision fp32]
 
-Workloads: 200x40, 1600x200, 2400x300, 800x100, 9600x1200 (see workloads.py).
+Workloads: 200x40, 1600x200, 2400x300, 800x100, 9600x1200, 900x150-open
+(see workloads.py).
 With FCD_NO_GRAPH=1 in the environment the potential-solve loop is driven from
 the host instead of a CUDA-graph while node (same kernels; profilers that do
 not follow conditional graph nodes can then see every launch).
@@ -16,7 +17,7 @@ from . import fcd
 from . import workloads as W
 
 NAMED = {"200x40": W.C1, "1600x200": W.C2, "2400x300": W.C3, "800x100": W.C5,
-         "9600x1200": W.ROOF}
+         "9600x1200": W.ROOF, "900x150-open": W.PAPER}
 
 
 def main(argv=None):

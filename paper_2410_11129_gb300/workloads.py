@@ -67,6 +67,14 @@ C3 = dict(channel(2400, 300, 45, 90, Ca=0.2, Bo_m=3.0, alpha_deg=90.0, ferro="co
 C5 = dict(channel(800, 100, 15, 30, Ca=0.15, Bo_m=2.0, alpha_deg=0.0, ferro="shell", eps_n=1e-6),
           name="channel-800x100", steps=20000, precision="fp64")
 
+# The paper's own channel (Sec. 2.6: H x L = 150 x 900, L = 6H) as an open channel
+# (Eq. 37 inlet, convective outlet), with the parameters of its grid study (Fig. 4):
+# shell ferrofluid, Ca 0.15, alpha 0, r2/r1 = 1.75, Bo_m 2. r2 = 0.3 H is an
+# assumption (no radius is given); centre 4 r1 from the inlet (Sec. 2.5).
+PAPER = dict(channel(900, 150, 45.0 / 1.75, 45.0, xc=4 * 45.0 / 1.75, Ca=0.15, Bo_m=2.0,
+                     alpha_deg=0.0, ferro="shell", mag_tol=1e-4, open_x=1),
+             name="open-channel-900x150-fp32", steps=20000, precision="fp32")
+
 # L2-busting roofline channel: the 1600x200 physics on 9600x1200 (droplet x6).
 # The FP32 residual floor grows with the droplet (|psi'| ~ H0 r1): 1e-3 here.
 ROOF = dict(channel(9600, 1200, 180, 360, Ca=0.2, Bo_m=3.0, alpha_deg=90.0, ferro="core",
