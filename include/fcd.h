@@ -80,7 +80,7 @@ typedef struct {
                             * parabola (centre-line speed u_max) enters at x = 0 as
                             * pure carrier, a convective outlet at x = nx - 1 holds
                             * the reference p* = 0; no body force. The potential
-                            * psi' stays periodic in x. Not for tangent contexts. */
+                            * psi' stays periodic in x. */
 } fcd_params;
 
 /* Observables (Sec. 2.5, Eqs. 38 and 42). */

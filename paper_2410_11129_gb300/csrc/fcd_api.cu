@@ -974,7 +974,7 @@ struct TangentEngine : Engine<double> {
     // kernels of one step outside the multigrid cycles (those are counted on
     // the device): two phase kernels, per direction the right-hand side, two
     // copies and the reset, the potential copy and the collision
-    long step_kernels() const { return 2 + (magnetic() ? 4 * NT : 0) + 2; }
+    long step_kernels() const { return 2 + (magnetic() ? 4 * NT : 0) + 2 + (prm.open_x ? 1 : 0); }
 
     long launches() const override {
         long n = Engine<double>::launches();
@@ -1030,7 +1030,10 @@ struct TangentEngine : Engine<double> {
         a.macro = store_macro ? macro : nullptr;
         a.brk = brk;
         a.step = d_step;
+        a.open_x = prm.open_x;
         launch_collide_tangent(a, s);
+        if (prm.open_x)
+            launch_open_bc_tangent(P, f[c], g[c], f[c ^ 1], g[c ^ 1], prm.u_max, D.u_avg, s);
         CK(cudaGetLastError());
         return FCD_OK;
     }
@@ -1164,7 +1167,6 @@ fcd_status fcd_create_tangent(const fcd_params *params, fcd_ctx **out) {
         why = "lattice too large for the tangent copies (90 planes within 2^31 elements)";
     if (!why && p.ferro_phase != 0 && !(p.Bo_m > 0))
         why = "the Bo_m direction needs Bo_m > 0 (H0 ~ sqrt(Bo_m))";
-    if (!why && p.open_x) why = "the open channel is not available for tangent contexts";
     if (why) {
         snprintf(g_last, sizeof g_last, "fcd_create_tangent: %s", why);
         return FCD_EINVAL;

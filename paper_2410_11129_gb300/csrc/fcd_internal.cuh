@@ -183,6 +183,8 @@ void launch_phase(int mode, const Phys<T> &P, const void *g, T *phi1, T *phi2, T
 template <typename T>
 void launch_collide(int mode, const LbmArgs<T> &a, cudaStream_t s);
 void launch_collide_tangent(const LbmArgs<double, DualT> &a, cudaStream_t s);
+void launch_open_bc_tangent(const Phys<double> &P, const void *f_src, const void *g_src,
+                            void *f_dst, void *g_dst, double u_max, double u_avg, cudaStream_t s);
 // Open channel: the populations entering through the inlet (x = 0) and the
 // outlet (x = nx - 1) after a collide-stream from (f_src, g_src) into
 // (f_dst, g_dst); one thread per row.

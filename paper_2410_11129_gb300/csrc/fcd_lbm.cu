@@ -458,21 +458,23 @@ template <typename T, int MODE>
 __global__ void open_bc_kernel(Phys<T> P, const void *fsv, const void *gsv, void *fdv, void *gdv,
                                T u_max, T u_avg) {
     using S = typename StoreT<MODE>::type;
+    using R = typename Compute<T, MODE>::type;  // dual numbers in the tangent step
+    using B = T;
     const int y = blockIdx.x * blockDim.x + threadIdx.x;
     const int nx = P.nx, ny = P.ny;
     if (y >= ny) return;
-    const long long ps = P.ps, n = (long long)y * P.pitch, o = n + nx - 1, b = o - 1;
+    const int ps = (int)P.ps, n = y * P.pitch, o = n + nx - 1, b = o - 1;
     const S *fs = static_cast<const S *>(fsv);
     const S *gs = static_cast<const S *>(gsv);
     S *fd = static_cast<S *>(fdv);
     S *gd = static_cast<S *>(gdv);
-    auto F = [&](const S *p, int a, long long m) { return T(p[a * ps + m]) - f_off<MODE, T>(a); };
-    auto G = [&](const S *p, int q, int a, long long m) {
-        return T(p[(q * 9 + a) * ps + m]) - g_off<MODE, T>(a);
+    auto F = [&](const S *p, int a, int m) { return ld_pop<R>(p, a, 9, ps, m) - f_off<MODE, B>(a); };
+    auto G = [&](const S *p, int q, int a, int m) {
+        return ld_pop<R>(p, q * 9 + a, 18, ps, m) - g_off<MODE, B>(a);
     };
-    // inlet
-    const T u = u_max * T(4) * (T(y) + T(0.5)) * (T(ny) - T(0.5) - T(y)) / (T(ny) * T(ny));
-    T fl[9];
+    // inlet (the profile is data: no derivative)
+    const B u = u_max * B(4) * (B(y) + B(0.5)) * (B(ny) - B(0.5) - B(y)) / (B(ny) * B(ny));
+    R fl[9];
 #pragma unroll
     for (int a = 0; a < 9; a++) fl[a] = F(fd, a, n);
     if (y == 0) {
@@ -480,36 +482,36 @@ __global__ void open_bc_kernel(Phys<T> P, const void *fsv, const void *gsv, void
     } else if (y == ny - 1) {
         fl[5] = fl[4] - fl[2] - fl[6] + fl[7] + fl[8];
     } else {
-        fl[5] = fl[7] + T(6) * wgt<T>(5) * u - T(0.5) * (fl[2] - fl[4]);
-        fl[8] = fl[6] + T(6) * wgt<T>(8) * u + T(0.5) * (fl[2] - fl[4]);
+        fl[5] = fl[7] + B(6) * wgt<B>(5) * u - B(0.5) * (fl[2] - fl[4]);
+        fl[8] = fl[6] + B(6) * wgt<B>(8) * u + B(0.5) * (fl[2] - fl[4]);
     }
     if (y == 0 || y == ny - 1) fl[1] = u + fl[3] - fl[5] + fl[6] + fl[7] - fl[8];
-    else fl[1] = fl[3] + T(6) * wgt<T>(1) * u;
-    fd[1 * ps + n] = S(fl[1] + f_off<MODE, T>(1));
-    fd[5 * ps + n] = S(fl[5] + f_off<MODE, T>(5));
-    fd[8 * ps + n] = S(fl[8] + f_off<MODE, T>(8));
+    else fl[1] = fl[3] + B(6) * wgt<B>(1) * u;
+    st_pop(fd, 1, 9, ps, n, fl[1] + f_off<MODE, B>(1));
+    st_pop(fd, 5, 9, ps, n, fl[5] + f_off<MODE, B>(5));
+    st_pop(fd, 8, 9, ps, n, fl[8] + f_off<MODE, B>(8));
     for (int q = 0; q < 2; q++) {
-        gd[(q * 9 + 1) * ps + n] = S(g_off<MODE, T>(1));
-        if (y != 0) gd[(q * 9 + 5) * ps + n] = S(g_off<MODE, T>(5));
-        if (y != ny - 1) gd[(q * 9 + 8) * ps + n] = S(g_off<MODE, T>(8));
+        st_pop(gd, q * 9 + 1, 18, ps, n, R(g_off<MODE, B>(1)));
+        if (y != 0) st_pop(gd, q * 9 + 5, 18, ps, n, R(g_off<MODE, B>(5)));
+        if (y != ny - 1) st_pop(gd, q * 9 + 8, 18, ps, n, R(g_off<MODE, B>(8)));
     }
     // outlet
-    T pb = T(0), po = T(0);
+    R pb = R(B(0)), po = R(B(0));
     for (int a = 0; a < 9; a++) {
         pb += F(fd, a, b);
         po += F(fs, a, o);
     }
-    const T pout = T(0);
+    const B pout = B(0);
     const int in3[3] = {3, 6, 7};
     for (int k = 0; k < 3; k++) {
         const int a = in3[k];
         if ((a == 6 && y == 0) || (a == 7 && y == ny - 1)) continue;  // from the wall
-        const T chi = ((F(fs, a, o) - wgt<T>(a) * po) + u_avg * (F(fd, a, b) - wgt<T>(a) * pb)) /
-                      (T(1) + u_avg);
-        fd[a * ps + o] = S(chi + wgt<T>(a) * pout + f_off<MODE, T>(a));
+        const R chi = ((F(fs, a, o) - wgt<B>(a) * po) + u_avg * (F(fd, a, b) - wgt<B>(a) * pb)) /
+                      (B(1) + u_avg);
+        st_pop(fd, a, 9, ps, o, chi + wgt<B>(a) * pout + f_off<MODE, B>(a));
         for (int q = 0; q < 2; q++)
-            gd[(q * 9 + a) * ps + o] =
-                S((G(gs, q, a, o) + u_avg * G(gd, q, a, b)) / (T(1) + u_avg) + g_off<MODE, T>(a));
+            st_pop(gd, q * 9 + a, 18, ps, o,
+                   (G(gs, q, a, o) + u_avg * G(gd, q, a, b)) / (B(1) + u_avg) + g_off<MODE, B>(a));
     }
 }
 
@@ -648,7 +650,14 @@ void launch_collide(int mode, const LbmArgs<T> &a, cudaStream_t s) {
 
 void launch_collide_tangent(const LbmArgs<double, DualT> &a, cudaStream_t s) {
     dim3 b(TX, tile_y<MODE_TANGENT>()), gr = grid2(a.P.nx, a.P.ny, b);
-    collide_kernel<double, MODE_TANGENT, false><<<gr, b, 0, s>>>(a);
+    if (a.open_x) collide_kernel<double, MODE_TANGENT, true><<<gr, b, 0, s>>>(a);
+    else collide_kernel<double, MODE_TANGENT, false><<<gr, b, 0, s>>>(a);
+}
+
+void launch_open_bc_tangent(const Phys<double> &P, const void *f_src, const void *g_src,
+                            void *f_dst, void *g_dst, double u_max, double u_avg, cudaStream_t s) {
+    const int b = 64, gr = (P.ny + b - 1) / b;
+    open_bc_kernel<double, MODE_TANGENT><<<gr, b, 0, s>>>(P, f_src, g_src, f_dst, g_dst, u_max, u_avg);
 }
 
 template <typename T>

@@ -66,8 +66,9 @@ def tangent_run(F, cfg, steps):
     return o, plain_obs, fields
 
 
-def test_tangent_primal_matches_plain(fcd):
-    cfg = grad_cfg()
+@pytest.mark.parametrize("open_x", [0, 1])
+def test_tangent_primal_matches_plain(fcd, open_x):
+    cfg = grad_cfg(open_x=open_x)
     o, ob, fields = tangent_run(fcd, cfg, STEPS)
     ch = fcd.Channel(cfg)
     ch.step(STEPS)
@@ -84,9 +85,11 @@ def test_tangent_primal_matches_plain(fcd):
     assert abs(o["overlap"] - overlap_of(phi1, phi2)) <= 1e-10 * max(1.0, o["overlap"])
 
 
-def test_tangent_against_oracle_differences(fcd, orc):
-    """Forward-mode derivatives vs Richardson central differences of the oracle."""
-    cfg = grad_cfg()
+@pytest.mark.parametrize("open_x", [0, 1])
+def test_tangent_against_oracle_differences(fcd, orc, open_x):
+    """Forward-mode derivatives vs Richardson central differences of the oracle,
+    in the periodic and in the open channel."""
+    cfg = grad_cfg(open_x=open_x)
     theta = list(fcd.parameters_of(cfg))
     o, _, _ = tangent_run(fcd, cfg, STEPS)
 
