@@ -8,6 +8,7 @@
 // launches n such graphs; nothing synchronises with the host in between.
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -188,7 +189,9 @@ struct SnapHeader {
     int nx, ny, precision, pitch;
     long long step;
     unsigned long long brk;
+    int cur, pad;  // which level-0 potential buffer is current
 };
+static const unsigned SNAP_VERSION = 3;
 static const unsigned SNAP_MAGIC = 0x46434453u;  // "FCDS"
 
 template <typename T>
@@ -214,6 +217,7 @@ struct Engine : fcd_ctx {
     ObsOut *obs_out = nullptr;
     MgCtl *h_ctl = nullptr;
     ObsOut *h_obs = nullptr;
+    SnapHeader *h_snap = nullptr;  // pinned staging of snapshot headers
     unsigned long long *h_brk = nullptr;
     cudaStream_t cap = nullptr;
     cudaGraph_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
@@ -243,6 +247,7 @@ struct Engine : fcd_ctx {
         for (void *p : mem) release(p, user);
         if (h_ctl) cudaFreeHost(h_ctl);
         if (h_obs) cudaFreeHost(h_obs);
+        if (h_snap) cudaFreeHost(h_snap);
         if (h_brk) cudaFreeHost(h_brk);
         if (cap) cudaStreamDestroy(cap);
         for (auto e : ev)
@@ -280,6 +285,7 @@ struct Engine : fcd_ctx {
             if (!p) return fail(FCD_ENOMEM, "device allocation failed");
         CK(cudaMallocHost(&h_ctl, sizeof(MgCtl)));
         CK(cudaMallocHost(&h_obs, sizeof(ObsOut)));
+        CK(cudaMallocHost(&h_snap, sizeof(SnapHeader)));
         CK(cudaMallocHost(&h_brk, sizeof(unsigned long long)));
         CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
         for (auto &e : ev) CK(cudaEventCreate(&e));
@@ -689,49 +695,63 @@ struct Engine : fcd_ctx {
         return pi ? keep_history() : FCD_OK;
     }
 
+    // Snapshot: header, the 27 stored population planes of the current buffer,
+    // both level-0 potential buffers and the previous potential. Both potential
+    // buffers travel, with the device's current-buffer index, so neither call
+    // needs to read the control block on the host: each is one stream of
+    // asynchronous copies and a single synchronisation.
     size_t state_bytes() const override {
-        return sizeof(SnapHeader) + 27 * (size_t)ps * sizeof(S) + 2 * (size_t)ps * sizeof(T);
+        return sizeof(SnapHeader) + 27 * (size_t)ps * sizeof(S) + 3 * (size_t)ps * sizeof(T);
     }
 
     fcd_status get_state(void *dst, size_t bytes) override {
         if (!dst || bytes < state_bytes()) return fail(FCD_EINVAL, "snapshot buffer too small");
-        if (sync_ctl() != FCD_OK) return FCD_ECUDA;
         cudaStream_t s = stream;
-        SnapHeader h;
+        CK(cudaStreamSynchronize(s));  // the staging header may still be in flight
+        SnapHeader &h = *h_snap;
         std::memset(&h, 0, sizeof h);
         h.magic = SNAP_MAGIC;
-        h.version = 2;
+        h.version = SNAP_VERSION;
         h.nx = prm.nx;
         h.ny = prm.ny;
         h.precision = prm.precision;
         h.pitch = pitch;
         h.step = step;
-        CK(cudaMemcpyAsync(h_brk, brk, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        h.brk = *h_brk;
         char *d = static_cast<char *>(dst);
         CK(cudaMemcpyAsync(d, &h, sizeof h, cudaMemcpyDefault, s));
-        CK(cudaStreamSynchronize(s));
+        CK(cudaMemcpyAsync(d + offsetof(SnapHeader, brk), brk, sizeof(unsigned long long),
+                           cudaMemcpyDefault, s));
+        CK(cudaMemcpyAsync(d + offsetof(SnapHeader, cur), &ctl->cur, sizeof(int), cudaMemcpyDefault, s));
         size_t off = sizeof h;
         CK(cudaMemcpyAsync(d + off, f[cur], 9 * ps * sizeof(S), cudaMemcpyDefault, s));
         off += 9 * ps * sizeof(S);
         CK(cudaMemcpyAsync(d + off, g[cur], 18 * ps * sizeof(S), cudaMemcpyDefault, s));
         off += 18 * ps * sizeof(S);
-        CK(cudaMemcpyAsync(d + off, h_ctl->cur ? psiB : psiA, ps * sizeof(T), cudaMemcpyDefault, s));
-        off += ps * sizeof(T);
-        CK(cudaMemcpyAsync(d + off, psiP, ps * sizeof(T), cudaMemcpyDefault, s));
+        for (T *q : {psiA, psiB, psiP}) {
+            CK(cudaMemcpyAsync(d + off, q, ps * sizeof(T), cudaMemcpyDefault, s));
+            off += ps * sizeof(T);
+        }
         CK(cudaStreamSynchronize(s));
         return FCD_OK;
     }
 
     fcd_status set_state(const void *src, size_t bytes) override {
         if (!src || bytes < state_bytes()) return fail(FCD_ESTATE, "snapshot too small");
-        SnapHeader h;
         cudaStream_t s = stream;
-        CK(cudaMemcpyAsync(&h, src, sizeof h, cudaMemcpyDefault, s));
         CK(cudaStreamSynchronize(s));
-        if (h.magic != SNAP_MAGIC || h.version != 2 || h.nx != prm.nx || h.ny != prm.ny ||
-            h.precision != prm.precision || h.pitch != pitch)
+        SnapHeader &h = *h_snap;
+        cudaPointerAttributes at;
+        const bool host = cudaPointerGetAttributes(&at, src) == cudaSuccess &&
+                          at.type != cudaMemoryTypeDevice;
+        cudaGetLastError();  // clear the error of an unregistered pointer query
+        if (host) {
+            std::memcpy(&h, src, sizeof h);
+        } else {
+            CK(cudaMemcpyAsync(&h, src, sizeof h, cudaMemcpyDefault, s));
+            CK(cudaStreamSynchronize(s));
+        }
+        if (h.magic != SNAP_MAGIC || h.version != SNAP_VERSION || h.nx != prm.nx || h.ny != prm.ny ||
+            h.precision != prm.precision || h.pitch != pitch || (h.cur != 0 && h.cur != 1))
             return fail(FCD_ESTATE, "snapshot does not match this context");
         const char *p = static_cast<const char *>(src);
         size_t off = sizeof h;
@@ -739,14 +759,13 @@ struct Engine : fcd_ctx {
         off += 9 * ps * sizeof(S);
         CK(cudaMemcpyAsync(g[cur], p + off, 18 * ps * sizeof(S), cudaMemcpyDefault, s));
         off += 18 * ps * sizeof(S);
-        if (sync_ctl() != FCD_OK) return FCD_ECUDA;
-        CK(cudaMemcpyAsync(h_ctl->cur ? psiB : psiA, p + off, ps * sizeof(T), cudaMemcpyDefault, s));
-        off += ps * sizeof(T);
-        CK(cudaMemcpyAsync(psiP, p + off, ps * sizeof(T), cudaMemcpyDefault, s));
-        *h_brk = h.brk;
-        CK(cudaMemcpyAsync(brk, h_brk, sizeof(unsigned long long), cudaMemcpyHostToDevice, s));
-        long long st64 = h.step;
-        CK(cudaMemcpyAsync(d_step, &st64, sizeof st64, cudaMemcpyHostToDevice, s));
+        for (T *q : {psiA, psiB, psiP}) {
+            CK(cudaMemcpyAsync(q, p + off, ps * sizeof(T), cudaMemcpyDefault, s));
+            off += ps * sizeof(T);
+        }
+        CK(cudaMemcpyAsync(&ctl->cur, &h.cur, sizeof(int), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(brk, &h.brk, sizeof(unsigned long long), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(d_step, &h.step, sizeof(long long), cudaMemcpyHostToDevice, s));
         CK(cudaStreamSynchronize(s));
         step = (long)h.step;
         return FCD_OK;
