@@ -1,6 +1,7 @@
 """Pins of the oracle's observables (Eq. 42, Eq. 38, breakup metrics of Sec. 2.5)
 on constructed phase fields with known geometry (no GPU)."""
 import numpy as np
+import pytest
 
 from paper_2410_11129_gb300 import workloads as W
 
@@ -99,3 +100,46 @@ def test_breakup_is_sticky_through_steps(orc):
     s.step(3)
     o = s.observe()
     assert o["breakup"] == 1 and o["b_step"] == 0 and o["step"] == 3
+
+
+def _run_history(orc, cfg, chunk, n):
+    orc.set_threads(orc.max_threads())
+    try:
+        s = orc.Sim(cfg)
+        out = []
+        for _ in range(n):
+            s.step(chunk)
+            out.append(s.observe())
+    finally:
+        orc.set_threads(1)
+    return out
+
+
+@pytest.mark.parametrize("alpha_deg,sign", [(0.0, -1), (90.0, 1)])
+def test_ferrofluid_drop_elongates_along_the_field(orc, alpha_deg, sign):
+    """A ferrofluid drop at rest in a uniform field stretches along the field
+    (the Kelvin force of Eq. 7 pulls hardest where the field crosses the
+    interface): T = (l_y - l_x)/(l_y + l_x) < 0 for alpha = 0, > 0 for 90 deg."""
+    n = 64
+    cfg = W.channel(n, n, 12.0, 12.0, xc=n / 2 - 0.5, yc=n / 2 - 0.5, xi=4.0, Bo_m=3.0,
+                    alpha_deg=alpha_deg, ferro="core", chi_ferro=2.0, u_max=0.0, sigma23=0.005,
+                    Ca=0.0, mag_tol=1e-7)
+    T = _run_history(orc, cfg, 1500, 1)[-1]["T_i"]
+    assert sign * T > 0.05, T
+
+
+def test_deformation_trends_of_the_paper(orc):
+    """Sec. 3.1-3.2, on 200x40 channels before the shell breaks:
+    - no field: the drag stretches the shell along the flow, T_o < 0;
+    - shell ferrofluid, alpha = 0: field and drag both act along x, T_o falls
+      further as Bo_m grows;
+    - core ferrofluid, alpha = 0: the field stretches the core along x, T_i
+      falls as Bo_m grows."""
+    def cfg(ferro, bo):
+        return W.channel(200, 40, 6, 12, xc=50, xi=4.0, Ca=0.1, Bo_m=bo, alpha_deg=0.0,
+                         ferro=ferro, chi_ferro=1.0, mag_tol=1e-7)
+    shell0, shell2 = (_run_history(orc, cfg("shell", b), 750, 2) for b in (0.0, 2.0))
+    core0, core3 = (_run_history(orc, cfg("core", b), 750, 2) for b in (0.0, 3.0))
+    assert shell0[-1]["T_o"] < 0
+    assert all(b["T_o"] < a["T_o"] for a, b in zip(shell0, shell2))
+    assert all(b["T_i"] < a["T_i"] for a, b in zip(core0, core3))
