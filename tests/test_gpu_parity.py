@@ -67,6 +67,8 @@ def compare_fp64(orc, cfg, steps, tol=1e-10):
     dict(),                                                           # shell ferro, alpha 0
     dict(ferro="core", chi_ferro=2.0, alpha=np.pi / 2, rho_r=2.0, nu_r=2.0, Ca=0.2, Bo_m=3.0),
     dict(nx=38, ny=13, xc=11.0, yc=6.3, alpha=0.6),                   # ragged tiles, odd ny, off-centre
+    dict(nx=8, ny=6, r1=1.0, r2=2.0, xc=3.0, yc=2.5),                 # brute-force tiny grids
+    dict(nx=12, ny=10, r1=2.0, r2=3.5, xc=5.0, yc=4.5, alpha=0.4),
 ])
 def test_fp64_parity_small(orc, fcd, kw):
     compare_fp64(orc, parity_cfg(**kw), 120)
