@@ -298,6 +298,9 @@ def run_ours(args):
     from paper_2410_11129_gb300 import workloads as W
 
     cfg = dict(WORKLOADS[args.workload])
+    if args.precision:
+        cfg["precision"] = args.precision
+        cfg["name"] = cfg["name"].rsplit("-fp", 1)[0] + "-" + args.precision
     N = cfg["nx"] * cfg["ny"]
     ch = fcd.Channel(cfg)
     ch.set_profiling(True)
@@ -439,6 +442,8 @@ def main():
                     help="steps of the batched-vs-looped regime sweep (0 skips it)")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS),
                     help="the default is the benchmark workload; the others are extra data points")
+    ap.add_argument("--precision", default=None, choices=["fp64", "fp32", "fp32_offset"],
+                    help="storage form (default: the workload's)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
