@@ -238,6 +238,42 @@ fcd_status fcd_create_tangent(const fcd_params *params, fcd_ctx **out);
  * (l_x: the two centre-line crossings; l_y: the column of largest extent). */
 fcd_status fcd_tangent_observables(fcd_ctx *ctx, fcd_tangent_obs *out);
 
+/* ---- Discrete adjoint (reverse mode): gradients of one scalar functional of
+ * the final state, J = w_T T_o + w_overlap sum_nodes phi_1 phi_3 (T_o of
+ * Eq. 42; the overlap as in fcd_tangent_obs), with respect to the four
+ * parameters of the tangent form (same direction order) and to the initial
+ * populations. An adjoint context is an FP64 periodic channel (open_x = 0;
+ * precision is ignored) that keeps a checkpoint of its state every
+ * checkpoint_interval steps from step 0 (device memory: 30 planes of nx*ny
+ * doubles per checkpoint). fcd_adjoint_gradient runs the reverse sweep from the
+ * current step N back to step 0, one segment between checkpoints at a time,
+ * last first: the segment's forward states are recomputed from its checkpoint
+ * into checkpoint_interval slots (28 planes each, allocated on the first call;
+ * FCD_ENOMEM if they do not fit), then the adjoint of every step runs backwards
+ * through them. Each adjoint step reverses the collision and streaming of every
+ * node and the potential solve: L(k) lam = psib (L of Eq. 6 is symmetric) with
+ * the multigrid of the plain solve to mag_tol relative to max |psib|, then the
+ * permeability and field-strength adjoints of b(k, H0) - L(k) psi'. Bo_m must
+ * be > 0 when a phase is ferrofluid. The handle accepts fcd_step (forward, with
+ * checkpoints), fcd_observables, fcd_get_field, fcd_solve_magnetic,
+ * fcd_kernel_launches, fcd_solver_stats, fcd_last_error and fcd_destroy; state
+ * snapshots and population import return FCD_ESTATE (they would cut the
+ * recorded trajectory). checkpoint_interval >= 1, else FCD_EINVAL. */
+typedef struct {
+    long step;                  /* N, the step of the final state */
+    double T_o, overlap;        /* values at step N */
+    double J;                   /* w_T T_o + w_overlap overlap */
+    double grad[FCD_NDIR];      /* dJ / d(Bo_m, Ca, alpha, nu_r) */
+    long capped_solves;         /* adjoint potential solves that stopped at mag_max_iter */
+} fcd_adjoint_out;
+fcd_status fcd_create_adjoint(const fcd_params *params, int checkpoint_interval, fcd_ctx **out);
+/* Reverse sweep (synchronous). df0, dg0: NULL, or host or device buffers of
+ * 9*nx*ny and 18*nx*ny doubles (layout of fcd_get_populations) that receive
+ * dJ / d(f, g at step 0). The context is back at step N afterwards. Returns
+ * FCD_ENOCONV (with out filled) when an adjoint solve stopped at the cap. */
+fcd_status fcd_adjoint_gradient(fcd_ctx *ctx, double w_T, double w_overlap, fcd_adjoint_out *out,
+                                double *df0, double *dg0);
+
 /* Observables of a caller's population buffer with no device allocation.
  * The paper has no counterpart: this serves callers that cannot allocate
  * device memory (another framework owns the memory budget, cudaMalloc/cudaFree

@@ -15,7 +15,7 @@
 #include <new>
 #include <vector>
 
-#include "fcd_internal.cuh"
+#include "fcd_adjoint.cuh"
 
 namespace fcd {
 size_t observe_scratch_doubles(int nx, int ny);
@@ -1134,6 +1134,343 @@ struct TangentEngine : Engine<double> {
     }
 };
 
+// ---------------------------------------------------------------- adjoint
+// FP64 periodic context that keeps a checkpoint of its state every K steps
+// from step 0 and runs the discrete adjoint of J = wT T_o + wO overlap at its
+// current step back to step 0. Two-level checkpointing: the forward pass stores
+// one state per K steps; the reverse sweep takes the segments last first,
+// recomputes each segment's K states from its checkpoint into slots (every
+// step once more, so the sweep costs one extra forward pass) and runs the
+// adjoint steps backwards through them. The recomputed states are bitwise the
+// ones of the forward pass (same kernels on the same data).
+struct AdjointEngine : Engine<double> {
+    int K = 1;
+    Phys<DualT> PT;                 // constants with their derivatives along theta
+    std::vector<double *> ckpt;     // checkpoint c: the state at step c K
+    size_t ck_doubles = 0;          // f 9, g 18, psiA, psiB, psiP planes; cur, brk, step
+    double *fin = nullptr;          // the final state during a sweep
+    double *seg = nullptr;          // K slots: f 9, g 18, psi' 1 plane
+    long long slot_stride = 0;
+    double *ab[2] = {nullptr, nullptr};  // adjoint states (27 planes each)
+    double *sb = nullptr, *pb = nullptr, *rhs = nullptr, *lamA = nullptr, *lamB = nullptr;
+    double *pacc = nullptr, *hacc = nullptr;
+    int nblk_c = 0, nblk_k = 0;
+    MgCtl *ctla = nullptr;
+    MgHost<double> *mga = nullptr;
+    unsigned long long *rmax = nullptr;
+    int *d_slot = nullptr;
+    void *seed_scr = nullptr;
+    AdjOut *adj_out = nullptr, *h_adj = nullptr;
+    cudaGraph_t agraph[2] = {nullptr, nullptr};
+    cudaGraphExec_t aexec[2] = {nullptr, nullptr};
+    int reported_adj_nonconv = 0;
+
+    ~AdjointEngine() override {
+        if (stream) cudaStreamSynchronize(stream);
+        cudaDeviceSynchronize();
+        for (int c = 0; c < 2; c++) {
+            if (aexec[c]) cudaGraphExecDestroy(aexec[c]);
+            if (agraph[c]) cudaGraphDestroy(agraph[c]);
+        }
+        if (mga) mg_destroy(mga);
+        if (h_adj) cudaFreeHost(h_adj);
+    }
+
+    fcd_status init() override {
+        const fcd_status st = Engine<double>::init();
+        if (st != FCD_OK) return st;
+        PT = tangent_phys(&prm, P);
+        ck_doubles = 30 * (size_t)ps + 4;
+        slot_stride = 28 * ps;
+        nblk_c = adj_collide_blocks(prm.nx, prm.ny);
+        nblk_k = adj_kbar_blocks(prm.nx, prm.ny);
+        for (int c = 0; c < 2; c++) ab[c] = dalloc(27 * ps * sizeof(double));
+        sb = dalloc(13 * ps * sizeof(double));
+        pb = dalloc(2 * ps * sizeof(double));
+        rhs = dalloc(ps * sizeof(double));
+        lamA = dalloc(ps * sizeof(double));
+        lamB = dalloc(ps * sizeof(double));
+        pacc = dalloc((size_t)nblk_c * NPB * sizeof(double));
+        hacc = dalloc((size_t)nblk_k * 2 * sizeof(double));
+        ctla = reinterpret_cast<MgCtl *>(dalloc(sizeof(MgCtl)));
+        rmax = reinterpret_cast<unsigned long long *>(dalloc(sizeof(unsigned long long)));
+        d_slot = reinterpret_cast<int *>(dalloc(sizeof(int)));
+        seed_scr = dalloc(adj_seed_scratch_bytes(prm.nx));
+        adj_out = reinterpret_cast<AdjOut *>(dalloc(sizeof(AdjOut)));
+        for (void *q : {(void *)ab[0], (void *)ab[1], (void *)sb, (void *)pb, (void *)rhs, (void *)lamA,
+                        (void *)lamB, (void *)pacc, (void *)hacc, (void *)ctla, (void *)rmax,
+                        (void *)d_slot, seed_scr, (void *)adj_out})
+            if (!q) return fail(FCD_ENOMEM, "device allocation failed");
+        // padding columns stay zero in every adjoint plane
+        for (int c = 0; c < 2; c++) CK(cudaMemsetAsync(ab[c], 0, 27 * ps * sizeof(double), stream));
+        CK(cudaMemsetAsync(sb, 0, 13 * ps * sizeof(double), stream));
+        CK(cudaMemsetAsync(pb, 0, 2 * ps * sizeof(double), stream));
+        CK(cudaMemsetAsync(rhs, 0, ps * sizeof(double), stream));
+        CK(cudaMallocHost(&h_adj, sizeof(AdjOut)));
+        return push_checkpoint();
+    }
+
+    fcd_status save(double *dst) {
+        cudaStream_t s = stream;
+        CK(cudaMemcpyAsync(dst, f[cur], 9 * ps * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(dst + 9 * ps, g[cur], 18 * ps * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(dst + 27 * ps, psiA, ps * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(dst + 28 * ps, psiB, ps * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(dst + 29 * ps, psiP, ps * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        double *tail = dst + 30 * ps;
+        CK(cudaMemcpyAsync(tail, &ctl->cur, sizeof(int), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(tail + 1, brk, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(tail + 2, d_step, sizeof(long long), cudaMemcpyDeviceToDevice, s));
+        return FCD_OK;
+    }
+
+    fcd_status restore(const double *src, long at_step) {
+        cudaStream_t s = stream;
+        CK(cudaMemcpyAsync(f[cur], src, 9 * ps * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(g[cur], src + 9 * ps, 18 * ps * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(psiA, src + 27 * ps, ps * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(psiB, src + 28 * ps, ps * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(psiP, src + 29 * ps, ps * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        const double *tail = src + 30 * ps;
+        CK(cudaMemcpyAsync(&ctl->cur, tail, sizeof(int), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(brk, tail + 1, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(d_step, tail + 2, sizeof(long long), cudaMemcpyDeviceToDevice, s));
+        step = at_step;
+        return FCD_OK;
+    }
+
+    fcd_status push_checkpoint() {
+        double *c = dalloc(ck_doubles * sizeof(double));
+        if (!c) return fail(FCD_ENOMEM, "checkpoint allocation failed at step %ld", step);
+        ckpt.push_back(c);
+        return save(c);
+    }
+
+    fcd_status do_step(long n) override {
+        if (n < 0) return fail(FCD_EINVAL, "negative step count");
+        while (n > 0) {
+            if (step % K == 0 && (size_t)(step / K) == ckpt.size()) {
+                const fcd_status st = push_checkpoint();
+                if (st != FCD_OK) return st;
+            }
+            const long m = std::min(n, (long)(K - step % K));
+            const fcd_status st = Engine<double>::do_step(m);
+            if (st != FCD_OK) return st;
+            n -= m;
+        }
+        return FCD_OK;
+    }
+
+    // One adjoint step on s: reads the slot *d_slot and ab[c], writes ab[c ^ 1].
+    fcd_status enqueue_adj_step(int c, cudaStream_t s, bool capture) {
+        launch_adj_phase(P, seg, d_slot, slot_stride, phi1, phi2, k, s);
+        AdjArgs A;
+        A.P = P;
+        A.seg = seg;
+        A.slot = d_slot;
+        A.stride = slot_stride;
+        A.phi1 = phi1;
+        A.phi2 = phi2;
+        A.ab_src = ab[c];
+        A.ab_dst = ab[c ^ 1];
+        A.sb = sb;
+        A.pacc = pacc;
+        launch_adj_collide(A, s);
+        launch_adj_gather(P, sb, phi1, phi2, pb, rhs, rmax, s);
+        if (magnetic()) {
+            mg_reset_scaled(ctla, rmax, prm.mag_tol, prm.mag_max_iter, s);
+            mg_presmooth<double>(mga, P.H0c, P.H0s, s);
+            const fcd_status st = capture ? capture_mg_loop(s, mga) : host_mg_loop(s, mga, ctla);
+            if (st != FCD_OK) return st;
+        }
+        AdjKArgs B;
+        B.P = P;
+        B.seg = seg;
+        B.slot = d_slot;
+        B.stride = slot_stride;
+        B.k = k;
+        B.phi1 = phi1;
+        B.phi2 = phi2;
+        B.pb = pb;
+        B.lamA = lamA;
+        B.lamB = lamB;
+        B.ctl = magnetic() ? ctla : nullptr;
+        B.ab = ab[c ^ 1];
+        B.hacc = hacc;
+        launch_adj_kbar(B, s);
+        launch_dec_slot(d_slot, s);
+        CK(cudaGetLastError());
+        return FCD_OK;
+    }
+    // kernels of one adjoint step outside the multigrid cycles
+    long adj_step_kernels() const { return 6 + (magnetic() ? 2 : 0); }
+
+    fcd_status adj_step(int c) {
+        cudaStream_t s = stream;
+        if (use_graph) {
+            if (!aexec[c]) {
+                CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+                const fcd_status st = enqueue_adj_step(c, cap, true);
+                cudaGraph_t gr = nullptr;
+                const cudaError_t e = cudaStreamEndCapture(cap, &gr);
+                if (st != FCD_OK) {
+                    if (gr) cudaGraphDestroy(gr);
+                    return st;
+                }
+                CK(e);
+                agraph[c] = gr;
+                CK(cudaGraphInstantiate(&aexec[c], agraph[c], 0));
+            }
+            CK(cudaGraphLaunch(aexec[c], s));
+        } else {
+            const fcd_status st = enqueue_adj_step(c, s, false);
+            if (st != FCD_OK) return st;
+        }
+        host_kernels += adj_step_kernels();
+        return FCD_OK;
+    }
+
+    fcd_status gradient(double wT, double wO, fcd_adjoint_out *o, double *df0, double *dg0) {
+        const long N = step;
+        cudaStream_t s = stream;
+        if (!mga && magnetic()) {
+            mga = mg_create<double>(prm.nx, prm.ny, pitch, k, lamA, lamB, ctla, alloc, release, user, err,
+                                    sizeof err);
+            if (!mga) return FCD_ENOMEM;
+            mg_set_rhs<double>(mga, rhs);
+        }
+        if (!seg && N > 0) {
+            seg = dalloc((size_t)K * slot_stride * sizeof(double));
+            if (!seg)
+                return fail(FCD_ENOMEM, "no room for %d recomputed states (%.2f GB); use a smaller "
+                            "checkpoint interval", K, K * slot_stride * 8.0 / 1e9);
+        }
+        if (!fin) {
+            fin = dalloc(ck_doubles * sizeof(double));
+            if (!fin) return fail(FCD_ENOMEM, "device allocation failed");
+        }
+        // J at the final state and its adjoint there
+        fcd_obs po;
+        fcd_status st = observe(&po);  // plain observables (seam column for l_x)
+        if (st != FCD_OK && st != FCD_ENOCONV) return st;
+        launch_phase<double>(MODE_FP64, P, g[cur], phi1, phi2, nullptr,
+                             PhaseCtl{nullptr, 0, 0.0, 0, nullptr, 0, nullptr, nullptr, nullptr}, s);
+        launch_adj_seed(P, phi1, phi2, obs_out, wT, wO, seed_scr, pb, ab[0], adj_out, s);
+        host_kernels += 3;
+        CK(cudaMemcpyAsync(h_adj, adj_out, sizeof(AdjOut), cudaMemcpyDeviceToHost, s));
+        if (wT == 0.0 && wO == 0.0 && !df0 && !dg0) {  // J = 0: values only, zero gradient
+            CK(cudaStreamSynchronize(s));
+            std::memset(o, 0, sizeof *o);
+            o->step = N;
+            o->T_o = h_adj->T_o;
+            o->overlap = h_adj->overlap;
+            return FCD_OK;
+        }
+        CK(cudaMemsetAsync(pacc, 0, (size_t)nblk_c * NPB * sizeof(double), s));
+        CK(cudaMemsetAsync(hacc, 0, (size_t)nblk_k * 2 * sizeof(double), s));
+        CK(cudaMemsetAsync(lamA, 0, ps * sizeof(double), s));
+        CK(cudaMemsetAsync(lamB, 0, ps * sizeof(double), s));
+        CK(cudaMemsetAsync(ctla, 0, sizeof(MgCtl), s));
+        int nonconv0 = 0;
+        st = save(fin);
+        if (st != FCD_OK) return st;
+        int ca = 0;
+        const long nseg = (N + K - 1) / K;
+        for (long q = nseg - 1; q >= 0; q--) {
+            const long n0 = q * K, n1 = std::min(N, n0 + K);
+            const int len = (int)(n1 - n0);
+            st = restore(ckpt[q], n0);
+            if (st != FCD_OK) return st;
+            for (int j = 0; j < len; j++) {
+                double *sl = seg + j * slot_stride;
+                CK(cudaMemcpyAsync(sl, f[cur], 9 * ps * sizeof(double), cudaMemcpyDeviceToDevice, s));
+                CK(cudaMemcpyAsync(sl + 9 * ps, g[cur], 18 * ps * sizeof(double), cudaMemcpyDeviceToDevice, s));
+                st = Engine<double>::do_step(1);
+                if (st != FCD_OK) return st;
+                mg_psi_io(mg, 0, sl + 27 * ps, nullptr, s);  // the potential that step used
+                host_kernels += 1;
+            }
+            launch_set_slot(d_slot, len - 1, s);
+            host_kernels += 1;
+            for (int j = len - 1; j >= 0; j--) {
+                st = adj_step(ca);
+                if (st != FCD_OK) return st;
+                ca ^= 1;
+            }
+        }
+        st = restore(fin, N);
+        if (st != FCD_OK) return st;
+        // constants' adjoints, summed block by block in a fixed order
+        std::vector<double> hp((size_t)nblk_c * NPB), hh((size_t)nblk_k * 2);
+        CK(cudaMemcpyAsync(hp.data(), pacc, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(hh.data(), hacc, hh.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        double pbar[NPB] = {0.0};
+        for (int b = 0; b < nblk_c; b++)
+            for (int q = 0; q < NPB; q++) pbar[q] += hp[(size_t)b * NPB + q];
+        for (int b = 0; b < nblk_k; b++) {
+            pbar[PB_H0C] += hh[2 * (size_t)b];
+            pbar[PB_H0S] += hh[2 * (size_t)b + 1];
+        }
+        const DualT *dp[NPB] = {&PT.s12, &PT.s13, &PT.s23, &PT.gam[0], &PT.gam[1], &PT.gam[2],
+                                &PT.eta, &PT.lap_coef[0], &PT.lap_coef[1], &PT.lap_coef[2],
+                                &PT.H0c, &PT.H0s, &PT.tau[0], &PT.tau[1], &PT.tau[2]};
+        std::memset(o, 0, sizeof *o);
+        o->step = N;
+        o->T_o = h_adj->T_o;
+        o->overlap = h_adj->overlap;
+        o->J = wT * h_adj->T_o + wO * h_adj->overlap;
+        for (int c = 0; c < NT; c++) {
+            double gsum = 0.0;
+            for (int q = 0; q < NPB; q++) gsum += pbar[q] * dp[q]->d[c];
+            o->grad[c] = gsum;
+        }
+        if (df0 || dg0) {
+            const size_t Nn = (size_t)prm.nx * prm.ny;
+            double *stg = staging(27 * Nn);
+            if (!stg) return fail(FCD_ENOMEM, "staging allocation failed");
+            launch_export<double>(MODE_FP64, P, ab[ca], ab[ca] + 9 * ps, stg, stg + 9 * Nn, s);
+            host_kernels += 1;
+            cudaError_t e = cudaGetLastError();
+            if (e == cudaSuccess && df0) e = cudaMemcpyAsync(df0, stg, 9 * Nn * sizeof(double), cudaMemcpyDefault, s);
+            if (e == cudaSuccess && dg0) e = cudaMemcpyAsync(dg0, stg + 9 * Nn, 18 * Nn * sizeof(double), cudaMemcpyDefault, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            cudaFree(stg);
+            if (e != cudaSuccess) return fail(FCD_ECUDA, "adjoint export: %s", cudaGetErrorString(e));
+        }
+        if (magnetic()) {
+            CK(cudaMemcpy(h_ctl, ctla, sizeof(MgCtl), cudaMemcpyDeviceToHost));
+            o->capped_solves = h_ctl->nonconv_count - nonconv0;
+            if (o->capped_solves > 0)
+                return fail(FCD_ENOCONV, "%ld adjoint potential solves stopped at the cycle cap",
+                            o->capped_solves);
+        }
+        return FCD_OK;
+    }
+
+    long launches() const override {
+        long n = Engine<double>::launches();
+        if (mga) {
+            MgCtl q;
+            if (cudaMemcpy(&q, ctla, sizeof q, cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+            n += (long)q.cycles_launched + (long)q.total_cycles * mg_kernels_per_cycle(mga) +
+                 (long)q.smooth_cycles + 2 * (long)q.twogrid_cycles;
+        }
+        return n;
+    }
+
+    size_t state_bytes() const override { return 0; }
+    fcd_status get_state(void *, size_t) override {
+        return fail(FCD_ESTATE, "state snapshots are not available for adjoint contexts");
+    }
+    fcd_status set_state(const void *, size_t) override {
+        return fail(FCD_ESTATE, "state snapshots are not available for adjoint contexts");
+    }
+    fcd_status set_pops(const double *, const double *, const double *, long) override {
+        return fail(FCD_ESTATE, "population import is not available for adjoint contexts");
+    }
+};
+
 // ---------------------------------------------------------------- C ABI
 static thread_local char g_last[512];  // reason of the last failed fcd_create on this thread
 
@@ -1212,6 +1549,49 @@ fcd_status fcd_tangent_observables(fcd_ctx *c, fcd_tangent_obs *o) {
     auto *e = dynamic_cast<TangentEngine *>(c);
     if (!e) return c->fail(FCD_EINVAL, "not a tangent context");
     return e->tangent_observe(o);
+}
+
+fcd_status fcd_create_adjoint(const fcd_params *params, int checkpoint_interval, fcd_ctx **out) {
+    if (!out) return FCD_EINVAL;
+    *out = nullptr;
+    if (!params) return FCD_EINVAL;
+    fcd_params p = *params;
+    p.precision = FCD_FP64;
+    Derived d;
+    std::memset(&d, 0, sizeof d);
+    const char *why = derive(&p, &d);
+    if (!why && checkpoint_interval < 1) why = "checkpoint_interval must be >= 1";
+    if (!why && p.open_x != 0) why = "the adjoint form covers the periodic channel (open_x = 0)";
+    if (!why && p.ferro_phase != 0 && !(p.Bo_m > 0))
+        why = "the Bo_m direction needs Bo_m > 0 (H0 ~ sqrt(Bo_m))";
+    if (why) {
+        snprintf(g_last, sizeof g_last, "fcd_create_adjoint: %s", why);
+        return FCD_EINVAL;
+    }
+    auto *e = new (std::nothrow) AdjointEngine();
+    if (!e) return FCD_ENOMEM;
+    e->alloc = g_alloc ? g_alloc : default_alloc;
+    e->release = g_free ? g_free : default_free;
+    e->user = g_alloc ? g_user : nullptr;
+    e->prm = p;
+    e->D = d;
+    e->K = checkpoint_interval;
+    const fcd_status st = e->init();
+    if (st != FCD_OK) {
+        snprintf(g_last, sizeof g_last, "%s", e->err);
+        delete e;
+        return st;
+    }
+    *out = e;
+    return FCD_OK;
+}
+
+fcd_status fcd_adjoint_gradient(fcd_ctx *c, double w_T, double w_overlap, fcd_adjoint_out *o,
+                                double *df0, double *dg0) {
+    if (!c || !o) return FCD_EINVAL;
+    auto *e = dynamic_cast<AdjointEngine *>(c);
+    if (!e) return c->fail(FCD_EINVAL, "not an adjoint context");
+    return e->gradient(w_T, w_overlap, o, df0, dg0);
 }
 
 fcd_status fcd_set_stream(fcd_ctx *c, void *stream) {

@@ -254,6 +254,52 @@ size_t tangent_obs_scratch_bytes(int nx);
 void launch_tangent_obs(const Phys<double> &P, const double *g, const ObsOut *prim, void *scratch,
                         TanOut *out, cudaStream_t s);
 
+// adjoint step (FP64, periodic channel). A segment of forward states sits in
+// slots of `stride` doubles (f 9 planes, g 18 planes, psi' 1 plane); *slot is
+// the slot of the step being reversed. Adjoint states hold 27 planes (fb, gb).
+struct AdjArgs {
+    Phys<double> P;
+    const double *seg;
+    const int *slot;
+    long long stride;
+    const double *phi1, *phi2;  // phase fields of the slot's state
+    const double *ab_src;       // adjoint after the step
+    double *ab_dst;             // adjoint before the step (direct terms)
+    double *sb;                 // 13 planes: adjoints of the reduced stencil values
+    double *pacc;               // per block: adjoints of the constants (NPB each)
+};
+struct AdjKArgs {
+    Phys<double> P;
+    const double *seg;
+    const int *slot;
+    long long stride;
+    const double *k, *phi1, *phi2;
+    const double *pb;              // 2 planes: phase-field adjoints from the stencils
+    const double *lamA, *lamB;     // adjoint potential buffers
+    const MgCtl *ctl;              // its control block (nullptr: no field)
+    double *ab;                    // adjoint before the step (gb += phib)
+    double *hacc;                  // per block: adjoints of H0 cos(alpha), H0 sin(alpha)
+};
+struct AdjOut {
+    double T_o, overlap, lx, ly;
+};
+int adj_collide_blocks(int nx, int ny);
+int adj_kbar_blocks(int nx, int ny);
+size_t adj_seed_scratch_bytes(int nx);
+void launch_adj_phase(const Phys<double> &P, const double *seg, const int *slot, long long stride,
+                      double *phi1, double *phi2, double *k, cudaStream_t s);
+void launch_adj_collide(const AdjArgs &a, cudaStream_t s);
+void launch_adj_gather(const Phys<double> &P, const double *sb, const double *phi1, const double *phi2,
+                       double *pb, double *rhs, unsigned long long *rmax, cudaStream_t s);
+void launch_adj_kbar(const AdjKArgs &a, cudaStream_t s);
+void launch_set_slot(int *slot, int v, cudaStream_t s);
+void launch_dec_slot(int *slot, cudaStream_t s);
+// seed of J = wT T_o + wO overlap at the state whose phase fields are phi1,
+// phi2 (prim: the plain observables of that state, for the seam column)
+void launch_adj_seed(const Phys<double> &P, const double *phi1, const double *phi2, const ObsOut *prim,
+                     double wT, double wO, void *scratch, double *pb, double *ab, AdjOut *out,
+                     cudaStream_t s);
+
 // observables
 size_t observe_scratch_doubles(int nx, int ny);
 template <typename T>

@@ -70,6 +70,17 @@ class fcd_tangent_obs(C.Structure):
                 for n, _ in self._fields_}
 
 
+class fcd_adjoint_out(C.Structure):
+    _fields_ = [
+        ("step", C.c_long), ("T_o", C.c_double), ("overlap", C.c_double), ("J", C.c_double),
+        ("grad", C.c_double * 4), ("capped_solves", C.c_long),
+    ]
+
+    def as_dict(self):
+        return {n: (list(getattr(self, n)) if n == "grad" else getattr(self, n))
+                for n, _ in self._fields_}
+
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 
@@ -107,6 +118,9 @@ _SIGS = {
     "fcd_batch_destroy": (None, [C.c_void_p]),
     "fcd_create_tangent": (C.c_int, [C.POINTER(fcd_params), C.POINTER(C.c_void_p)]),
     "fcd_tangent_observables": (C.c_int, [C.c_void_p, C.POINTER(fcd_tangent_obs)]),
+    "fcd_create_adjoint": (C.c_int, [C.POINTER(fcd_params), C.c_int, C.POINTER(C.c_void_p)]),
+    "fcd_adjoint_gradient": (C.c_int, [C.c_void_p, C.c_double, C.c_double,
+                                       C.POINTER(fcd_adjoint_out), C.c_void_p, C.c_void_p]),
     "fcd_destroy": (None, [C.c_void_p]),
 }
 
@@ -197,7 +211,7 @@ class Channel:
             use_torch_allocator()
         self.params = make_params(cfg)
         h = C.c_void_p()
-        st = getattr(L, self._create)(C.byref(self.params), C.byref(h))
+        st = self._make(L, h)
         if st != FCD_OK:
             raise FcdError(st, L.fcd_last_error(None).decode())
         self.h = h
@@ -206,6 +220,9 @@ class Channel:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
         self.check(L.fcd_set_stream(self.h, C.c_void_p(stream)))
+
+    def _make(self, L, h):
+        return getattr(L, self._create)(C.byref(self.params), C.byref(h))
 
     def check(self, st, allow=()):
         if st != FCD_OK and st not in allow:
@@ -310,6 +327,41 @@ class Tangent(Channel):
         return o.as_dict()
 
 
+class Adjoint(Channel):
+    """FP64 periodic context that keeps a checkpoint every `checkpoint` steps;
+    its reverse sweep gives dJ/d(Bo_m, Ca, alpha, nu_r) and dJ/d(initial
+    populations) for J = w_T T_o + w_overlap overlap (fcd_create_adjoint)."""
+
+    def __init__(self, cfg, checkpoint=500, stream=None, torch_alloc=True):
+        self.checkpoint = int(checkpoint)
+        super().__init__(cfg, stream, torch_alloc)
+
+    def _make(self, L, h):
+        return L.fcd_create_adjoint(C.byref(self.params), self.checkpoint, C.byref(h))
+
+    def gradient(self, w_T=1.0, w_overlap=0.0, initial=False, allow=()):
+        """Reverse sweep back to step 0. With initial=True the result also holds
+        df0 (9, ny, nx) and dg0 (2, 9, ny, nx): dJ/d(populations at step 0)."""
+        o = fcd_adjoint_out()
+        df0 = dg0 = None
+        if initial:
+            df0 = np.empty((9, self.ny, self.nx))
+            dg0 = np.empty((2, 9, self.ny, self.nx))
+        ptr = lambda a: None if a is None else C.c_void_p(a.ctypes.data)
+        st = load().fcd_adjoint_gradient(self.h, float(w_T), float(w_overlap), C.byref(o),
+                                         ptr(df0), ptr(dg0))
+        self.check(st, allow=allow)
+        out = o.as_dict()
+        if initial:
+            out["df0"], out["dg0"] = df0, dg0
+        return out
+
+    def values(self):
+        """(T_o, overlap) of the current state (no sweep: J = 0 has zero gradient)."""
+        o = self.gradient(0.0, 0.0, allow=(FCD_ENOCONV,))
+        return o["T_o"], o["overlap"]
+
+
 def with_parameters(cfg, theta):
     """cfg with (Bo_m, Ca, alpha [rad], nu_r) set; nu_r = nu_3 / nu_2 (Eq. 39)."""
     bo, ca, al, nr = (float(v) for v in theta)
@@ -355,15 +407,61 @@ def _droplet_function():
     return DropletObservables
 
 
+def _droplet_adjoint_function():
+    import torch
+
+    class DropletObservablesAdjoint(torch.autograd.Function):
+        """(T_o, overlap) of cfg after `steps` coupled steps, as a function of
+        theta = (Bo_m, Ca, alpha, nu_r). Forward runs the plain FP64 step with
+        checkpoints; backward runs the discrete adjoint once, for the scalar
+        grad_out . (T_o, overlap)."""
+
+        @staticmethod
+        def forward(ctx, theta, cfg, steps, checkpoint):
+            ch = Adjoint(with_parameters(cfg, theta.detach().cpu().tolist()), checkpoint)
+            try:
+                if steps:
+                    ch.step(int(steps))
+                vals = ch.values()
+            except Exception:
+                ch.close()
+                raise
+            ctx.ch = ch
+            return torch.tensor(vals, dtype=torch.float64, device=theta.device)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            w = grad_out.detach().to(device="cpu", dtype=torch.float64).tolist()
+            ch = ctx.ch
+            try:
+                o = ch.gradient(w[0], w[1])
+            finally:
+                ch.close()
+                ctx.ch = None
+            g = torch.tensor(o["grad"], dtype=torch.float64, device=grad_out.device)
+            return g, None, None, None
+
+    return DropletObservablesAdjoint
+
+
 _DROPLET_FN = None
+_DROPLET_ADJ_FN = None
 
 
-def droplet_observables(theta, cfg, steps):
-    """Differentiable (T_o, overlap): torch.autograd entry point of the tangent form."""
-    global _DROPLET_FN
-    if _DROPLET_FN is None:
-        _DROPLET_FN = _droplet_function()
-    return _DROPLET_FN.apply(theta, cfg, steps)
+def droplet_observables(theta, cfg, steps, method="tangent", checkpoint=500):
+    """Differentiable (T_o, overlap): torch.autograd entry point of the tangent
+    form (method="tangent": the 2 x 4 Jacobian is formed in forward) or of the
+    discrete adjoint (method="adjoint": one reverse sweep in backward)."""
+    global _DROPLET_FN, _DROPLET_ADJ_FN
+    if method == "tangent":
+        if _DROPLET_FN is None:
+            _DROPLET_FN = _droplet_function()
+        return _DROPLET_FN.apply(theta, cfg, steps)
+    if method == "adjoint":
+        if _DROPLET_ADJ_FN is None:
+            _DROPLET_ADJ_FN = _droplet_adjoint_function()
+        return _DROPLET_ADJ_FN.apply(theta, cfg, steps, checkpoint)
+    raise ValueError("method must be 'tangent' or 'adjoint'")
 
 
 class _Instance(Channel):

@@ -1,12 +1,14 @@
-"""Gradient of the shell deformation: tangent-linear run against central
-differences of the plain FP64 method, on the same GPU.
+"""Gradient of the shell deformation: tangent-linear run and discrete adjoint
+against central differences of the plain FP64 method, on the same GPU.
 
   python -m paper_2410_11129_gb300.gradient --steps 20000
-  python -m paper_2410_11129_gb300.gradient --steps 500 --h 1e-4
+  python -m paper_2410_11129_gb300.gradient --steps 500 --h 1e-4 --checkpoint 500
 
 The tangent context advances the state and its derivatives along
-(Bo_m, Ca, alpha, nu_r) together; central differences need two plain runs per
-direction (eight in all) with theta_j +- h * max(|theta_j|, 1). Both report
+(Bo_m, Ca, alpha, nu_r) together; the adjoint context runs the plain step with
+a checkpoint every `checkpoint` steps, then one reverse sweep per functional
+(T_o, then the overlap); central differences need two plain runs per
+direction (eight in all) with theta_j +- h * max(|theta_j|, 1). All report
 dT_o/dtheta and d overlap/dtheta (overlap = sum phi_1 phi_3) at the final
 step; the wall time of each includes every run it needs.
 """
@@ -39,6 +41,26 @@ def tangent_gradient(cfg, steps):
     return o, time.perf_counter() - t0, stats
 
 
+def adjoint_gradient(cfg, steps, checkpoint):
+    """Forward pass with checkpoints, then the sweep for T_o and the sweep for
+    the overlap; seconds: the forward pass plus the T_o sweep, and the total."""
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ch = fcd.Adjoint(cfg, checkpoint)
+    ch.step(steps)
+    aT = ch.gradient(1.0, 0.0, allow=(fcd.FCD_ENOCONV,))
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    aO = ch.gradient(0.0, 1.0, allow=(fcd.FCD_ENOCONV,))
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    ch.close()
+    return ({"dT_o": aT["grad"], "doverlap": aO["grad"], "T_o": aT["T_o"],
+             "capped_solves": aT["capped_solves"] + aO["capped_solves"]},
+            t1 - t0, t2 - t0)
+
+
 def difference_gradient(cfg, steps, h_rel):
     import torch
     theta = list(fcd.parameters_of(cfg))
@@ -62,21 +84,27 @@ def difference_gradient(cfg, steps, h_rel):
     return {"dT_o": dT, "doverlap": dO}, time.perf_counter() - t0
 
 
-def compare(cfg, steps, h_rel=1e-4):
+def compare(cfg, steps, h_rel=1e-4, checkpoint=500):
     cfg = dict(cfg, precision="fp64")
     o, t_tan, stats = tangent_gradient(cfg, steps)
+    adj, t_adj1, t_adj2 = adjoint_gradient(cfg, steps, checkpoint)
     fd, t_fd = difference_gradient(cfg, steps, h_rel)
     out = {"workload": cfg.get("name", "%dx%d" % (cfg["nx"], cfg["ny"])), "steps": steps,
            "directions": list(fcd.DIRECTIONS), "mag_tol": cfg["mag_tol"], "h_rel": h_rel,
            "T_o": o["T_o"], "overlap": o["overlap"],
            "tangent": {"dT_o": o["dT_o"], "doverlap": o["doverlap"], "seconds": t_tan,
                        "solver": stats},
+           "adjoint": dict(adj, checkpoint=checkpoint, seconds_one_functional=t_adj1,
+                           seconds_both=t_adj2),
            "central_differences": dict(fd, seconds=t_fd, runs=8),
-           "speedup": t_fd / t_tan}
+           "speedup": t_fd / t_tan,
+           "speedup_adjoint_one_functional": t_fd / t_adj1,
+           "speedup_adjoint_both": t_fd / t_adj2}
     for q in ("dT_o", "doverlap"):
-        a, b = np.array(o[q]), np.array(fd[q])
+        a, b, c = np.array(o[q]), np.array(fd[q]), np.array(adj[q])
         scale = max(np.abs(a).max(), 1e-300)
         out["max_rel_diff_" + q] = float(np.abs(a - b).max() / scale)
+        out["max_rel_diff_adjoint_tangent_" + q] = float(np.abs(c - a).max() / scale)
     return out
 
 
@@ -84,8 +112,10 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--steps", type=int, default=W.C5["steps"])
     ap.add_argument("--h", type=float, default=1e-4, help="relative step of the differences")
+    ap.add_argument("--checkpoint", type=int, default=W.C5.get("checkpoint", 500),
+                    help="checkpoint interval of the adjoint")
     args = ap.parse_args(argv)
-    print(json.dumps(compare(W.C5, args.steps, args.h), indent=1), flush=True)
+    print(json.dumps(compare(W.C5, args.steps, args.h, args.checkpoint), indent=1), flush=True)
     return 0
 
 

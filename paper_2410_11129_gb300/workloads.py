@@ -65,7 +65,7 @@ C3 = dict(channel(2400, 300, 45, 90, Ca=0.2, Bo_m=3.0, alpha_deg=90.0, ferro="co
 # of the bulk, where grad(phi) is round-off, has a Jacobian of order
 # theta / eps_n ~ 100 per step, and the tangent of the step grows without bound.
 C5 = dict(channel(800, 100, 15, 30, Ca=0.15, Bo_m=2.0, alpha_deg=0.0, ferro="shell", eps_n=1e-6),
-          name="channel-800x100", steps=20000, precision="fp64")
+          name="channel-800x100", steps=20000, checkpoint=500, precision="fp64")
 
 # The paper's own channel (Sec. 2.6: H x L = 150 x 900, L = 6H) as an open channel
 # (Eq. 37 inlet, convective outlet), with the parameters of its grid study (Fig. 4):

@@ -62,3 +62,21 @@ def test_null_arguments():
     assert L.fcd_create(None, None) == fcd.FCD_EINVAL
     assert L.fcd_step(None, 1) == fcd.FCD_EINVAL
     assert L.fcd_observables(None, None) == fcd.FCD_EINVAL
+
+
+@pytest.mark.parametrize("bad,K", [
+    (dict(open_x=1), 10),   # the adjoint form covers the periodic channel
+    ({}, 0),                # checkpoint interval
+    (dict(Bo_m=0.0), 10),   # H0 ~ sqrt(Bo_m): no derivative at 0
+    (dict(nx=7), 10),
+])
+def test_adjoint_create_rejects(bad, K):
+    L = fcd.load()
+    cfg = W.small()
+    cfg.update(bad)
+    p = fcd.make_params(cfg)
+    h = C.c_void_p()
+    assert L.fcd_create_adjoint(C.byref(p), K, C.byref(h)) == fcd.FCD_EINVAL
+    assert not h.value
+    assert L.fcd_last_error(None).decode().startswith("fcd_create_adjoint:")
+    assert L.fcd_adjoint_gradient(None, 1.0, 0.0, None, None, None) == fcd.FCD_EINVAL
