@@ -248,9 +248,10 @@ fcd_status fcd_tangent_observables(fcd_ctx *ctx, fcd_tangent_obs *out);
  * doubles per checkpoint). fcd_adjoint_gradient runs the reverse sweep from the
  * current step N back to step 0, one segment between checkpoints at a time,
  * last first: the segment's forward states are recomputed from its checkpoint
- * into checkpoint_interval slots (28 planes each, allocated on the first call;
+ * into checkpoint_interval slots (28 planes each, allocated by the first step;
  * FCD_ENOMEM if they do not fit), then the adjoint of every step runs backwards
- * through them. Each adjoint step reverses the collision and streaming of every
+ * through them. fcd_step keeps the states of the current segment in the slots,
+ * so the last segment is not recomputed (none is when checkpoint_interval >= N). Each adjoint step reverses the collision and streaming of every
  * node and the potential solve: L(k) lam = psib (L of Eq. 6 is symmetric) with
  * the multigrid of the plain solve to mag_tol relative to max |psib|, then the
  * permeability and field-strength adjoints of b(k, H0) - L(k) psi'. Bo_m must
@@ -265,6 +266,8 @@ typedef struct {
     double J;                   /* w_T T_o + w_overlap overlap */
     double grad[FCD_NDIR];      /* dJ / d(Bo_m, Ca, alpha, nu_r) */
     long capped_solves;         /* adjoint potential solves that stopped at mag_max_iter */
+    long recomputed_steps;      /* forward steps the sweep recomputed from checkpoints */
+    long long solve_cycles;     /* multigrid cycles of the sweep's adjoint potential solves */
 } fcd_adjoint_out;
 fcd_status fcd_create_adjoint(const fcd_params *params, int checkpoint_interval, fcd_ctx **out);
 /* Reverse sweep (synchronous). df0, dg0: NULL, or host or device buffers of

@@ -494,34 +494,40 @@ struct Engine : fcd_ctx {
         return FCD_OK;
     }
 
+    // One step; sm != 0 also stores the macroscopic fields.
+    fcd_status one_step(int sm) {
+        cudaStream_t s = stream;
+        if (use_graph) {
+            if (!gexec[cur][sm]) {
+                fcd_status st = build_graph(cur, sm);
+                if (st != FCD_OK) return st;
+            }
+            CK(cudaGraphLaunch(gexec[cur][sm], s));
+            host_kernels += pre_kernels() + post_kernels();
+        } else {
+            if (profiling) CK(cudaEventRecord(ev[0], s));
+            enqueue_pre(cur, s);
+            if (profiling) CK(cudaEventRecord(ev[1], s));
+            if (magnetic()) {
+                fcd_status st = host_mg_loop(s);
+                if (st != FCD_OK) return st;
+            }
+            if (profiling) CK(cudaEventRecord(ev[2], s));
+            enqueue_post(cur, sm != 0, s);
+            if (profiling) CK(cudaEventRecord(ev[3], s));
+            host_kernels += pre_kernels() + post_kernels();
+            CK(cudaGetLastError());
+        }
+        cur ^= 1;
+        step++;
+        return FCD_OK;
+    }
+
     fcd_status do_step(long n) override {
         if (n < 0) return fail(FCD_EINVAL, "negative step count");
-        cudaStream_t s = stream;
         for (long i = 0; i < n; i++) {
-            const int sm = i == n - 1 ? 1 : 0;
-            if (use_graph) {
-                if (!gexec[cur][sm]) {
-                    fcd_status st = build_graph(cur, sm);
-                    if (st != FCD_OK) return st;
-                }
-                CK(cudaGraphLaunch(gexec[cur][sm], s));
-                host_kernels += pre_kernels() + post_kernels();
-            } else {
-                if (profiling) CK(cudaEventRecord(ev[0], s));
-                enqueue_pre(cur, s);
-                if (profiling) CK(cudaEventRecord(ev[1], s));
-                if (magnetic()) {
-                    fcd_status st = host_mg_loop(s);
-                    if (st != FCD_OK) return st;
-                }
-                if (profiling) CK(cudaEventRecord(ev[2], s));
-                enqueue_post(cur, sm != 0, s);
-                if (profiling) CK(cudaEventRecord(ev[3], s));
-                host_kernels += pre_kernels() + post_kernels();
-                CK(cudaGetLastError());
-            }
-            cur ^= 1;
-            step++;
+            const fcd_status st = one_step(i == n - 1 ? 1 : 0);
+            if (st != FCD_OK) return st;
         }
         CK(cudaGetLastError());
         return FCD_OK;
@@ -1151,6 +1157,7 @@ struct AdjointEngine : Engine<double> {
     double *fin = nullptr;          // the final state during a sweep
     double *seg = nullptr;          // K slots: f 9, g 18, psi' 1 plane
     long long slot_stride = 0;
+    std::vector<long> slot_step;    // the step whose state slot j holds (-1: none)
     double *ab[2] = {nullptr, nullptr};  // adjoint states (27 planes each)
     double *sb = nullptr, *pb = nullptr, *rhs = nullptr, *lamA = nullptr, *lamB = nullptr;
     double *pacc = nullptr, *hacc = nullptr;
@@ -1246,18 +1253,49 @@ struct AdjointEngine : Engine<double> {
         return save(c);
     }
 
+    fcd_status alloc_slots() {
+        if (seg) return FCD_OK;
+        seg = dalloc((size_t)K * slot_stride * sizeof(double));
+        if (!seg)
+            return fail(FCD_ENOMEM, "no room for %d recomputed states (%.2f GB); use a smaller "
+                        "checkpoint interval", K, K * slot_stride * 8.0 / 1e9);
+        slot_step.assign(K, -1);
+        return FCD_OK;
+    }
+
+    // One forward step that also keeps its state in slot (step mod K): the
+    // populations before the step and the potential the step solved for.
+    fcd_status record_step(int sm) {
+        cudaStream_t s = stream;
+        const int j = (int)(step % K);
+        double *sl = seg + j * slot_stride;
+        const long at = step;
+        CK(cudaMemcpyAsync(sl, f[cur], 9 * ps * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(sl + 9 * ps, g[cur], 18 * ps * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        const fcd_status st = one_step(sm);
+        if (st != FCD_OK) return st;
+        mg_psi_io(mg, 0, sl + 27 * ps, nullptr, s);
+        host_kernels += 1;
+        slot_step[j] = at;
+        return FCD_OK;
+    }
+
+    // Forward steps with a checkpoint every K steps; the states of the
+    // current segment stay in the slots, so a sweep that starts in this
+    // segment need not recompute it.
     fcd_status do_step(long n) override {
         if (n < 0) return fail(FCD_EINVAL, "negative step count");
-        while (n > 0) {
+        fcd_status st = alloc_slots();
+        if (st != FCD_OK) return st;
+        for (long i = 0; i < n; i++) {
             if (step % K == 0 && (size_t)(step / K) == ckpt.size()) {
-                const fcd_status st = push_checkpoint();
+                st = push_checkpoint();
                 if (st != FCD_OK) return st;
             }
-            const long m = std::min(n, (long)(K - step % K));
-            const fcd_status st = Engine<double>::do_step(m);
+            st = record_step(i == n - 1 ? 1 : 0);
             if (st != FCD_OK) return st;
-            n -= m;
         }
+        CK(cudaGetLastError());
         return FCD_OK;
     }
 
@@ -1339,11 +1377,9 @@ struct AdjointEngine : Engine<double> {
             if (!mga) return FCD_ENOMEM;
             mg_set_rhs<double>(mga, rhs);
         }
-        if (!seg && N > 0) {
-            seg = dalloc((size_t)K * slot_stride * sizeof(double));
-            if (!seg)
-                return fail(FCD_ENOMEM, "no room for %d recomputed states (%.2f GB); use a smaller "
-                            "checkpoint interval", K, K * slot_stride * 8.0 / 1e9);
+        if (N > 0) {
+            const fcd_status sa = alloc_slots();
+            if (sa != FCD_OK) return sa;
         }
         if (!fin) {
             fin = dalloc(ck_doubles * sizeof(double));
@@ -1375,20 +1411,21 @@ struct AdjointEngine : Engine<double> {
         st = save(fin);
         if (st != FCD_OK) return st;
         int ca = 0;
+        long recomputed = 0;
         const long nseg = (N + K - 1) / K;
         for (long q = nseg - 1; q >= 0; q--) {
             const long n0 = q * K, n1 = std::min(N, n0 + K);
             const int len = (int)(n1 - n0);
-            st = restore(ckpt[q], n0);
-            if (st != FCD_OK) return st;
-            for (int j = 0; j < len; j++) {
-                double *sl = seg + j * slot_stride;
-                CK(cudaMemcpyAsync(sl, f[cur], 9 * ps * sizeof(double), cudaMemcpyDeviceToDevice, s));
-                CK(cudaMemcpyAsync(sl + 9 * ps, g[cur], 18 * ps * sizeof(double), cudaMemcpyDeviceToDevice, s));
-                st = Engine<double>::do_step(1);
+            bool have = true;  // the segment's states already in the slots?
+            for (int j = 0; j < len && have; j++) have = slot_step[j] == n0 + j;
+            if (!have) {
+                st = restore(ckpt[q], n0);
                 if (st != FCD_OK) return st;
-                mg_psi_io(mg, 0, sl + 27 * ps, nullptr, s);  // the potential that step used
-                host_kernels += 1;
+                for (int j = 0; j < len; j++) {
+                    st = record_step(0);
+                    if (st != FCD_OK) return st;
+                }
+                recomputed += len;
             }
             launch_set_slot(d_slot, len - 1, s);
             host_kernels += 1;
@@ -1420,6 +1457,7 @@ struct AdjointEngine : Engine<double> {
         o->T_o = h_adj->T_o;
         o->overlap = h_adj->overlap;
         o->J = wT * h_adj->T_o + wO * h_adj->overlap;
+        o->recomputed_steps = recomputed;
         for (int c = 0; c < NT; c++) {
             double gsum = 0.0;
             for (int q = 0; q < NPB; q++) gsum += pbar[q] * dp[q]->d[c];
@@ -1440,6 +1478,7 @@ struct AdjointEngine : Engine<double> {
         }
         if (magnetic()) {
             CK(cudaMemcpy(h_ctl, ctla, sizeof(MgCtl), cudaMemcpyDeviceToHost));
+            o->solve_cycles = h_ctl->total_cycles + h_ctl->twogrid_cycles + h_ctl->smooth_cycles;
             o->capped_solves = h_ctl->nonconv_count - nonconv0;
             if (o->capped_solves > 0)
                 return fail(FCD_ENOCONV, "%ld adjoint potential solves stopped at the cycle cap",

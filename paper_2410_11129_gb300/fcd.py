@@ -73,7 +73,8 @@ class fcd_tangent_obs(C.Structure):
 class fcd_adjoint_out(C.Structure):
     _fields_ = [
         ("step", C.c_long), ("T_o", C.c_double), ("overlap", C.c_double), ("J", C.c_double),
-        ("grad", C.c_double * 4), ("capped_solves", C.c_long),
+        ("grad", C.c_double * 4), ("capped_solves", C.c_long), ("recomputed_steps", C.c_long),
+        ("solve_cycles", C.c_longlong),
     ]
 
     def as_dict(self):

@@ -49,6 +49,8 @@ def adjoint_gradient(cfg, steps, checkpoint):
     t0 = time.perf_counter()
     ch = fcd.Adjoint(cfg, checkpoint)
     ch.step(steps)
+    torch.cuda.synchronize()
+    tf = time.perf_counter()
     aT = ch.gradient(1.0, 0.0, allow=(fcd.FCD_ENOCONV,))
     torch.cuda.synchronize()
     t1 = time.perf_counter()
@@ -57,7 +59,10 @@ def adjoint_gradient(cfg, steps, checkpoint):
     t2 = time.perf_counter()
     ch.close()
     return ({"dT_o": aT["grad"], "doverlap": aO["grad"], "T_o": aT["T_o"],
-             "capped_solves": aT["capped_solves"] + aO["capped_solves"]},
+             "capped_solves": aT["capped_solves"] + aO["capped_solves"],
+             "recomputed_steps": [aT["recomputed_steps"], aO["recomputed_steps"]],
+             "solve_cycles": [aT["solve_cycles"], aO["solve_cycles"]],
+             "seconds_forward": tf - t0, "seconds_sweeps": [t1 - tf, t2 - t1]},
             t1 - t0, t2 - t0)
 
 

@@ -82,6 +82,11 @@ def test_adjoint_matches_tangent(fcd):
         err = max(abs(x - y) for x, y in zip(a["grad"], ref))
         assert err <= 1e-9 * scale, (name, a["grad"], ref)
         assert a["capped_solves"] == 0
+    # the forward pass kept the last segment (steps 24-29); the first sweep
+    # recomputes the other three, the second finds the slots reused and
+    # recomputes all four
+    assert aT["recomputed_steps"] == 24 and aO["recomputed_steps"] == 30
+    assert aT["solve_cycles"] > 0
     assert abs(aT["T_o"] - t["T_o"]) <= 1e-13
     assert abs(aO["overlap"] - t["overlap"]) <= 1e-10 * max(1.0, t["overlap"])
     assert aT["J"] == aT["T_o"] and aO["J"] == aO["overlap"]
