@@ -1160,6 +1160,7 @@ struct AdjointEngine : Engine<double> {
     std::vector<long> slot_step;    // the step whose state slot j holds (-1: none)
     double *ab[2] = {nullptr, nullptr};  // adjoint states (27 planes each)
     double *sb = nullptr, *pb = nullptr, *rhs = nullptr, *lamA = nullptr, *lamB = nullptr;
+    double *lamS = nullptr, *lamP = nullptr;  // the last two adjoint potentials (extrapolation)
     double *pacc = nullptr, *hacc = nullptr;
     int nblk_c = 0, nblk_k = 0;
     MgCtl *ctla = nullptr;
@@ -1197,6 +1198,8 @@ struct AdjointEngine : Engine<double> {
         rhs = dalloc(ps * sizeof(double));
         lamA = dalloc(ps * sizeof(double));
         lamB = dalloc(ps * sizeof(double));
+        lamS = dalloc(ps * sizeof(double));
+        lamP = dalloc(ps * sizeof(double));
         pacc = dalloc((size_t)nblk_c * NPB * sizeof(double));
         hacc = dalloc((size_t)nblk_k * 2 * sizeof(double));
         ctla = reinterpret_cast<MgCtl *>(dalloc(sizeof(MgCtl)));
@@ -1205,7 +1208,8 @@ struct AdjointEngine : Engine<double> {
         seed_scr = dalloc(adj_seed_scratch_bytes(prm.nx));
         adj_out = reinterpret_cast<AdjOut *>(dalloc(sizeof(AdjOut)));
         for (void *q : {(void *)ab[0], (void *)ab[1], (void *)sb, (void *)pb, (void *)rhs, (void *)lamA,
-                        (void *)lamB, (void *)pacc, (void *)hacc, (void *)ctla, (void *)rmax,
+                        (void *)lamB, (void *)lamS, (void *)lamP, (void *)pacc, (void *)hacc,
+                        (void *)ctla, (void *)rmax,
                         (void *)d_slot, seed_scr, (void *)adj_out})
             if (!q) return fail(FCD_ENOMEM, "device allocation failed");
         // padding columns stay zero in every adjoint plane
@@ -1316,10 +1320,13 @@ struct AdjointEngine : Engine<double> {
         launch_adj_collide(A, s);
         launch_adj_gather(P, sb, phi1, phi2, pb, rhs, rmax, s);
         if (magnetic()) {
+            // initial guess 2 lam(n+1) - lam(n+2), as the plain solve extrapolates psi'
+            mg_psi_io(mga, 2, lamS, lamP, s);
             mg_reset_scaled(ctla, rmax, prm.mag_tol, prm.mag_max_iter, s);
             mg_presmooth<double>(mga, P.H0c, P.H0s, s);
             const fcd_status st = capture ? capture_mg_loop(s, mga) : host_mg_loop(s, mga, ctla);
             if (st != FCD_OK) return st;
+            mg_psi_io(mga, 0, lamS, nullptr, s);
         }
         AdjKArgs B;
         B.P = P;
@@ -1341,7 +1348,7 @@ struct AdjointEngine : Engine<double> {
         return FCD_OK;
     }
     // kernels of one adjoint step outside the multigrid cycles
-    long adj_step_kernels() const { return 6 + (magnetic() ? 2 : 0); }
+    long adj_step_kernels() const { return 6 + (magnetic() ? 4 : 0); }
 
     fcd_status adj_step(int c) {
         cudaStream_t s = stream;
@@ -1406,6 +1413,8 @@ struct AdjointEngine : Engine<double> {
         CK(cudaMemsetAsync(hacc, 0, (size_t)nblk_k * 2 * sizeof(double), s));
         CK(cudaMemsetAsync(lamA, 0, ps * sizeof(double), s));
         CK(cudaMemsetAsync(lamB, 0, ps * sizeof(double), s));
+        CK(cudaMemsetAsync(lamS, 0, ps * sizeof(double), s));
+        CK(cudaMemsetAsync(lamP, 0, ps * sizeof(double), s));
         CK(cudaMemsetAsync(ctla, 0, sizeof(MgCtl), s));
         int nonconv0 = 0;
         st = save(fin);

@@ -3,6 +3,7 @@ against central differences of the plain FP64 method, on the same GPU.
 
   python -m paper_2410_11129_gb300.gradient --steps 20000
   python -m paper_2410_11129_gb300.gradient --steps 500 --h 1e-4 --checkpoint 500
+  python -m paper_2410_11129_gb300.gradient --steps 20 --checkpoint 20 --only adjoint
 
 The tangent context advances the state and its derivatives along
 (Bo_m, Ca, alpha, nu_r) together; the adjoint context runs the plain step with
@@ -89,8 +90,12 @@ def difference_gradient(cfg, steps, h_rel):
     return {"dT_o": dT, "doverlap": dO}, time.perf_counter() - t0
 
 
-def compare(cfg, steps, h_rel=1e-4, checkpoint=500):
+def compare(cfg, steps, h_rel=1e-4, checkpoint=500, only=None):
     cfg = dict(cfg, precision="fp64")
+    if only == "adjoint":  # the adjoint alone (profiling runs)
+        adj, t_adj1, t_adj2 = adjoint_gradient(cfg, steps, checkpoint)
+        return {"steps": steps, "adjoint": dict(adj, checkpoint=checkpoint,
+                                                seconds_one_functional=t_adj1, seconds_both=t_adj2)}
     o, t_tan, stats = tangent_gradient(cfg, steps)
     adj, t_adj1, t_adj2 = adjoint_gradient(cfg, steps, checkpoint)
     fd, t_fd = difference_gradient(cfg, steps, h_rel)
@@ -119,8 +124,11 @@ def main(argv=None):
     ap.add_argument("--h", type=float, default=1e-4, help="relative step of the differences")
     ap.add_argument("--checkpoint", type=int, default=W.C5.get("checkpoint", 500),
                     help="checkpoint interval of the adjoint")
+    ap.add_argument("--only", choices=["adjoint"], default=None,
+                    help="run only the adjoint (forward pass and two sweeps)")
     args = ap.parse_args(argv)
-    print(json.dumps(compare(W.C5, args.steps, args.h, args.checkpoint), indent=1), flush=True)
+    print(json.dumps(compare(W.C5, args.steps, args.h, args.checkpoint, args.only), indent=1),
+          flush=True)
     return 0
 
 
