@@ -85,6 +85,7 @@ struct Phys {
 // walls at y = 0 and y = ny0 (cell faces) and period nx0 along x.
 template <typename T>
 struct Level {
+    using value_type = T;
     int nx, ny, pitch;
     T *e, *b, *k;             // correction (level 0: psi'), right-hand side, 1 + chi
     T *r;                     // scratch (level 0: second psi' buffer)

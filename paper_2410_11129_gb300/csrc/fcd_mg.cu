@@ -9,7 +9,12 @@
 // -L psi0 = 6 H0 sum_a w_a k_0a (e_a . e_alpha) is formed on the fly from k.
 // Coarser levels merge cells in pairs (the last three when a count is odd),
 // giving tensor grids of any size, and carry a 5-point finite-volume operator
-// with arithmetic face permeabilities. Cycles are V(0, 2) on level 0 and V(2, 2)
+// with arithmetic face permeabilities. The coarse levels run in FP32 for both
+// storage types (mixed-precision defect correction): level 0 keeps the compute
+// type, forms the residual that is restricted and adds the interpolated
+// correction, so the coarse precision only perturbs each cycle's contraction,
+// not the converged potential; on this GPU FP64 arithmetic is 1/58 of FP32, and
+// the single-block coarse levels are bound by one SM's arithmetic. Cycles are V(0, 2) on level 0 and V(2, 2)
 // below; residuals are summed onto the coarse cells and corrections are
 // interpolated bilinearly between cell centres (zero on the walls).
 //
@@ -27,6 +32,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "fcd_internal.cuh"
@@ -49,6 +55,7 @@ constexpr double SMOOTH_RATIO = 2.5;
 constexpr int NU_SMOOTH_ONLY = 3, NU_TWOGRID = 4;
 constexpr size_t CTA_SMEM_MAX = 200 * 1024;  // shared memory of the single-block levels
 constexpr size_t CTA_CELLS = 2048;            // cells of the single-block levels
+using TC = float;                             // type of the coarse levels (>= 1)
 
 __device__ __forceinline__ double norm_of(const MgCtl *c) {
     return __longlong_as_double((long long)c->norm_bits);
@@ -148,14 +155,16 @@ __device__ __forceinline__ void prolong_tile_load(ProlongTile<T, NXT, NYT> &pt, 
     }
 }
 
-template <typename T, int NXT, int NYT>
-__device__ __forceinline__ T prolong_at(const ProlongTile<T, NXT, NYT> &pt, const Level<T> &C,
+template <typename T, typename U, int NXT, int NYT>
+__device__ __forceinline__ T prolong_at(const ProlongTile<T, NXT, NYT> &pt, const Level<U> &C,
                                         int lx, int ly) {
     const int x0 = pt.x0[lx], x1 = pt.x1[lx], y0 = pt.y0[ly], y1 = pt.y1[ly];
     const T wx = pt.wx[lx], wy = pt.wy[ly];
     T a = T(0), b = T(0);
-    if (y0 >= 0) a = (T(1) - wx) * C.e[(long long)y0 * C.pitch + x0] + wx * C.e[(long long)y0 * C.pitch + x1];
-    if (y1 >= 0) b = (T(1) - wx) * C.e[(long long)y1 * C.pitch + x0] + wx * C.e[(long long)y1 * C.pitch + x1];
+    if (y0 >= 0)
+        a = (T(1) - wx) * T(C.e[(long long)y0 * C.pitch + x0]) + wx * T(C.e[(long long)y0 * C.pitch + x1]);
+    if (y1 >= 0)
+        b = (T(1) - wx) * T(C.e[(long long)y1 * C.pitch + x0]) + wx * T(C.e[(long long)y1 * C.pitch + x1]);
     return (T(1) - wy) * a + wy * b;
 }
 
@@ -170,7 +179,7 @@ __device__ void cycle_decide(MgCtl *ctl, cudaGraphConditionalHandle hw,
 constexpr int RX = 2 * 32 + 1 + 2, RY = 2 * 8 + 1 + 2;
 
 template <typename T>
-__global__ void __launch_bounds__(256) resid0_restrict(Level<T> L0, Level<T> L1, T H0c, T H0s,
+__global__ void __launch_bounds__(256) resid0_restrict(Level<T> L0, Level<TC> L1, T H0c, T H0s,
                                                        MgCtl *ctl, cudaGraphConditionalHandle hw,
                                                        cudaGraphConditionalHandle hi, int in_graph) {
     const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
@@ -240,8 +249,8 @@ __global__ void __launch_bounds__(256) resid0_restrict(Level<T> L0, Level<T> L1,
             for (int j = ja; j < jb; j++)
                 for (int i = ia; i < ib; i++) child(i, j);
         }
-        L1.b[(long long)J * L1.pitch + I] = sum;
-        L1.k[(long long)J * L1.pitch + I] = ksum / (L1.wx[I] * L1.wy[J]);  // unit lattice cells
+        L1.b[(long long)J * L1.pitch + I] = TC(sum);
+        L1.k[(long long)J * L1.pitch + I] = TC(ksum / (T(L1.wx[I]) * T(L1.wy[J])));  // unit lattice cells
     }
     for (int o = 16; o > 0; o >>= 1) mxt = fmax(mxt, __shfl_xor_sync(0xffffffffu, mxt, o));
     const double mx = (double)mxt;
@@ -269,7 +278,7 @@ constexpr int QT = (SX / 2) * (SY / 2);  // threads of a smoothing tile
 constexpr int TILE_LOADS = ((SX + 2) * (SY + 2) + QT - 1) / QT;
 
 template <typename T>
-__global__ void __launch_bounds__(QT) smooth0(Level<T> L0, Level<T> L1, int add_coarse,
+__global__ void __launch_bounds__(QT) smooth0(Level<T> L0, Level<TC> L1, int add_coarse,
                                               int sweeps, T H0c, T H0s, MgCtl *ctl, int first) {
     const int tid = threadIdx.x;
     // first: the sweeps that open a solve (no residual known yet)
@@ -685,8 +694,9 @@ __device__ void cycle_close(MgCtl *ctl) {
 template <typename T>
 struct MgHost {
     int nl = 0, lc = 1;
-    std::vector<Level<T>> lv;
-    Level<T> *d_lv = nullptr;
+    Level<T> L0;                // the lattice level
+    std::vector<Level<TC>> lv;  // levels 1 .. nl-1 (entry 0 unused)
+    Level<TC> *d_lv = nullptr;
     MgCtl *ctl = nullptr;
     std::vector<void *> mem;
     void *(*alloc)(size_t, void *) = nullptr;
@@ -793,12 +803,12 @@ MgHost<T> *mg_create(int nx, int ny, int pitch, T *k0, T *psiA, T *psiB, MgCtl *
         size_t bytes = 0, cells = 0;
         for (int q = l; q < m->nl; q++) {
             cells += xcs[q].size() * ycs[q].size();
-            bytes += (size_t)CTA_ARRAYS * xcs[q].size() * ycs[q].size() * sizeof(T);
+            bytes += (size_t)CTA_ARRAYS * xcs[q].size() * ycs[q].size() * sizeof(TC);
         }
         if (bytes <= CTA_SMEM_MAX && cells <= CTA_CELLS) { m->lc = l; break; }
     }
     m->cta_smem = 0;
-    for (int q = m->lc; q < m->nl; q++) m->cta_smem += (size_t)CTA_ARRAYS * xcs[q].size() * ycs[q].size() * sizeof(T);
+    for (int q = m->lc; q < m->nl; q++) m->cta_smem += (size_t)CTA_ARRAYS * xcs[q].size() * ycs[q].size() * sizeof(TC);
     if (m->nl > MAX_LEVELS || m->cta_smem > CTA_SMEM_MAX) {
         snprintf(err, errlen, "multigrid: hierarchy too deep or coarse levels too large");
         mg_destroy(m);
@@ -806,72 +816,80 @@ MgHost<T> *mg_create(int nx, int ny, int pitch, T *k0, T *psiA, T *psiB, MgCtl *
     }
     // The limit is a property of the kernel, shared by every context in the
     // process: set it to the fixed budget, not to this hierarchy's need.
-    if (cudaFuncSetAttribute(coarse_cta<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(coarse_cta<TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)CTA_SMEM_MAX) != cudaSuccess) {
         snprintf(err, errlen, "multigrid: cannot reserve %zu bytes of shared memory", m->cta_smem);
         mg_destroy(m);
         return nullptr;
     }
-    for (int l = 0; l < m->nl; l++) {
-        Level<T> &L = m->lv[l];
-        std::memset(&L, 0, sizeof(L));
+    // geometry of level l in the level's own type U
+    auto geometry = [&](auto &L, int l) {
+        using U = typename std::remove_reference_t<decltype(L)>::value_type;
         L.nx = (int)xcs[l].size();
         L.ny = (int)ycs[l].size();
-        L.Lx = T(nx);
-        L.ylo = T(0);
-        L.yhi = T(ny);
-        if (l == 0) {
-            L.pitch = pitch;
-            L.k = k0;
-            L.e = psiA;
-            L.r = psiB;
-        } else {
-            L.pitch = L.nx;
-            size_t cells = (size_t)L.nx * L.ny;
-            L.e = up.put<T>(nullptr, cells * sizeof(T));
-            L.r = up.put<T>(nullptr, cells * sizeof(T));
-            L.b = up.put<T>(nullptr, cells * sizeof(T));
-            L.k = up.put<T>(nullptr, cells * sizeof(T));
-            L.cx0 = up.put<int>(cx0[l].data(), cx0[l].size() * sizeof(int));
-            L.cy0 = up.put<int>(cy0[l].data(), cy0[l].size() * sizeof(int));
-        }
-        std::vector<T> xc(L.nx), wx(L.nx), yc(L.ny), wy(L.ny);
-        for (int i = 0; i < L.nx; i++) { xc[i] = T(xcs[l][i]); wx[i] = T(fx[l][i + 1] - fx[l][i]); }
-        for (int j = 0; j < L.ny; j++) { yc[j] = T(ycs[l][j]); wy[j] = T(fy[l][j + 1] - fy[l][j]); }
-        L.xc = up.put<T>(xc.data(), xc.size() * sizeof(T));
-        L.wx = up.put<T>(wx.data(), wx.size() * sizeof(T));
-        L.yc = up.put<T>(yc.data(), yc.size() * sizeof(T));
-        L.wy = up.put<T>(wy.data(), wy.size() * sizeof(T));
+        L.Lx = U(nx);
+        L.ylo = U(0);
+        L.yhi = U(ny);
+        std::vector<U> xc(L.nx), wx(L.nx), yc(L.ny), wy(L.ny);
+        for (int i = 0; i < L.nx; i++) { xc[i] = U(xcs[l][i]); wx[i] = U(fx[l][i + 1] - fx[l][i]); }
+        for (int j = 0; j < L.ny; j++) { yc[j] = U(ycs[l][j]); wy[j] = U(fy[l][j + 1] - fy[l][j]); }
+        L.xc = up.put<U>(xc.data(), xc.size() * sizeof(U));
+        L.wx = up.put<U>(wx.data(), wx.size() * sizeof(U));
+        L.yc = up.put<U>(yc.data(), yc.size() * sizeof(U));
+        L.wy = up.put<U>(wy.data(), wy.size() * sizeof(U));
         {  // inverse centre distances (periodic in x; walls at 0 and ny in y)
-            std::vector<T> ixe(L.nx), iyn(L.ny), iys(L.ny);
+            std::vector<U> ixe(L.nx), iyn(L.ny), iys(L.ny);
             for (int i = 0; i < L.nx; i++) {
                 const double d = i + 1 == L.nx ? xcs[l][0] + nx - xcs[l][i] : xcs[l][i + 1] - xcs[l][i];
-                ixe[i] = T(1.0 / d);
+                ixe[i] = U(1.0 / d);
             }
             for (int j = 0; j < L.ny; j++) {
                 const double dn = j + 1 < L.ny ? ycs[l][j + 1] - ycs[l][j] : double(ny) - ycs[l][j];
                 const double ds = j > 0 ? ycs[l][j] - ycs[l][j - 1] : ycs[l][j];
-                iyn[j] = T(1.0 / dn);
-                iys[j] = T(1.0 / ds);
+                iyn[j] = U(1.0 / dn);
+                iys[j] = U(1.0 / ds);
             }
-            L.ixe = up.put<T>(ixe.data(), ixe.size() * sizeof(T));
-            L.iyn = up.put<T>(iyn.data(), iyn.size() * sizeof(T));
-            L.iys = up.put<T>(iys.data(), iys.size() * sizeof(T));
+            L.ixe = up.put<U>(ixe.data(), ixe.size() * sizeof(U));
+            L.iyn = up.put<U>(iyn.data(), iyn.size() * sizeof(U));
+            L.iys = up.put<U>(iys.data(), iys.size() * sizeof(U));
         }
-        if (l + 1 < m->nl) {
+        if (l + 1 < m->nl) {  // interpolation from level l + 1 onto level l
             std::vector<int> a0, a1, b0, b1;
-            std::vector<T> wa, wb;
-            interp_table<T>(xcs[l], xcs[l + 1], double(nx), 0, 0, a0, a1, wa);
-            interp_table<T>(ycs[l], ycs[l + 1], -1.0, 0.0, double(ny), b0, b1, wb);
+            std::vector<U> wa, wb;
+            interp_table<U>(xcs[l], xcs[l + 1], double(nx), 0, 0, a0, a1, wa);
+            interp_table<U>(ycs[l], ycs[l + 1], -1.0, 0.0, double(ny), b0, b1, wb);
             L.px0 = up.put<int>(a0.data(), a0.size() * sizeof(int));
             L.px1 = up.put<int>(a1.data(), a1.size() * sizeof(int));
-            L.pwx = up.put<T>(wa.data(), wa.size() * sizeof(T));
+            L.pwx = up.put<U>(wa.data(), wa.size() * sizeof(U));
             L.py0 = up.put<int>(b0.data(), b0.size() * sizeof(int));
             L.py1 = up.put<int>(b1.data(), b1.size() * sizeof(int));
-            L.pwy = up.put<T>(wb.data(), wb.size() * sizeof(T));
+            L.pwy = up.put<U>(wb.data(), wb.size() * sizeof(U));
         }
+    };
+    {
+        Level<T> &L = m->L0;
+        std::memset(&L, 0, sizeof(L));
+        geometry(L, 0);
+        L.pitch = pitch;
+        L.k = k0;
+        L.e = psiA;
+        L.r = psiB;
     }
-    m->d_lv = up.put<Level<T>>(m->lv.data(), m->lv.size() * sizeof(Level<T>));
+    for (int l = 0; l < m->nl; l++) {
+        Level<TC> &L = m->lv[l];
+        std::memset(&L, 0, sizeof(L));
+        if (l == 0) continue;  // the lattice level is m->L0
+        geometry(L, l);
+        L.pitch = L.nx;
+        const size_t cells = (size_t)L.nx * L.ny;
+        L.e = up.put<TC>(nullptr, cells * sizeof(TC));
+        L.r = up.put<TC>(nullptr, cells * sizeof(TC));
+        L.b = up.put<TC>(nullptr, cells * sizeof(TC));
+        L.k = up.put<TC>(nullptr, cells * sizeof(TC));
+        L.cx0 = up.put<int>(cx0[l].data(), cx0[l].size() * sizeof(int));
+        L.cy0 = up.put<int>(cy0[l].data(), cy0[l].size() * sizeof(int));
+    }
+    m->d_lv = up.put<Level<TC>>(m->lv.data(), m->lv.size() * sizeof(Level<TC>));
     if (!up.ok) {
         snprintf(err, errlen, "multigrid: device allocation or upload failed");
         mg_destroy(m);
@@ -893,48 +911,48 @@ template <typename T>
 void mg_cycle_head(MgHost<T> *m, T H0c, T H0s, cudaGraphConditionalHandle hw,
                    cudaGraphConditionalHandle hi, int in_graph, cudaStream_t s) {
     dim3 b(32, 8);
-    const std::vector<Level<T>> &lv = m->lv;
-    resid0_restrict<T><<<g2(lv[1].nx, lv[1].ny, b), b, 0, s>>>(lv[0], lv[1], H0c, H0s, m->ctl,
+    const std::vector<Level<TC>> &lv = m->lv;
+    resid0_restrict<T><<<g2(lv[1].nx, lv[1].ny, b), b, 0, s>>>(m->L0, lv[1], H0c, H0s, m->ctl,
                                                                hw, hi, in_graph);
 }
 
 template <typename T>
 void mg_cycle_rest(MgHost<T> *m, T H0c, T H0s, cudaStream_t s) {
     dim3 b(32, 8), bs(SX, SY);
-    const std::vector<Level<T>> &lv = m->lv;
+    const std::vector<Level<TC>> &lv = m->lv;
     for (int l = 1; l < m->lc; l++) {
-        fv_smooth<T, 0><<<g2(lv[l].nx, lv[l].ny, bs), bs, 0, s>>>(lv[l], lv[l + 1], NU_PRE, m->ctl);
-        fv_resid_restrict<T><<<g2(lv[l + 1].nx, lv[l + 1].ny, b), b, 0, s>>>(lv[l], lv[l + 1], m->ctl);
+        fv_smooth<TC, 0><<<g2(lv[l].nx, lv[l].ny, bs), bs, 0, s>>>(lv[l], lv[l + 1], NU_PRE, m->ctl);
+        fv_resid_restrict<TC><<<g2(lv[l + 1].nx, lv[l + 1].ny, b), b, 0, s>>>(lv[l], lv[l + 1], m->ctl);
     }
-    coarse_cta<T><<<1, CTA_THREADS, m->cta_smem, s>>>(m->d_lv, m->lc, m->nl, m->ctl);
+    coarse_cta<TC><<<1, CTA_THREADS, m->cta_smem, s>>>(m->d_lv, m->lc, m->nl, m->ctl);
     for (int l = m->lc - 1; l >= 1; l--)
-        fv_smooth<T, 1><<<g2(lv[l].nx, lv[l].ny, bs), bs, 0, s>>>(lv[l], lv[l + 1], NU_POST, m->ctl);
-    smooth0<T><<<g2(lv[0].nx, lv[0].ny, bs), QT, 0, s>>>(lv[0], lv[1], 1, NU_FINE, H0c, H0s, m->ctl,
+        fv_smooth<TC, 1><<<g2(lv[l].nx, lv[l].ny, bs), bs, 0, s>>>(lv[l], lv[l + 1], NU_POST, m->ctl);
+    smooth0<T><<<g2(m->L0.nx, m->L0.ny, bs), QT, 0, s>>>(m->L0, lv[1], 1, NU_FINE, H0c, H0s, m->ctl,
                                                           0);
 }
 
 template <typename T>
 void mg_cycle_smooth(MgHost<T> *m, T H0c, T H0s, cudaStream_t s) {
     dim3 bs(SX, SY);
-    const std::vector<Level<T>> &lv = m->lv;
-    smooth0<T><<<g2(lv[0].nx, lv[0].ny, bs), QT, 0, s>>>(lv[0], lv[1], 0, NU_SMOOTH_ONLY, H0c, H0s,
+    const std::vector<Level<TC>> &lv = m->lv;
+    smooth0<T><<<g2(m->L0.nx, m->L0.ny, bs), QT, 0, s>>>(m->L0, lv[1], 0, NU_SMOOTH_ONLY, H0c, H0s,
                                                           m->ctl, 0);
 }
 
 template <typename T>
 void mg_presmooth(MgHost<T> *m, T H0c, T H0s, cudaStream_t s) {
     dim3 bs(SX, SY);
-    const std::vector<Level<T>> &lv = m->lv;
-    smooth0<T><<<g2(lv[0].nx, lv[0].ny, bs), QT, 0, s>>>(lv[0], lv[1], 0, NU_SMOOTH_ONLY, H0c, H0s,
+    const std::vector<Level<TC>> &lv = m->lv;
+    smooth0<T><<<g2(m->L0.nx, m->L0.ny, bs), QT, 0, s>>>(m->L0, lv[1], 0, NU_SMOOTH_ONLY, H0c, H0s,
                                                           m->ctl, 1);
 }
 
 template <typename T>
 void mg_cycle_twogrid(MgHost<T> *m, T H0c, T H0s, cudaStream_t s) {
     dim3 bs(SX, SY);
-    const std::vector<Level<T>> &lv = m->lv;
-    fv_smooth<T, 2><<<g2(lv[1].nx, lv[1].ny, bs), bs, 0, s>>>(lv[1], lv[1], NU_TWOGRID, m->ctl);
-    smooth0<T><<<g2(lv[0].nx, lv[0].ny, bs), QT, 0, s>>>(lv[0], lv[1], 1, NU_FINE, H0c, H0s, m->ctl,
+    const std::vector<Level<TC>> &lv = m->lv;
+    fv_smooth<TC, 2><<<g2(lv[1].nx, lv[1].ny, bs), bs, 0, s>>>(lv[1], lv[1], NU_TWOGRID, m->ctl);
+    smooth0<T><<<g2(m->L0.nx, m->L0.ny, bs), QT, 0, s>>>(m->L0, lv[1], 1, NU_FINE, H0c, H0s, m->ctl,
                                                           0);
 }
 
@@ -946,7 +964,7 @@ int mg_levels(const MgHost<T> *m) { return m->nl; }
 
 // ------------------------------------------------------------ tangent solves
 template <typename T>
-void mg_set_rhs(MgHost<T> *m, const T *rhs) { m->lv[0].rhs = rhs; }
+void mg_set_rhs(MgHost<T> *m, const T *rhs) { m->L0.rhs = rhs; }
 
 // The reset the phase kernel performs at the start of a solve, with the
 // tolerance scaled by max |rhs| of the tangent right-hand side (the first
@@ -1012,7 +1030,7 @@ __global__ void __launch_bounds__(256) tangent_rhs_kernel(Level<double> L0, cons
 void mg_tangent_rhs(MgHost<double> *m, const double *dk, double H0c, double H0s, double dH0c,
                     double dH0s, double *rhs, unsigned long long *rmax_bits, cudaStream_t s) {
     dim3 b(32, 8);
-    const Level<double> &L0 = m->lv[0];
+    const Level<double> &L0 = m->L0;
     cudaMemsetAsync(rmax_bits, 0, sizeof(unsigned long long), s);
     tangent_rhs_kernel<<<g2(L0.nx, L0.ny, b), b, 0, s>>>(L0, dk, H0c, H0s, dH0c, dH0s, m->ctl, rhs,
                                                           rmax_bits);
@@ -1035,7 +1053,7 @@ __global__ void psi_io_kernel(const MgCtl *ctl, double *A, double *B, int op, do
 }
 
 void mg_psi_io(MgHost<double> *m, int op, double *plane, double *prev, cudaStream_t s) {
-    const Level<double> &L0 = m->lv[0];
+    const Level<double> &L0 = m->L0;
     const long long n = (long long)L0.pitch * L0.ny;
     psi_io_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(m->ctl, L0.e, L0.r, op, plane, prev, n);
 }
