@@ -96,6 +96,19 @@ def compare(cfg, steps, h_rel=1e-4, checkpoint=500, only=None):
         adj, t_adj1, t_adj2 = adjoint_gradient(cfg, steps, checkpoint)
         return {"steps": steps, "adjoint": dict(adj, checkpoint=checkpoint,
                                                 seconds_one_functional=t_adj1, seconds_both=t_adj2)}
+    if only == "tangent,adjoint":  # both exact forms, no difference runs
+        o, t_tan, stats = tangent_gradient(cfg, steps)
+        adj, t_adj1, t_adj2 = adjoint_gradient(cfg, steps, checkpoint)
+        out = {"steps": steps, "T_o": o["T_o"], "overlap": o["overlap"],
+               "tangent": {"dT_o": o["dT_o"], "doverlap": o["doverlap"], "seconds": t_tan,
+                           "solver": stats},
+               "adjoint": dict(adj, checkpoint=checkpoint, seconds_one_functional=t_adj1,
+                               seconds_both=t_adj2)}
+        for q in ("dT_o", "doverlap"):
+            a, c = np.array(o[q]), np.array(adj[q])
+            out["max_rel_diff_adjoint_tangent_" + q] = float(
+                np.abs(c - a).max() / max(np.abs(a).max(), 1e-300))
+        return out
     o, t_tan, stats = tangent_gradient(cfg, steps)
     adj, t_adj1, t_adj2 = adjoint_gradient(cfg, steps, checkpoint)
     fd, t_fd = difference_gradient(cfg, steps, h_rel)
@@ -124,8 +137,8 @@ def main(argv=None):
     ap.add_argument("--h", type=float, default=1e-4, help="relative step of the differences")
     ap.add_argument("--checkpoint", type=int, default=W.C5.get("checkpoint", 500),
                     help="checkpoint interval of the adjoint")
-    ap.add_argument("--only", choices=["adjoint"], default=None,
-                    help="run only the adjoint (forward pass and two sweeps)")
+    ap.add_argument("--only", choices=["adjoint", "tangent,adjoint"], default=None,
+                    help="run only the adjoint, or only the tangent and the adjoint")
     args = ap.parse_args(argv)
     print(json.dumps(compare(W.C5, args.steps, args.h, args.checkpoint, args.only), indent=1),
           flush=True)
