@@ -4,8 +4,9 @@ The reverse sweep's gradients of J = w_T T_o + w_overlap sum phi_1 phi_3 are
 checked against (1) the tangent-linear context, which differentiates the same
 discrete step forwards (agreement up to the potential-solve tolerance),
 (2) Richardson-extrapolated central differences of the FP64 CPU oracle,
-(3) central differences of the plain FP64 GPU path along random directions of
-the initial populations (the state adjoint dJ/d(f0, g0)), and (4) the exact
+(3) central differences of the plain FP64 GPU path and of the oracle along
+random directions of the initial populations (the state adjoint
+dJ/d(f0, g0)), and (4) the exact
 zero of dT_o/dalpha at alpha = 0 for a droplet on the centre line. The
 checkpoint interval must not change a bit.
 """
@@ -179,6 +180,41 @@ def test_initial_state_adjoint_against_gpu_differences(fcd):
             mag = float(np.sum(np.abs(o["df0"] * d)))
         assert mag > 0
         assert abs(fd - ad) <= 1e-6 * mag + 1e-7 * abs(ad), (which, fd, ad, mag)
+
+
+def test_initial_state_adjoint_against_oracle_differences(fcd, orc):
+    """The same directional derivatives along the initial populations, the
+    differences taken with the FP64 CPU oracle instead of the GPU path."""
+    cfg = grad_cfg()
+    wT, wO = 1.0, 2.0
+    o = adjoint_grads(fcd, cfg, STEPS, 10, initial=True, weights=((wT, wO),))[0]
+    base = orc.Sim(cfg)
+    g0 = base.g.copy()
+    p1, p2 = g0[0].sum(axis=0), g0[1].sum(axis=0)
+    p3 = 1.0 - p1 - p2
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)[:, None, None]
+    rng = np.random.default_rng(7)
+
+    def J(df, dg):
+        sim = orc.Sim(cfg)
+        sim.f += df
+        sim.g += dg
+        sim.step(STEPS)
+        phi = sim.phi()
+        return wT * sim.observe()["T_o"] + wO * overlap_of(phi[0], phi[1])
+
+    h = 1e-6
+    r = rng.standard_normal((2,) + p1.shape)
+    dg = np.stack([w * (p1 * p3 * r[0]), w * (p2 * p3 * r[1])])
+    df = rng.standard_normal(base.f.shape)
+    zf, zg = np.zeros_like(df), np.zeros_like(dg)
+    for name, a, b, bar in (("g", zf, dg, o["dg0"]), ("f", df, zg, o["df0"])):
+        fd = (J(h * a, h * b) - J(-h * a, -h * b)) / (2 * h)
+        d = b if name == "g" else a
+        ad = float(np.sum(bar * d))
+        mag = float(np.sum(np.abs(bar * d)))
+        assert mag > 0
+        assert abs(fd - ad) <= 1e-6 * mag + 1e-7 * abs(ad), (name, fd, ad, mag)
 
 
 def test_adjoint_alpha_derivative_vanishes_by_symmetry(fcd):
