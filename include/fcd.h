@@ -242,8 +242,8 @@ fcd_status fcd_tangent_observables(fcd_ctx *ctx, fcd_tangent_obs *out);
  * the final state, J = w_T T_o + w_overlap sum_nodes phi_1 phi_3 (T_o of
  * Eq. 42; the overlap as in fcd_tangent_obs), with respect to the four
  * parameters of the tangent form (same direction order) and to the initial
- * populations. An adjoint context is an FP64 periodic channel (open_x = 0;
- * precision is ignored) that keeps a checkpoint of its state every
+ * populations. An adjoint context is an FP64 channel, periodic or open
+ * (precision is ignored), that keeps a checkpoint of its state every
  * checkpoint_interval steps from step 0 (device memory: 30 planes of nx*ny
  * doubles per checkpoint). fcd_adjoint_gradient runs the reverse sweep from the
  * current step N back to step 0, one segment between checkpoints at a time,

@@ -1,5 +1,5 @@
 // fcd_adjoint.cu -- kernels of the discrete adjoint (reverse-mode) step of the
-// coupled method (arXiv 2410.11129), FP64, periodic channel.
+// coupled method (arXiv 2410.11129), FP64, periodic or open channel.
 //
 // One forward step maps the state (f_n, g_n) to (f_{n+1}, g_{n+1}) through
 //   phi_i = sum_a g^i_a (Eq. 32), k = 1/sum_i phi^_i/(1 + chi_i) (Eq. 8),
@@ -82,6 +82,9 @@ __global__ void __launch_bounds__(256) adj_phase_kernel(Phys<double> P, const do
     k[n] = 1.0 / (P.ik[0] * cl01(p1) + P.ik[1] * cl01(p2) + P.ik[2] * cl01(1.0 - p1 - p2));
 }
 
+// OPEN: the channel's x ends are an inlet and an outlet: phi-like halo columns
+// mirrored there, populations leaving through them dropped (zero adjoint).
+template <bool OPEN>
 __global__ void __launch_bounds__(TX *ATY) adj_collide_kernel(AdjArgs A) {
     __shared__ double s1[ATY + 2][TX + 2], s2[ATY + 2][TX + 2], sr[ATY + 2][TX + 2], sp[ATY + 2][TX + 2];
     const Phys<double> &P = A.P;
@@ -100,7 +103,9 @@ __global__ void __launch_bounds__(TX *ATY) adj_collide_kernel(AdjArgs A) {
         const int gy = y0 - 1 + ly;
         const bool ghost = gy < 0 || gy >= ny;
         const long long m = (long long)mrow(gy, ny) * pitch + gx;
-        const double p1 = A.phi1[m], p2 = A.phi2[m];
+        const int xr = x0 - 1 + lx, gm = xr < 0 ? 0 : (xr >= nx ? nx - 1 : xr);
+        const long long mp = OPEN ? (long long)mrow(gy, ny) * pitch + gm : m;
+        const double p1 = A.phi1[mp], p2 = A.phi2[mp];
         s1[ly][lx] = p1;
         s2[ly][lx] = p2;
         sr[ly][lx] = P.rho[0] * cl01(p1) + P.rho[1] * cl01(p2) + P.rho[2] * cl01(1.0 - p1 - p2);
@@ -141,11 +146,13 @@ __global__ void __launch_bounds__(TX *ATY) adj_collide_kernel(AdjArgs A) {
 #pragma unroll
         for (int a = 0; a < 9; a++) {
             const bool walled = (cy(a) > 0 && y == ny - 1) || (cy(a) < 0 && y == 0);
+            // dropped through an open end (a wall reflection takes precedence, as in the push)
+            const bool leaves = OPEN && !walled && ((cx(a) > 0 && x == nx - 1) || (cx(a) < 0 && x == 0));
             const long long d = walled ? n : n + cy(a) * pitch + (cx(a) > 0 ? dxp : (cx(a) < 0 ? dxm : 0));
             const int q = walled ? opp(a) : a;
-            fb[a] = A.ab_src[q * ps + d];
-            gb[a] = A.ab_src[(9 + q) * ps + d];
-            gb[9 + a] = A.ab_src[(18 + q) * ps + d];
+            fb[a] = leaves ? 0.0 : A.ab_src[q * ps + d];
+            gb[a] = leaves ? 0.0 : A.ab_src[(9 + q) * ps + d];
+            gb[9 + a] = leaves ? 0.0 : A.ab_src[(18 + q) * ps + d];
         }
         NodeBar B;
         node_reverse(F, P, fb, gb, B, pacc);
@@ -162,8 +169,12 @@ __global__ void __launch_bounds__(TX *ATY) adj_collide_kernel(AdjArgs A) {
 }
 
 // Transposed stencils: the node at m receives, from every node s whose stencil
-// read it (s = m - e_b; at a wall row also the nodes whose ghost mirrors onto m),
-// the adjoint of that read.
+// read it, the adjoint of that read. Rows: s = m - e_b, and at a wall row also
+// the node whose ghost row mirrors onto m (negated for psi'). Columns: periodic,
+// or in the open channel (OPEN) s = m - e_b inside and, at an end column, the
+// node whose ghost column mirrors onto m (phi-like fields only; psi' stays
+// periodic in x).
+template <bool OPEN>
 __global__ void __launch_bounds__(256) adj_gather_kernel(Phys<double> P, const double *sb, const double *phi1,
                                                          const double *phi2, double *pb, double *rhs,
                                                          unsigned long long *rmax) {
@@ -173,19 +184,35 @@ __global__ void __launch_bounds__(256) adj_gather_kernel(Phys<double> P, const d
     double ar = 0.0;
     if (x < nx && y < ny) {
         double b1 = 0.0, b2 = 0.0, br = 0.0, bp = 0.0;
-        auto add = [&](long long s, int b, double sign) {
+        auto add_phi = [&](long long s, int b) {
             const double wx = wgx(b), wy = wgy(b), wl = wlp(b), wc = b == 0 ? 1.0 : 0.0;
             b1 += sb[0 * ps + s] * wc + sb[1 * ps + s] * wx + sb[2 * ps + s] * wy + sb[3 * ps + s] * wl;
             b2 += sb[4 * ps + s] * wc + sb[5 * ps + s] * wx + sb[6 * ps + s] * wy + sb[7 * ps + s] * wl;
             br += sb[8 * ps + s] * wc + sb[9 * ps + s] * wx + sb[10 * ps + s] * wy;
-            bp += sign * (sb[11 * ps + s] * wx + sb[12 * ps + s] * wy);
+        };
+        auto add_psi = [&](long long s, int b, double sign) {
+            bp += sign * (sb[11 * ps + s] * wgx(b) + sb[12 * ps + s] * wgy(b));
         };
 #pragma unroll
         for (int b = 0; b < 9; b++) {
-            const int sx = wrapx(x - cx(b), nx), sy = y - cy(b);
-            if (sy >= 0 && sy < ny) add((long long)sy * pitch + sx, b, 1.0);
-            if ((y == 0 && cy(b) < 0) || (y == ny - 1 && cy(b) > 0))  // ghost of a wall row
-                add((long long)y * pitch + sx, b, -1.0);
+            // source rows: the plain neighbour, and the mirror of a ghost row
+            int ys[2], nys = 0;
+            bool ghost_row[2];
+            if (y - cy(b) >= 0 && y - cy(b) < ny) { ys[nys] = y - cy(b); ghost_row[nys++] = false; }
+            if ((y == 0 && cy(b) < 0) || (y == ny - 1 && cy(b) > 0)) { ys[nys] = y; ghost_row[nys++] = true; }
+            // source columns of the phi-like fields
+            int xs[2], nxs = 0;
+            if (OPEN) {
+                if (x - cx(b) >= 0 && x - cx(b) < nx) xs[nxs++] = x - cx(b);
+                if ((x == 0 && cx(b) < 0) || (x == nx - 1 && cx(b) > 0)) xs[nxs++] = x;
+            } else {
+                xs[nxs++] = wrapx(x - cx(b), nx);
+            }
+            const int xp = wrapx(x - cx(b), nx);  // psi' is periodic in x
+            for (int j = 0; j < nys; j++) {
+                for (int i = 0; i < nxs; i++) add_phi((long long)ys[j] * pitch + xs[i], b);
+                add_psi((long long)ys[j] * pitch + xp, b, ghost_row[j] ? -1.0 : 1.0);
+            }
         }
         const long long m = (long long)y * pitch + x;
         const double p1 = phi1[m], p2 = phi2[m], d3 = dcl01(1.0 - p1 - p2);
@@ -198,6 +225,96 @@ __global__ void __launch_bounds__(256) adj_gather_kernel(Phys<double> P, const d
     for (int o = 16; o > 0; o >>= 1) ar = fmax(ar, __shfl_xor_sync(0xffffffffu, ar, o));
     if (((threadIdx.y * blockDim.x + threadIdx.x) & 31) == 0 && ar > 0.0)
         atomicMax(rmax, (unsigned long long)__double_as_longlong(ar));
+}
+
+// Open channel: transpose of the boundary kernel that follows the collision
+// (the Eq. 37 Zou-He inlet and the convective outlet, linear in the populations
+// with constant coefficients, so no forward values are needed). In place on the
+// adjoint after the step, one thread per row: the adjoints of the values the
+// boundary overwrote go to the values they were computed from and become 0;
+// the outlet's dependence on the state before the step goes to `keep`
+// (27 values per row), added to the adjoint before the step by adj_open_add.
+__global__ void adj_open_bc_kernel(Phys<double> P, double *ab, double *keep, double u_avg) {
+    const int y = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nx = P.nx, ny = P.ny;
+    if (y >= ny) return;
+    const long long ps = P.ps, n = (long long)y * P.pitch, o = n + nx - 1, bn = o - 1;
+    auto FA = [&](int a, long long m) -> double & { return ab[a * ps + m]; };
+    auto GA = [&](int q, int a, long long m) -> double & { return ab[(9 + q * 9 + a) * ps + m]; };
+    // inlet: reverse of the assignments (last first)
+    double f1 = FA(1, n);
+    FA(1, n) = 0.0;
+    if (y == 0 || y == ny - 1) {  // f1 = u + f3 - f5 + f6 + f7 - f8
+        FA(3, n) += f1;
+        FA(5, n) -= f1;
+        FA(6, n) += f1;
+        FA(7, n) += f1;
+        FA(8, n) -= f1;
+    } else {  // f1 = f3 + 6 w1 u
+        FA(3, n) += f1;
+    }
+    if (y == 0) {  // f8 = f2 - f4 + f5 + f6 - f7
+        const double f8 = FA(8, n);
+        FA(8, n) = 0.0;
+        FA(2, n) += f8;
+        FA(4, n) -= f8;
+        FA(5, n) += f8;
+        FA(6, n) += f8;
+        FA(7, n) -= f8;
+    } else if (y == ny - 1) {  // f5 = f4 - f2 - f6 + f7 + f8
+        const double f5 = FA(5, n);
+        FA(5, n) = 0.0;
+        FA(4, n) += f5;
+        FA(2, n) -= f5;
+        FA(6, n) -= f5;
+        FA(7, n) += f5;
+        FA(8, n) += f5;
+    } else {  // f5 = f7 + c - (f2 - f4)/2, f8 = f6 + c + (f2 - f4)/2
+        const double f5 = FA(5, n), f8 = FA(8, n);
+        FA(5, n) = 0.0;
+        FA(8, n) = 0.0;
+        FA(7, n) += f5;
+        FA(6, n) += f8;
+        FA(2, n) += 0.5 * (f8 - f5);
+        FA(4, n) += 0.5 * (f5 - f8);
+    }
+    for (int q = 0; q < 2; q++) {  // inflowing phase-field populations are constants
+        GA(q, 1, n) = 0.0;
+        if (y != 0) GA(q, 5, n) = 0.0;
+        if (y != ny - 1) GA(q, 8, n) = 0.0;
+    }
+    // outlet: chi_a = ((f_a - w_a p*)(t) + U (f_a - w_a p*)_{nx-2}(t+1)) / (1 + U)
+    double *kf = keep + (long long)y * 27, *kg = kf + 9;
+    for (int a = 0; a < 27; a++) kf[a] = 0.0;
+    const double iu = 1.0 / (1.0 + u_avg);
+    const int in3[3] = {3, 6, 7};
+    for (int k = 0; k < 3; k++) {
+        const int a = in3[k];
+        if ((a == 6 && y == 0) || (a == 7 && y == ny - 1)) continue;  // from the wall
+        const double s = FA(a, o) * iu;
+        FA(a, o) = 0.0;
+        kf[a] += s;
+        FA(a, bn) += u_avg * s;
+        const double w = wgt<double>(a);
+        for (int c = 0; c < 9; c++) {
+            kf[c] -= w * s;
+            FA(c, bn) -= u_avg * w * s;
+        }
+        for (int q = 0; q < 2; q++) {
+            const double sg = GA(q, a, o) * iu;
+            GA(q, a, o) = 0.0;
+            kg[q * 9 + a] += sg;
+            GA(q, a, bn) += u_avg * sg;
+        }
+    }
+}
+
+// the outlet column's share of the adjoint before the step (see adj_open_bc)
+__global__ void adj_open_add_kernel(Phys<double> P, const double *keep, double *ab) {
+    const int y = blockIdx.x * blockDim.x + threadIdx.x;
+    if (y >= P.ny) return;
+    const long long o = (long long)y * P.pitch + P.nx - 1;
+    for (int q = 0; q < 27; q++) ab[q * P.ps + o] += keep[(long long)y * 27 + q];
 }
 
 // kb, the adjoint of H0 (cos, sin) through the right-hand side, and the
@@ -447,16 +564,26 @@ void launch_adj_phase(const Phys<double> &P, const double *seg, const int *slot,
     adj_phase_kernel<<<grid2(P.nx, P.ny, b), b, 0, s>>>(P, seg, slot, stride, phi1, phi2, k);
 }
 
-void launch_adj_collide(const AdjArgs &a, cudaStream_t s) {
+void launch_adj_collide(const AdjArgs &a, int open_x, cudaStream_t s) {
     dim3 b(TX, ATY);
-    adj_collide_kernel<<<grid2(a.P.nx, a.P.ny, b), b, 0, s>>>(a);
+    if (open_x) adj_collide_kernel<true><<<grid2(a.P.nx, a.P.ny, b), b, 0, s>>>(a);
+    else adj_collide_kernel<false><<<grid2(a.P.nx, a.P.ny, b), b, 0, s>>>(a);
 }
 
 void launch_adj_gather(const Phys<double> &P, const double *sb, const double *phi1, const double *phi2,
-                       double *pb, double *rhs, unsigned long long *rmax, cudaStream_t s) {
+                       double *pb, double *rhs, unsigned long long *rmax, int open_x, cudaStream_t s) {
     dim3 b(32, 8);
     cudaMemsetAsync(rmax, 0, sizeof(unsigned long long), s);
-    adj_gather_kernel<<<grid2(P.nx, P.ny, b), b, 0, s>>>(P, sb, phi1, phi2, pb, rhs, rmax);
+    if (open_x) adj_gather_kernel<true><<<grid2(P.nx, P.ny, b), b, 0, s>>>(P, sb, phi1, phi2, pb, rhs, rmax);
+    else adj_gather_kernel<false><<<grid2(P.nx, P.ny, b), b, 0, s>>>(P, sb, phi1, phi2, pb, rhs, rmax);
+}
+
+void launch_adj_open_bc(const Phys<double> &P, double *ab, double *keep, double u_avg, cudaStream_t s) {
+    adj_open_bc_kernel<<<(P.ny + 63) / 64, 64, 0, s>>>(P, ab, keep, u_avg);
+}
+
+void launch_adj_open_add(const Phys<double> &P, const double *keep, double *ab, cudaStream_t s) {
+    adj_open_add_kernel<<<(P.ny + 63) / 64, 64, 0, s>>>(P, keep, ab);
 }
 
 void launch_adj_kbar(const AdjKArgs &a, cudaStream_t s) {

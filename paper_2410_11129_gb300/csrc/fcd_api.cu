@@ -1162,6 +1162,7 @@ struct AdjointEngine : Engine<double> {
     double *sb = nullptr, *pb = nullptr, *rhs = nullptr, *lamA = nullptr, *lamB = nullptr;
     double *lamS = nullptr, *lamP = nullptr;  // the last two adjoint potentials (extrapolation)
     double *pacc = nullptr, *hacc = nullptr;
+    double *keep = nullptr;  // open channel: the outlet's share of the adjoint before a step
     int nblk_c = 0, nblk_k = 0;
     MgCtl *ctla = nullptr;
     MgHost<double> *mga = nullptr;
@@ -1207,6 +1208,10 @@ struct AdjointEngine : Engine<double> {
         d_slot = reinterpret_cast<int *>(dalloc(sizeof(int)));
         seed_scr = dalloc(adj_seed_scratch_bytes(prm.nx));
         adj_out = reinterpret_cast<AdjOut *>(dalloc(sizeof(AdjOut)));
+        if (prm.open_x) {
+            keep = dalloc((size_t)prm.ny * 27 * sizeof(double));
+            if (!keep) return fail(FCD_ENOMEM, "device allocation failed");
+        }
         for (void *q : {(void *)ab[0], (void *)ab[1], (void *)sb, (void *)pb, (void *)rhs, (void *)lamA,
                         (void *)lamB, (void *)lamS, (void *)lamP, (void *)pacc, (void *)hacc,
                         (void *)ctla, (void *)rmax,
@@ -1305,6 +1310,8 @@ struct AdjointEngine : Engine<double> {
 
     // One adjoint step on s: reads the slot *d_slot and ab[c], writes ab[c ^ 1].
     fcd_status enqueue_adj_step(int c, cudaStream_t s, bool capture) {
+        // open channel: the boundary kernel ran last in the step, so its transpose runs first
+        if (prm.open_x) launch_adj_open_bc(P, ab[c], keep, D.u_avg, s);
         launch_adj_phase(P, seg, d_slot, slot_stride, phi1, phi2, k, s);
         AdjArgs A;
         A.P = P;
@@ -1317,8 +1324,9 @@ struct AdjointEngine : Engine<double> {
         A.ab_dst = ab[c ^ 1];
         A.sb = sb;
         A.pacc = pacc;
-        launch_adj_collide(A, s);
-        launch_adj_gather(P, sb, phi1, phi2, pb, rhs, rmax, s);
+        launch_adj_collide(A, prm.open_x, s);
+        if (prm.open_x) launch_adj_open_add(P, keep, ab[c ^ 1], s);
+        launch_adj_gather(P, sb, phi1, phi2, pb, rhs, rmax, prm.open_x, s);
         if (magnetic()) {
             // initial guess 2 lam(n+1) - lam(n+2), as the plain solve extrapolates psi'
             mg_psi_io(mga, 2, lamS, lamP, s);
@@ -1348,7 +1356,7 @@ struct AdjointEngine : Engine<double> {
         return FCD_OK;
     }
     // kernels of one adjoint step outside the multigrid cycles
-    long adj_step_kernels() const { return 6 + (magnetic() ? 4 : 0); }
+    long adj_step_kernels() const { return 6 + (magnetic() ? 4 : 0) + (prm.open_x ? 2 : 0); }
 
     fcd_status adj_step(int c) {
         cudaStream_t s = stream;
@@ -1609,7 +1617,6 @@ fcd_status fcd_create_adjoint(const fcd_params *params, int checkpoint_interval,
     std::memset(&d, 0, sizeof d);
     const char *why = derive(&p, &d);
     if (!why && checkpoint_interval < 1) why = "checkpoint_interval must be >= 1";
-    if (!why && p.open_x != 0) why = "the adjoint form covers the periodic channel (open_x = 0)";
     if (!why && p.ferro_phase != 0 && !(p.Bo_m > 0))
         why = "the Bo_m direction needs Bo_m > 0 (H0 ~ sqrt(Bo_m))";
     if (why) {

@@ -289,9 +289,14 @@ int adj_kbar_blocks(int nx, int ny);
 size_t adj_seed_scratch_bytes(int nx);
 void launch_adj_phase(const Phys<double> &P, const double *seg, const int *slot, long long stride,
                       double *phi1, double *phi2, double *k, cudaStream_t s);
-void launch_adj_collide(const AdjArgs &a, cudaStream_t s);
+void launch_adj_collide(const AdjArgs &a, int open_x, cudaStream_t s);
 void launch_adj_gather(const Phys<double> &P, const double *sb, const double *phi1, const double *phi2,
-                       double *pb, double *rhs, unsigned long long *rmax, cudaStream_t s);
+                       double *pb, double *rhs, unsigned long long *rmax, int open_x, cudaStream_t s);
+// open channel: transpose of the boundary kernel on the adjoint after the step
+// (keep: ny x 27 doubles, the outlet's dependence on the state before it), and
+// the addition of keep into the adjoint before the step
+void launch_adj_open_bc(const Phys<double> &P, double *ab, double *keep, double u_avg, cudaStream_t s);
+void launch_adj_open_add(const Phys<double> &P, const double *keep, double *ab, cudaStream_t s);
 void launch_adj_kbar(const AdjKArgs &a, cudaStream_t s);
 void launch_set_slot(int *slot, int v, cudaStream_t s);
 void launch_dec_slot(int *slot, cudaStream_t s);

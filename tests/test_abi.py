@@ -65,7 +65,6 @@ def test_null_arguments():
 
 
 @pytest.mark.parametrize("bad,K", [
-    (dict(open_x=1), 10),   # the adjoint form covers the periodic channel
     ({}, 0),                # checkpoint interval
     (dict(Bo_m=0.0), 10),   # H0 ~ sqrt(Bo_m): no derivative at 0
     (dict(nx=7), 10),
