@@ -6,7 +6,8 @@ discrete step forwards (agreement up to the potential-solve tolerance),
 (2) Richardson-extrapolated central differences of the FP64 CPU oracle,
 (3) central differences of the plain FP64 GPU path and of the oracle along
 random directions of the initial populations (the state adjoint
-dJ/d(f0, g0)), and (4) the exact
+dJ/d(f0, g0)), (4) the FP64 CPU adjoint of oracle/torch_step.py, element by
+element, and (5) the exact
 zero of dT_o/dalpha at alpha = 0 for a droplet on the centre line. The
 checkpoint interval must not change a bit.
 """
@@ -218,6 +219,26 @@ def test_initial_state_adjoint_against_oracle_differences(fcd, orc):
         mag = float(np.sum(np.abs(bar * d)))
         assert mag > 0
         assert abs(fd - ad) <= 1e-6 * mag + 1e-7 * abs(ad), (name, fd, ad, mag)
+
+
+@pytest.mark.parametrize("open_x", [0, 1])
+def test_adjoint_against_cpu_adjoint(fcd, orc, open_x):
+    """The GPU sweep against the FP64 CPU adjoint (oracle/torch_step.py: the
+    oracle's step in PyTorch float64 with an exact potential solve, reverse
+    mode by torch.autograd): the four parameter derivatives, and the fields
+    dJ/d(f0, g0) element by element."""
+    from oracle import torch_step as TS
+    cfg = grad_cfg(open_x=open_x)
+    o = adjoint_grads(fcd, cfg, STEPS, 8, initial=True, weights=((1.0, 2.0),))[0]
+    sim = orc.Sim(cfg)
+    r = TS.gradients(cfg, STEPS, sim.f.copy(), sim.g.copy(), 1.0, 2.0)
+    assert abs(o["J"] - r["J"]) <= 1e-10 * max(1.0, abs(r["J"]))
+    scale = max(abs(v) for v in r["grad"])
+    assert max(abs(a - b) for a, b in zip(o["grad"], r["grad"])) <= 1e-8 * scale, (o["grad"], r["grad"])
+    for key in ("df0", "dg0"):
+        ref, got = r[key], o[key]
+        assert got.shape == ref.shape
+        assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max(), key
 
 
 def test_adjoint_alpha_derivative_vanishes_by_symmetry(fcd):
