@@ -1424,7 +1424,6 @@ struct AdjointEngine : Engine<double> {
         CK(cudaMemsetAsync(lamS, 0, ps * sizeof(double), s));
         CK(cudaMemsetAsync(lamP, 0, ps * sizeof(double), s));
         CK(cudaMemsetAsync(ctla, 0, sizeof(MgCtl), s));
-        int nonconv0 = 0;
         st = save(fin);
         if (st != FCD_OK) return st;
         int ca = 0;
@@ -1496,7 +1495,7 @@ struct AdjointEngine : Engine<double> {
         if (magnetic()) {
             CK(cudaMemcpy(h_ctl, ctla, sizeof(MgCtl), cudaMemcpyDeviceToHost));
             o->solve_cycles = h_ctl->total_cycles + h_ctl->twogrid_cycles + h_ctl->smooth_cycles;
-            o->capped_solves = h_ctl->nonconv_count - nonconv0;
+            o->capped_solves = h_ctl->nonconv_count;  // the control block is cleared per sweep
             if (o->capped_solves > 0)
                 return fail(FCD_ENOCONV, "%ld adjoint potential solves stopped at the cycle cap",
                             o->capped_solves);
