@@ -422,5 +422,5 @@ def gradients(cfg, steps, f0, g0, w_T=1.0, w_overlap=0.0):
     (To, ov), _ = run(cfg, theta, steps, f, g)
     J = w_T * To + w_overlap * ov
     J.backward()
-    return {"T_o": float(To), "overlap": float(ov), "J": float(J),
+    return {"T_o": float(To.detach()), "overlap": float(ov.detach()), "J": float(J.detach()),
             "grad": theta.grad.tolist(), "df0": f.grad.numpy(), "dg0": g.grad.numpy()}
