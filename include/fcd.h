@@ -276,6 +276,14 @@ fcd_status fcd_create_adjoint(const fcd_params *params, int checkpoint_interval,
  * FCD_ENOCONV (with out filled) when an adjoint solve stopped at the cap. */
 fcd_status fcd_adjoint_gradient(fcd_ctx *ctx, double w_T, double w_overlap, fcd_adjoint_out *out,
                                 double *df0, double *dg0);
+/* The same sweep for any functional J of the final state, given by its
+ * derivative: seed_f, seed_g = dJ/d(f, g at step N) in the layout of
+ * fcd_get_populations (9*nx*ny and 18*nx*ny doubles, host or device memory;
+ * one of them may be NULL, meaning zero; both NULL is FCD_EINVAL). out->grad
+ * and df0, dg0 as above; out->T_o and out->overlap are the state's values and
+ * out->J is 0 (J is the caller's). Synchronous; the context stays at step N. */
+fcd_status fcd_adjoint_gradient_state(fcd_ctx *ctx, const double *seed_f, const double *seed_g,
+                                      fcd_adjoint_out *out, double *df0, double *dg0);
 
 /* Observables of a caller's population buffer with no device allocation.
  * The paper has no counterpart: this serves callers that cannot allocate

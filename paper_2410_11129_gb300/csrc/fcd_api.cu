@@ -1383,8 +1383,13 @@ struct AdjointEngine : Engine<double> {
         return FCD_OK;
     }
 
-    fcd_status gradient(double wT, double wO, fcd_adjoint_out *o, double *df0, double *dg0) {
+    // seed_f, seed_g (state seed, exchange layout, host or device; either may be
+    // null): dJ/d(f, g at the final step) given by the caller instead of the
+    // built-in J = wT T_o + wO overlap (then wT = wO = 0).
+    fcd_status gradient(double wT, double wO, fcd_adjoint_out *o, double *df0, double *dg0,
+                        const double *seed_f = nullptr, const double *seed_g = nullptr) {
         const long N = step;
+        const bool state_seed = seed_f || seed_g;
         cudaStream_t s = stream;
         if (!mga && magnetic()) {
             mga = mg_create<double>(prm.nx, prm.ny, pitch, k, lamA, lamB, ctla, alloc, release, user, err,
@@ -1409,7 +1414,25 @@ struct AdjointEngine : Engine<double> {
         launch_adj_seed(P, phi1, phi2, obs_out, wT, wO, seed_scr, pb, ab[0], adj_out, s);
         host_kernels += 3;
         CK(cudaMemcpyAsync(h_adj, adj_out, sizeof(AdjOut), cudaMemcpyDeviceToHost, s));
-        if (wT == 0.0 && wO == 0.0 && !df0 && !dg0) {  // J = 0: values only, zero gradient
+        if (state_seed) {  // the caller's dJ/d(f_N, g_N) replaces the seed's planes
+            const size_t Nn = (size_t)prm.nx * prm.ny;
+            double *stg = staging(27 * Nn);
+            if (!stg) return fail(FCD_ENOMEM, "staging allocation failed");
+            cudaError_t e = cudaSuccess;
+            if (seed_f) e = cudaMemcpyAsync(stg, seed_f, 9 * Nn * sizeof(double), cudaMemcpyDefault, s);
+            if (e == cudaSuccess && seed_g)
+                e = cudaMemcpyAsync(stg + 9 * Nn, seed_g, 18 * Nn * sizeof(double), cudaMemcpyDefault, s);
+            if (e == cudaSuccess) {
+                launch_import<double>(MODE_FP64, P, seed_f ? stg : nullptr, seed_g ? stg + 9 * Nn : nullptr,
+                                      ab[0], ab[0] + 9 * ps, s);
+                host_kernels += 1;
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            cudaFree(stg);
+            if (e != cudaSuccess) return fail(FCD_ECUDA, "adjoint seed import: %s", cudaGetErrorString(e));
+        }
+        if (wT == 0.0 && wO == 0.0 && !df0 && !dg0 && !state_seed) {  // J = 0: values only, zero gradient
             CK(cudaStreamSynchronize(s));
             std::memset(o, 0, sizeof *o);
             o->step = N;
@@ -1472,7 +1495,7 @@ struct AdjointEngine : Engine<double> {
         o->step = N;
         o->T_o = h_adj->T_o;
         o->overlap = h_adj->overlap;
-        o->J = wT * h_adj->T_o + wO * h_adj->overlap;
+        o->J = state_seed ? 0.0 : wT * h_adj->T_o + wO * h_adj->overlap;
         o->recomputed_steps = recomputed;
         for (int c = 0; c < NT; c++) {
             double gsum = 0.0;
@@ -1646,6 +1669,15 @@ fcd_status fcd_adjoint_gradient(fcd_ctx *c, double w_T, double w_overlap, fcd_ad
     auto *e = dynamic_cast<AdjointEngine *>(c);
     if (!e) return c->fail(FCD_EINVAL, "not an adjoint context");
     return e->gradient(w_T, w_overlap, o, df0, dg0);
+}
+
+fcd_status fcd_adjoint_gradient_state(fcd_ctx *c, const double *seed_f, const double *seed_g,
+                                      fcd_adjoint_out *o, double *df0, double *dg0) {
+    if (!c || !o) return FCD_EINVAL;
+    auto *e = dynamic_cast<AdjointEngine *>(c);
+    if (!e) return c->fail(FCD_EINVAL, "not an adjoint context");
+    if (!seed_f && !seed_g) return c->fail(FCD_EINVAL, "no seed given");
+    return e->gradient(0.0, 0.0, o, df0, dg0, seed_f, seed_g);
 }
 
 fcd_status fcd_set_stream(fcd_ctx *c, void *stream) {

@@ -122,6 +122,8 @@ _SIGS = {
     "fcd_create_adjoint": (C.c_int, [C.POINTER(fcd_params), C.c_int, C.POINTER(C.c_void_p)]),
     "fcd_adjoint_gradient": (C.c_int, [C.c_void_p, C.c_double, C.c_double,
                                        C.POINTER(fcd_adjoint_out), C.c_void_p, C.c_void_p]),
+    "fcd_adjoint_gradient_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p,
+                                             C.POINTER(fcd_adjoint_out), C.c_void_p, C.c_void_p]),
     "fcd_destroy": (None, [C.c_void_p]),
 }
 
@@ -357,6 +359,24 @@ class Adjoint(Channel):
             out["df0"], out["dg0"] = df0, dg0
         return out
 
+    def gradient_state(self, seed_f=None, seed_g=None, initial=False, allow=()):
+        """Reverse sweep for any functional J of the final state, given as
+        seed_f = dJ/df (9, ny, nx) and/or seed_g = dJ/dg (2, 9, ny, nx)."""
+        o = fcd_adjoint_out()
+        df0 = dg0 = None
+        if initial:
+            df0 = np.empty((9, self.ny, self.nx))
+            dg0 = np.empty((2, 9, self.ny, self.nx))
+        keep = [None if a is None else np.ascontiguousarray(a, np.float64) for a in (seed_f, seed_g)]
+        ptr = lambda a: None if a is None else C.c_void_p(a.ctypes.data)
+        st = load().fcd_adjoint_gradient_state(self.h, ptr(keep[0]), ptr(keep[1]), C.byref(o),
+                                               ptr(df0), ptr(dg0))
+        self.check(st, allow=allow)
+        out = o.as_dict()
+        if initial:
+            out["df0"], out["dg0"] = df0, dg0
+        return out
+
     def values(self):
         """(T_o, overlap) of the current state (no sweep: J = 0 has zero gradient)."""
         o = self.gradient(0.0, 0.0, allow=(FCD_ENOCONV,))
@@ -443,6 +463,55 @@ def _droplet_adjoint_function():
             return g, None, None, None
 
     return DropletObservablesAdjoint
+
+
+def _final_state_function():
+    import torch
+
+    class FinalState(torch.autograd.Function):
+        """The populations (f, g) after `steps` coupled steps, as a function of
+        theta = (Bo_m, Ca, alpha, nu_r): forward runs the plain FP64 step with
+        checkpoints, backward runs one discrete-adjoint sweep seeded with the
+        incoming gradients of f and g."""
+
+        @staticmethod
+        def forward(ctx, theta, cfg, steps, checkpoint):
+            ch = Adjoint(with_parameters(cfg, theta.detach().cpu().tolist()), checkpoint)
+            try:
+                if steps:
+                    ch.step(int(steps))
+                f, g, _ = ch.populations()
+            except Exception:
+                ch.close()
+                raise
+            ctx.ch = ch
+            return torch.from_numpy(f), torch.from_numpy(g)
+
+        @staticmethod
+        def backward(ctx, grad_f, grad_g):
+            ch = ctx.ch
+            as_np = lambda x: None if x is None else x.detach().cpu().numpy()
+            try:
+                o = ch.gradient_state(as_np(grad_f), as_np(grad_g))
+            finally:
+                ch.close()
+                ctx.ch = None
+            return torch.tensor(o["grad"], dtype=torch.float64), None, None, None
+
+    return FinalState
+
+
+_FINAL_STATE_FN = None
+
+
+def final_state(theta, cfg, steps, checkpoint=500):
+    """Differentiable final populations (f (9, ny, nx), g (2, 9, ny, nx), FP64,
+    on the host): any torch loss of them back-propagates to theta through one
+    reverse sweep of the discrete adjoint."""
+    global _FINAL_STATE_FN
+    if _FINAL_STATE_FN is None:
+        _FINAL_STATE_FN = _final_state_function()
+    return _FINAL_STATE_FN.apply(theta, cfg, steps, checkpoint)
 
 
 _DROPLET_FN = None

@@ -241,6 +241,49 @@ def test_adjoint_against_cpu_adjoint(fcd, orc, open_x):
         assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max(), key
 
 
+def test_state_seed_reproduces_the_overlap_functional(fcd):
+    """Seeding the sweep with dJ/dg_N of the overlap (phi_3 - phi_1 on the
+    core planes, -phi_1 on the shell planes) gives the built-in gradient."""
+    cfg = grad_cfg()
+    ch = fcd.Adjoint(cfg, 8)
+    ch.step(STEPS)
+    o1 = ch.gradient(0.0, 1.0, initial=True)
+    f, g, _ = ch.populations()
+    p1, p2 = g[0].sum(axis=0), g[1].sum(axis=0)
+    sg = np.stack([np.repeat((1.0 - 2.0 * p1 - p2)[None], 9, axis=0),
+                   np.repeat((-p1)[None], 9, axis=0)])
+    o2 = ch.gradient_state(None, sg, initial=True)
+    ch.close()
+    scale = max(abs(v) for v in o1["grad"])
+    assert max(abs(a - b) for a, b in zip(o1["grad"], o2["grad"])) <= 1e-12 * scale
+    assert np.abs(o1["dg0"] - o2["dg0"]).max() <= 1e-12 * np.abs(o1["dg0"]).max()
+    assert o2["J"] == 0.0 and o2["overlap"] == o1["overlap"]
+
+
+def test_final_state_autograd_against_cpu_adjoint(fcd, orc):
+    """A torch loss of the final populations back-propagated through
+    fcd.final_state (one GPU sweep) against the same loss through the FP64
+    CPU adjoint."""
+    import torch
+    from oracle import torch_step as TS
+    cfg = grad_cfg()
+    rng = np.random.default_rng(5)
+    S = torch.from_numpy(rng.standard_normal((9, 20, 48)))
+    R = torch.from_numpy(rng.standard_normal((2, 9, 20, 48)))
+    th = torch.tensor(fcd.parameters_of(cfg), dtype=torch.float64, requires_grad=True)
+    f, g = fcd.final_state(th, cfg, STEPS, checkpoint=8)
+    loss = (f * S).sum() + (g * R).sum()
+    loss.backward()
+    sim = orc.Sim(cfg)
+    theta = torch.tensor(TS.parameters_of(cfg), dtype=torch.float64, requires_grad=True)
+    _, (fc, gc) = TS.run(cfg, theta, STEPS, sim.f.copy(), sim.g.copy())
+    lc = (fc * S.reshape(9, -1)).sum() + (gc * R.reshape(2, 9, -1)).sum()
+    lc.backward()
+    assert abs(loss.item() - lc.item()) <= 1e-10 * max(1.0, abs(lc.item()))
+    ref, got = theta.grad.numpy(), th.grad.numpy()
+    assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max(), (got, ref)
+
+
 def test_adjoint_alpha_derivative_vanishes_by_symmetry(fcd):
     cfg = grad_cfg(alpha_deg=0.0, yc=9.5)
     aT, aO = adjoint_grads(fcd, cfg, STEPS, 10)
