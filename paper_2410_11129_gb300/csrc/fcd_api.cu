@@ -1386,6 +1386,37 @@ struct AdjointEngine : Engine<double> {
     // seed_f, seed_g (state seed, exchange layout, host or device; either may be
     // null): dJ/d(f, g at the final step) given by the caller instead of the
     // built-in J = wT T_o + wO overlap (then wT = wO = 0).
+    // The segments last first: recompute a segment's states into the slots
+    // unless the slots already hold them, then its adjoint steps backwards.
+    // ca: the adjoint buffer that holds the current adjoint (updated).
+    fcd_status sweep(long N, int &ca, long &recomputed) {
+        cudaStream_t s = stream;
+        const long nseg = (N + K - 1) / K;
+        for (long q = nseg - 1; q >= 0; q--) {
+            const long n0 = q * K, n1 = std::min(N, n0 + K);
+            const int len = (int)(n1 - n0);
+            bool have = true;  // the segment's states already in the slots?
+            for (int j = 0; j < len && have; j++) have = slot_step[j] == n0 + j;
+            if (!have) {
+                fcd_status st = restore(ckpt[q], n0);
+                if (st != FCD_OK) return st;
+                for (int j = 0; j < len; j++) {
+                    st = record_step(0);
+                    if (st != FCD_OK) return st;
+                }
+                recomputed += len;
+            }
+            launch_set_slot(d_slot, len - 1, s);
+            host_kernels += 1;
+            for (int j = len - 1; j >= 0; j--) {
+                const fcd_status st = adj_step(ca);
+                if (st != FCD_OK) return st;
+                ca ^= 1;
+            }
+        }
+        return FCD_OK;
+    }
+
     fcd_status gradient(double wT, double wO, fcd_adjoint_out *o, double *df0, double *dg0,
                         const double *seed_f = nullptr, const double *seed_g = nullptr) {
         const long N = step;
@@ -1451,31 +1482,14 @@ struct AdjointEngine : Engine<double> {
         if (st != FCD_OK) return st;
         int ca = 0;
         long recomputed = 0;
-        const long nseg = (N + K - 1) / K;
-        for (long q = nseg - 1; q >= 0; q--) {
-            const long n0 = q * K, n1 = std::min(N, n0 + K);
-            const int len = (int)(n1 - n0);
-            bool have = true;  // the segment's states already in the slots?
-            for (int j = 0; j < len && have; j++) have = slot_step[j] == n0 + j;
-            if (!have) {
-                st = restore(ckpt[q], n0);
-                if (st != FCD_OK) return st;
-                for (int j = 0; j < len; j++) {
-                    st = record_step(0);
-                    if (st != FCD_OK) return st;
-                }
-                recomputed += len;
-            }
-            launch_set_slot(d_slot, len - 1, s);
-            host_kernels += 1;
-            for (int j = len - 1; j >= 0; j--) {
-                st = adj_step(ca);
-                if (st != FCD_OK) return st;
-                ca ^= 1;
-            }
+        st = sweep(N, ca, recomputed);
+        // back to the final state whether or not the sweep completed
+        const fcd_status rs = restore(fin, N);
+        if (st != FCD_OK) {
+            if (rs == FCD_OK) cudaStreamSynchronize(s);
+            return st;
         }
-        st = restore(fin, N);
-        if (st != FCD_OK) return st;
+        if (rs != FCD_OK) return rs;
         // constants' adjoints, summed block by block in a fixed order
         std::vector<double> hp((size_t)nblk_c * NPB), hh((size_t)nblk_k * 2);
         CK(cudaMemcpyAsync(hp.data(), pacc, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
