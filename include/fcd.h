@@ -251,10 +251,13 @@ fcd_status fcd_tangent_observables(fcd_ctx *ctx, fcd_tangent_obs *out);
  * into checkpoint_interval slots (28 planes each, allocated by the first step;
  * FCD_ENOMEM if they do not fit), then the adjoint of every step runs backwards
  * through them. fcd_step keeps the states of the current segment in the slots,
- * so the last segment is not recomputed (none is when checkpoint_interval >= N). Each adjoint step reverses the collision and streaming of every
- * node and the potential solve: L(k) lam = psib (L of Eq. 6 is symmetric) with
- * the multigrid of the plain solve to mag_tol relative to max |psib|, then the
- * permeability and field-strength adjoints of b(k, H0) - L(k) psi'. Bo_m must
+ * so the last segment is not recomputed (none is when checkpoint_interval >= N).
+ * Each adjoint step reverses the open channel's boundary populations (inlet of
+ * Eq. 37, convective outlet) when open_x = 1, the collision and streaming of
+ * every node, and the potential solve: L(k) lam = psib (L of Eq. 6 is
+ * symmetric) with the multigrid of the plain solve to mag_tol relative to
+ * max |psib|, then the permeability and field-strength adjoints of
+ * b(k, H0) - L(k) psi'. Bo_m must
  * be > 0 when a phase is ferrofluid. The handle accepts fcd_step (forward, with
  * checkpoints), fcd_observables, fcd_get_field, fcd_solve_magnetic,
  * fcd_kernel_launches, fcd_solver_stats, fcd_last_error and fcd_destroy; state
@@ -272,8 +275,10 @@ typedef struct {
 fcd_status fcd_create_adjoint(const fcd_params *params, int checkpoint_interval, fcd_ctx **out);
 /* Reverse sweep (synchronous). df0, dg0: NULL, or host or device buffers of
  * 9*nx*ny and 18*nx*ny doubles (layout of fcd_get_populations) that receive
- * dJ / d(f, g at step 0). The context is back at step N afterwards. Returns
- * FCD_ENOCONV (with out filled) when an adjoint solve stopped at the cap. */
+ * dJ / d(f, g at step 0). The context is back at step N afterwards, also when
+ * the sweep fails. Returns FCD_ENOCONV (with out filled) when an adjoint solve
+ * stopped at the cap. With w_T = w_overlap = 0 and no df0, dg0 the call only
+ * fills the values (J = 0 has a zero gradient; no sweep runs). */
 fcd_status fcd_adjoint_gradient(fcd_ctx *ctx, double w_T, double w_overlap, fcd_adjoint_out *out,
                                 double *df0, double *dg0);
 /* The same sweep for any functional J of the final state, given by its
