@@ -117,3 +117,27 @@ def test_cpu_adjoint_initial_state_against_oracle_differences(orc):
         mag = float(np.sum(np.abs(bar * d)))
         assert mag > 0
         assert abs(fd - ad) <= 1e-6 * mag + 1e-7 * abs(ad), (fd, ad, mag)
+
+
+def test_cpu_adjoint_alpha_derivative_vanishes_by_symmetry(orc):
+    """alpha = 0 with the droplet on the centre line: T_o(alpha) = T_o(-alpha)."""
+    from oracle import torch_step as TS
+    cfg = grad_cfg(alpha_deg=0.0, yc=9.5)
+    sim = orc.Sim(cfg)
+    r = TS.gradients(cfg, STEPS, sim.f.copy(), sim.g.copy(), 1.0, 0.0)
+    other = max(abs(v) for v in r["grad"])
+    assert other > 0
+    assert abs(r["grad"][2]) <= 1e-12 * other
+
+
+def test_torch_step_total_spreading_matches_the_oracle(orc):
+    """eta > 0 with a negative spreading coefficient (sigma_13 = 3 sigma_12)."""
+    from oracle import torch_step as TS
+    cfg = grad_cfg(s13_over_s12=3.0, eta=0.02)
+    sim = orc.Sim(cfg)
+    f0, g0 = sim.f.copy(), sim.g.copy()
+    theta = torch.tensor(TS.parameters_of(cfg), dtype=torch.float64)
+    (To, _), (f, g) = TS.run(cfg, theta, STEPS, f0, g0)
+    sim.step(STEPS)
+    assert np.abs(g.numpy().reshape(sim.g.shape) - sim.g).max() <= 1e-13
+    assert abs(float(To) - sim.observe()["T_o"]) <= 1e-12
