@@ -363,7 +363,9 @@ struct Engine : fcd_ctx {
             launch_open_bc<T>(mode, P, f[c], g[c], f[c ^ 1], g[c ^ 1], prm.u_max, D.u_avg, s);
     }
     int post_kernels() const { return prm.open_x ? 2 : 1; }
-    int pre_kernels() const { return 1; }
+    // the phase kernel, and in FP64 contexts with a field the solve's
+    // coefficient kernel (the multigrid counts its own cycles)
+    int pre_kernels() const { return 1 + (magnetic() && sizeof(T) == 8 ? 1 : 0); }
 
     // One solve with host checks between cycles (hierarchy m with control
     // block c; default: the context's own).
@@ -554,7 +556,7 @@ struct Engine : fcd_ctx {
         }
         launch_phase<T>(mode, P, g[cur], phi1, phi2, k,
                         PhaseCtl{ctl, 1, tol * D.H0, max_iter, nullptr, 0, nullptr, nullptr, nullptr}, s);
-        host_kernels += 1;  // the opening sweeps are counted with the sweep cycles
+        host_kernels += pre_kernels();  // the opening sweeps are counted with the sweep cycles
         CK(cudaGetLastError());
         fcd_status st = host_mg_loop(s);
         if (st != FCD_OK) return st;
@@ -999,7 +1001,9 @@ struct TangentEngine : Engine<double> {
     // kernels of one step outside the multigrid cycles (those are counted on
     // the device): two phase kernels, per direction the right-hand side, two
     // copies and the reset, the potential copy and the collision
-    long step_kernels() const { return 2 + (magnetic() ? 4 * NT : 0) + 2 + (prm.open_x ? 1 : 0); }
+    long step_kernels() const {
+        return 2 + (magnetic() ? 5 * NT + 1 : 0) + 2 + (prm.open_x ? 1 : 0);  // + coefficient kernels
+    }
 
     long launches() const override {
         long n = Engine<double>::launches();
@@ -1019,7 +1023,7 @@ struct TangentEngine : Engine<double> {
         const fcd_status st = Engine<double>::solve(tol, max_iter, iters, resid);
         if (st != FCD_OK && st != FCD_ENOCONV) return st;
         launch_tangent_phase(P, static_cast<const double *>(g[cur]), phi1, phi2, k, stream);
-        host_kernels += 1 + (magnetic() ? 4 * NT : 0);
+        host_kernels += 1 + (magnetic() ? 5 * NT : 0);  // + one coefficient kernel per solve
         const fcd_status st2 = tangent_solves(false, tol, max_iter, stream, false);
         return st2 != FCD_OK ? st2 : st;
     }
@@ -1356,7 +1360,7 @@ struct AdjointEngine : Engine<double> {
         return FCD_OK;
     }
     // kernels of one adjoint step outside the multigrid cycles
-    long adj_step_kernels() const { return 6 + (magnetic() ? 4 : 0) + (prm.open_x ? 2 : 0); }
+    long adj_step_kernels() const { return 6 + (magnetic() ? 5 : 0) + (prm.open_x ? 2 : 0); }
 
     fcd_status adj_step(int c) {
         cudaStream_t s = stream;

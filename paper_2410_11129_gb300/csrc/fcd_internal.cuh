@@ -98,6 +98,9 @@ struct Level {
     const int *px0, *px1, *py0, *py1;  // -1 in py* stands for the wall (value 0)
     const T *pwx, *pwy;
     const T *rhs;  // level 0: explicit right-hand side (nullptr: -L psi0 formed from k)
+    // level 0 of FP64 hierarchies: the 9-point coefficients of every node, formed
+    // once per solve (planes c_1..c_8, diagonal, its reciprocal, -L psi0)
+    T *coef;
 };
 
 // Device-side control block of one potential solve.

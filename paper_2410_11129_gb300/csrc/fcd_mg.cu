@@ -123,6 +123,44 @@ __device__ __forceinline__ T off9(const Node9<T> &n, PF pat, int y, int ny) {
     return s;
 }
 
+// FP64 hierarchies keep the lattice level's node coefficients in COEF planes,
+// formed once per solve by coef0_kernel (k does not change within a solve):
+// the FP64 arithmetic of node9 and its division cost more than the loads on
+// this GPU (FP64 is 1/58 of FP32). FP32 hierarchies form them on the fly.
+constexpr int COEF = 11;  // c_1..c_8, diag, 1/diag, b
+template <typename T>
+__host__ __device__ constexpr bool keeps_coef() { return sizeof(T) == 8; }
+
+template <typename T>
+__device__ __forceinline__ void coef_load(const Level<T> &L0, long long n, Node9<T> &nd, T &inv) {
+    const long long ps = (long long)L0.pitch * L0.ny;
+#pragma unroll
+    for (int a = 1; a < 9; a++) nd.c[a] = L0.coef[(a - 1) * ps + n];
+    nd.diag = L0.coef[8 * ps + n];
+    inv = L0.coef[9 * ps + n];
+    nd.b = L0.coef[10 * ps + n];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) coef0_kernel(Level<T> L0, T H0c, T H0s) {
+    const int nx = L0.nx, ny = L0.ny, pitch = L0.pitch;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= nx || y >= ny) return;
+    auto kat = [&](int dx, int dy) {
+        int xx = x + dx;
+        xx = xx < 0 ? xx + nx : (xx >= nx ? xx - nx : xx);
+        const int yy = y + dy < 0 ? 0 : (y + dy >= ny ? ny - 1 : y + dy);  // mirrored ghost rows
+        return L0.k[(long long)yy * pitch + xx];
+    };
+    const Node9<T> nd = node9<T>(kat, y, ny, H0c, H0s);
+    const long long ps = (long long)pitch * ny, n = (long long)y * pitch + x;
+#pragma unroll
+    for (int a = 1; a < 9; a++) L0.coef[(a - 1) * ps + n] = nd.c[a];
+    L0.coef[8 * ps + n] = nd.diag;
+    L0.coef[9 * ps + n] = T(1) / nd.diag;
+    L0.coef[10 * ps + n] = nd.b;
+}
+
 // Interpolation weights of a tile's columns and rows, staged in shared memory.
 template <typename T, int NXT, int NYT>
 struct ProlongTile {
@@ -231,7 +269,14 @@ __global__ void __launch_bounds__(256) resid0_restrict(Level<T> L0, Level<TC> L1
             const int lx = i - fx0 + 1, ly = j - fy0 + 1;
             auto kat = [&](int dx, int dy) { return sk[ly + dy][lx + dx]; };
             auto pat = [&](int dx, int dy) { return sp[ly + dy][lx + dx]; };
-            const Node9<T> nd = node9<T>(kat, j, ny, H0c, H0s);
+            Node9<T> nd;
+            if constexpr (keeps_coef<T>()) {
+                T inv;
+                coef_load(L0, (long long)j * pitch + i, nd, inv);
+                (void)kat;
+            } else {
+                nd = node9<T>(kat, j, ny, H0c, H0s);
+            }
             const T bb = L0.rhs ? L0.rhs[(long long)j * pitch + i] : nd.b;
             const T r = bb - (off9<T>(nd, pat, j, ny) - nd.diag * sp[ly][lx]);
             sum += r;
@@ -337,10 +382,14 @@ __global__ void __launch_bounds__(QT) smooth0(Level<T> L0, Level<TC> L1, int add
         own[c] = x < nx && y < ny;
         inv_diag[c] = T(0);
         if (own[c]) {
-            auto kat = [&](int dx, int dy) { return sk[ly + dy][lx + dx]; };
-            nd[c] = node9<T>(kat, y, ny, H0c, H0s);
+            if constexpr (keeps_coef<T>()) {
+                coef_load(L0, (long long)y * pitch + x, nd[c], inv_diag[c]);
+            } else {
+                auto kat = [&](int dx, int dy) { return sk[ly + dy][lx + dx]; };
+                nd[c] = node9<T>(kat, y, ny, H0c, H0s);
+                inv_diag[c] = T(1) / nd[c].diag;
+            }
             if (L0.rhs) nd[c].b = L0.rhs[(long long)y * pitch + x];
-            inv_diag[c] = T(1) / nd[c].diag;
         }
     }
     for (int s = 0; s < sweeps; s++) {
@@ -874,6 +923,7 @@ MgHost<T> *mg_create(int nx, int ny, int pitch, T *k0, T *psiA, T *psiB, MgCtl *
         L.k = k0;
         L.e = psiA;
         L.r = psiB;
+        if (keeps_coef<T>()) L.coef = up.put<T>(nullptr, (size_t)COEF * pitch * ny * sizeof(T));
     }
     for (int l = 0; l < m->nl; l++) {
         Level<TC> &L = m->lv[l];
@@ -943,6 +993,10 @@ template <typename T>
 void mg_presmooth(MgHost<T> *m, T H0c, T H0s, cudaStream_t s) {
     dim3 bs(SX, SY);
     const std::vector<Level<TC>> &lv = m->lv;
+    if (keeps_coef<T>()) {  // the solve's node coefficients, before its first sweep
+        dim3 b(32, 8);
+        coef0_kernel<T><<<g2(m->L0.nx, m->L0.ny, b), b, 0, s>>>(m->L0, H0c, H0s);
+    }
     smooth0<T><<<g2(m->L0.nx, m->L0.ny, bs), QT, 0, s>>>(m->L0, lv[1], 0, NU_SMOOTH_ONLY, H0c, H0s,
                                                           m->ctl, 1);
 }
