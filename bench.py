@@ -205,20 +205,27 @@ def measure_large(steps, warmup, peak, peak_kind):
         ch.step(1)
     torch.cuda.synchronize()
     a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    coll = 0.0
+    stage = {"phase": 0.0, "solve": 0.0, "collide": 0.0}
     total = 0.0
+    st0 = ch.solver_stats()
     for _ in range(steps):
         a.record(stream)
         ch.step(1)
         z.record(stream)
-        coll += ch.last_step_profile()["collide"]
+        prof = ch.last_step_profile()
+        for k in stage:
+            stage[k] += prof[k]
         torch.cuda.synchronize()
         total += a.elapsed_time(z)
+    st1 = ch.solver_stats()
     ch.close()
+    coll = stage["collide"]
     bpn = COLLIDE_BYTES_PER_NODE_F32
     achieved = bpn * N / (coll / steps * 1e-3) / 1e9
     return {"workload": cfg["name"], "steps": steps, "value": N * steps / (total * 1e-3) / 1e6,
             "unit": UNIT, "ms_per_step": total / steps,
+            "stage_ms_per_step": {k: v / steps for k, v in stage.items()},
+            "solver_per_step": {k: (st1[k] - st0[k]) / steps for k in st0},
             "roofline": {"bound": "hbm", "kernel": "collide_kernel (fp32)", "achieved": achieved,
                          "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": achieved / peak,

@@ -161,6 +161,13 @@ fcd_status fcd_set_state(fcd_ctx *ctx, const void *src, size_t bytes);
  * (15 doubles). */
 fcd_status fcd_get_derived(const fcd_ctx *ctx, double *out15);
 
+/* The same 15 derived quantities straight from a parameter set, without a
+ * context: the lattice mapping of Sec. 2.5 (Eq. 40: sigma23 from Ca; Eq. 41:
+ * mu0 H0^2 from Bo_m, core or shell branch; Eqs. 14, 26-27, 30). Host code
+ * only: no CUDA call, no allocation. FCD_EINVAL (reason in fcd_last_error(NULL))
+ * for a parameter set that fcd_create would reject. */
+fcd_status fcd_derive_params(const fcd_params *params, double *out15);
+
 /* Number of kernels launched by this context since create (for accounting;
  * synchronises to read the device-side cycle count). */
 long fcd_kernel_launches(const fcd_ctx *ctx);

@@ -1738,12 +1738,29 @@ fcd_status fcd_set_state(fcd_ctx *c, const void *src, size_t bytes) {
     return c ? c->set_state(src, bytes) : FCD_EINVAL;
 }
 
-fcd_status fcd_get_derived(const fcd_ctx *c, double *o) {
-    if (!c || !o) return FCD_EINVAL;
-    const Derived &d = c->D;
+static void derived_out(const Derived &d, double *o) {
     const double v[15] = {d.u_avg, d.s12, d.s13, d.s23, d.gam[0], d.gam[1], d.gam[2], d.gamT,
                           d.tau[0], d.tau[1], d.tau[2], d.tau_phi, d.mu0H0sq, d.H0, d.G};
     std::memcpy(o, v, sizeof v);
+}
+
+fcd_status fcd_get_derived(const fcd_ctx *c, double *o) {
+    if (!c || !o) return FCD_EINVAL;
+    derived_out(c->D, o);
+    return FCD_OK;
+}
+
+fcd_status fcd_derive_params(const fcd_params *params, double *o) {
+    if (!params || !o) {
+        std::snprintf(g_last, sizeof g_last, "fcd_derive_params: null argument");
+        return FCD_EINVAL;
+    }
+    Derived d;
+    if (const char *why = derive(params, &d)) {
+        std::snprintf(g_last, sizeof g_last, "fcd_derive_params: %s", why);
+        return FCD_EINVAL;
+    }
+    derived_out(d, o);
     return FCD_OK;
 }
 

@@ -102,6 +102,7 @@ _SIGS = {
     "fcd_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "fcd_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "fcd_get_derived": (C.c_int, [C.c_void_p, DP]),
+    "fcd_derive_params": (C.c_int, [C.POINTER(fcd_params), DP]),
     "fcd_kernel_launches": (C.c_long, [C.c_void_p]),
     "fcd_solver_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong)]),
     "fcd_set_profiling": (C.c_int, [C.c_void_p, C.c_int]),
@@ -179,6 +180,22 @@ def make_params(cfg):
     p.eps_n = cfg.get("eps_n", 1e-12 if p.precision == FCD_FP64 else 1e-6)
     p.open_x = int(cfg.get("open_x", 0))
     return p
+
+
+DERIVED = ["u_avg", "sigma12", "sigma13", "sigma23", "gamma1", "gamma2", "gamma3", "gammaT",
+           "tau1", "tau2", "tau3", "tau_phi", "mu0H0sq", "H0", "G"]
+
+
+def derive_params(cfg):
+    """The library's lattice mapping of a workload (fcd_derive_params): host
+    code only, no context and no GPU."""
+    L = load()
+    p = make_params(cfg)
+    out = (C.c_double * 15)()
+    st = L.fcd_derive_params(C.byref(p), out)
+    if st != FCD_OK:
+        raise FcdError(st, L.fcd_last_error(None).decode())
+    return dict(zip(DERIVED, list(out)))
 
 
 _torch_alloc = None
@@ -285,9 +302,7 @@ class Channel:
     def derived(self):
         out = (C.c_double * 15)()
         self.check(load().fcd_get_derived(self.h, out))
-        names = ["u_avg", "sigma12", "sigma13", "sigma23", "gamma1", "gamma2", "gamma3", "gammaT",
-                 "tau1", "tau2", "tau3", "tau_phi", "mu0H0sq", "H0", "G"]
-        return dict(zip(names, list(out)))
+        return dict(zip(DERIVED, list(out)))
 
     def solver_stats(self):
         out = (C.c_longlong * 5)()
