@@ -149,9 +149,12 @@ def replica_throughput(total_ms, nodes, steps, ws, device=None):
 
 def measure_batched(steps, warmup):
     """The 96-instance regime sweep (FP32, Bo_m x Ca x {core, shell}, lengths
-    800-2400 x 200): all instances advanced by fcd_batch_step (one stream and
-    graph set per instance) against looping the plain method over the same
-    instances on one stream, at the same tolerance. The 8 GB state exceeds L2."""
+    800-2400 x 200, 29 M nodes, 8 GB of state: larger than L2) at one
+    tolerance: fcd_batch_step as it stands after its first steps chose a mode
+    (value), each mode fixed (the batched kernels: one launch per kernel over a
+    tile work list spanning every instance, one multigrid loop for all; and
+    every instance's own step graph on its own stream), and the plain method
+    looped over the instances on one stream."""
     import torch
     from paper_2410_11129_gb300 import fcd
     from paper_2410_11129_gb300 import workloads as W
@@ -159,34 +162,43 @@ def measure_batched(steps, warmup):
     nodes = sum(c["nx"] * c["ny"] for c in cfgs)
     stream = torch.cuda.current_stream()
     batch = fcd.Batch(cfgs)
-    batch.step(warmup)
-    torch.cuda.synchronize()
     a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    batch.step(steps)
-    z.record(stream)
-    torch.cuda.synchronize()
-    t_batch = a.elapsed_time(z)
+
+    def timed(run, warm):
+        run(warm)
+        torch.cuda.synchronize()
+        a.record(stream)
+        run(steps)
+        z.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(z)
+
+    t_auto = timed(batch.step, max(warmup, 6))  # the first 6 steps time both modes
+    tuning = batch.tuning()
+    batch.set_mode(1)
+    t_kernels = timed(batch.step, 2)
+    batch.set_mode(0)
+    t_streams = timed(batch.step, 2)
     L = fcd.load()
     for inst in batch.instances:  # the plain method: one instance after the other
         L.fcd_set_stream(inst.h, stream.cuda_stream)
-    for inst in batch.instances:
-        inst.step(1)
-    torch.cuda.synchronize()
-    a.record(stream)
-    for _ in range(steps):
-        for inst in batch.instances:
-            inst.step(1)
-    z.record(stream)
-    torch.cuda.synchronize()
-    t_loop = a.elapsed_time(z)
+
+    def looped(n):
+        for _ in range(n):
+            for inst in batch.instances:
+                inst.step(1)
+
+    t_loop = timed(looped, 1)
     obs = batch.observe(allow=(fcd.FCD_ENOCONV,))
     batch.close()
-    v_b = nodes * steps / (t_batch * 1e-3) / 1e6
-    v_l = nodes * steps / (t_loop * 1e-3) / 1e6
+    v = lambda t: nodes * steps / (t * 1e-3) / 1e6
     return {"workload": "regime sweep, 96 channels 800-2400 x 200, fp32, seed 12345",
             "nodes": nodes, "steps": steps, "mag_tol": cfgs[0]["mag_tol"],
-            "value": v_b, "looped_value": v_l, "unit": UNIT, "speedup": v_b / v_l,
+            "value": v(t_auto), "mode_chosen": {1: "batched kernels", 0: "instance streams"}.get(
+                tuning["mode"], "timing"),
+            "batched_kernels_value": v(t_kernels), "instance_streams_value": v(t_streams),
+            "looped_value": v(t_loop), "unit": UNIT, "speedup": v(t_auto) / v(t_loop),
+            "collide_tile_height": tuning["tile_h"],
             "max_mag_resid": max(o["mag_resid"] for o in obs)}
 
 
@@ -441,8 +453,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--gradient-steps", type=int, default=200,
-                    help="steps of the 800x100 gradient comparison (0: skip)")
+    ap.add_argument("--gradient-steps", type=int, default=2000,
+                    help="steps of the 800x100 gradient comparison, checkpoints every 500 "
+                         "(0: skip)")
     ap.add_argument("--large-steps", type=int, default=20,
                     help="steps timed on the 9600x1200 channel (0: skip)")
     ap.add_argument("--batched-steps", type=int, default=10,

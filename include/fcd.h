@@ -45,7 +45,13 @@ typedef enum {
     FCD_ENOMEM = 2,     /* device allocation failed */
     FCD_ECUDA = 3,      /* a CUDA call failed; the message names it */
     FCD_ENOCONV = 4,    /* potential solve hit its cycle cap before the tolerance */
-    FCD_EUNSTABLE = 5,  /* non-finite values detected */
+    FCD_EUNSTABLE = 5,  /* non-finite values detected: a collision that produced a
+                         * non-finite velocity or pressure marks its step on the
+                         * device (no trap; the steps complete) and the next
+                         * fcd_observables, fcd_get_field or fcd_get_populations
+                         * returns this status with that step in fcd_last_error;
+                         * fcd_observables also flags a non-finite phase field.
+                         * fcd_set_populations and fcd_set_state clear the record. */
     FCD_ESTATE = 6      /* snapshot does not match this context */
 } fcd_status;
 
@@ -116,8 +122,11 @@ void fcd_set_allocator(fcd_alloc_fn alloc, fcd_free_fn release, void *user);
  * allocates the state, sets the initial condition (concentric tanh profiles
  * of width xi, Poiseuille flow, f = f^eq, g = phi Gamma) and solves the
  * potential once. EINVAL for nx odd or < 4, ny < 2, r1 > r2, non-positive
- * density, viscosity, mobility or xi, a gamma_i <= 0 (total spreading, Eq. 27),
- * or an Eq. 41 branch without a magnetic phase. *out is NULL on failure. */
+ * density, viscosity, mobility or xi, eta < 0, a gamma_i = 0 (Eq. 26
+ * undefined), total spreading (a gamma_i < 0, Eq. 27) with eta = 0 (Eq. 28
+ * needs eta > 0 then), gamma_1 gamma_2 + gamma_1 gamma_3 + gamma_2 gamma_3 <= 0
+ * (gradient energy not positive), or an Eq. 41 branch without a magnetic
+ * phase. *out is NULL on failure. */
 fcd_status fcd_create(const fcd_params *params, fcd_ctx **out);
 
 /* Queue later work on this cudaStream_t (passed as void*). */
@@ -189,12 +198,18 @@ fcd_status fcd_last_step_profile(fcd_ctx *ctx, double *ms4);
 const char *fcd_last_error(const fcd_ctx *ctx);
 
 /* ---- Batched form: many independent channels (the Bo_m x Ca regime map of
- * Sec. 3.7 is a grid of separate runs). Each instance is a full context with
- * its own CUDA stream and captured step graphs; fcd_batch_step launches every
- * instance's step on its own stream so that the latency-bound kernels of some
- * instances overlap the bandwidth-bound collide-stream of others, then makes
- * the batch's caller stream wait for all of them. Results are bit-identical
- * to stepping each instance alone. */
+ * Sec. 3.7 is a grid of separate runs). Each instance is a full context (its
+ * own state; every fcd_* call works on it). The periodic FP32 instances of
+ * one storage form are advanced together by one fixed set of kernels per
+ * step, each launched once over a work list of tiles that spans all of them:
+ * phase recovery, a single loop of batched multigrid kernels in which every
+ * instance runs the cycle its own residual chose, and the fused
+ * collide-stream, whose tile height an autotuner picks at create by timing.
+ * Other instances (FP64, open channels) step on their own streams beside
+ * them. fcd_batch_step then makes the caller's stream wait for everything.
+ * On their own streams (mode 0 of fcd_batch_tuning) the instances' results
+ * are bit-identical to stepping each alone; the batched kernels agree with
+ * them to the rounding of contracted multiply-adds. */
 typedef struct fcd_batch fcd_batch;
 /* n parameter sets (instances may differ in every field, sizes included). */
 fcd_status fcd_batch_create(const fcd_params *params, int n, fcd_batch **out);
@@ -206,6 +221,25 @@ fcd_status fcd_batch_step(fcd_batch *b, long n);
  * non-OK instance status is returned. */
 fcd_status fcd_batch_observables(fcd_batch *b, fcd_obs *out);
 int fcd_batch_size(const fcd_batch *b);
+/* How the batch steps. *mode: 1 = the batched kernels for the groups, 0 =
+ * every instance's own step graph on its own stream, all at once (the results
+ * of the two agree to the rounding of the fused multiply-adds the compiler
+ * forms in each kernel variant); -1 while the first steps still time both: 6
+ * single steps, the first two of which build the graphs, the last four timed
+ * alternately; the faster mode is kept (the environment variable
+ * FCD_BATCH_MODE=0 or 1 at create fixes it instead). *batched = instances the
+ * batched kernels advance, *groups = their groups (each storage form split
+ * into about one group per 6 M lattice nodes, at most 8, balanced by nodes,
+ * each group on its own stream; FCD_BATCH_GROUPS=k at create fixes the
+ * split), tile_h[g] for g < tile_h_len = the collide-stream tile height the
+ * autotuner chose for group g at create. Any pointer may be NULL. An instance
+ * stepped on its own (fcd_step) leaves its group out of phase with it; that
+ * group then steps its instances one by one until their parities agree again. */
+fcd_status fcd_batch_tuning(const fcd_batch *b, int *mode, int *batched, int *groups, int *tile_h,
+                            int tile_h_len);
+/* Fix the stepping mode (0 or 1, as above) or time both again (-1). EINVAL for
+ * mode 1 when no instance can take the batched kernels. */
+fcd_status fcd_batch_set_mode(fcd_batch *b, int mode);
 /* Instance i (owned by the batch; use any fcd_* call on it, not fcd_destroy). */
 fcd_ctx *fcd_batch_instance(fcd_batch *b, int i);
 /* Reason of the last failure on b; with b == NULL, of the last failed create. */
@@ -227,8 +261,11 @@ void fcd_batch_destroy(fcd_batch *b);
  * Ca direction is zero. The returned handle accepts fcd_step, fcd_observables
  * (primal values), fcd_get_field (primal fields), fcd_kernel_launches,
  * fcd_solver_stats, fcd_last_error and fcd_destroy; state snapshots and
- * population import return FCD_ESTATE. Steps synchronise the stream once per
- * multigrid cycle (the solve loop is driven from the host). */
+ * population import return FCD_ESTATE. Each step runs as one captured CUDA
+ * graph (the primal and the four tangent solves as while-node loops, as in
+ * fcd_step), with no host synchronisation between steps; with the environment
+ * variable FCD_NO_GRAPH=1 the solves are driven from the host instead, one
+ * synchronisation per multigrid cycle. */
 enum { FCD_DIR_BO_M = 0, FCD_DIR_CA = 1, FCD_DIR_ALPHA = 2, FCD_DIR_NU_R = 3, FCD_NDIR = 4 };
 typedef struct {
     long step;
@@ -304,19 +341,24 @@ fcd_status fcd_adjoint_gradient_state(fcd_ctx *ctx, const double *seed_f, const 
  * advance). g: device pointer to the phase-field populations in the FP64
  * exchange layout (18*nx*ny doubles, g[i][a][y][x]); nx >= 4, ny >= 2,
  * nx <= 16384 and nx*ny <= 524288, else FCD_EINVAL with the reason on stderr.
- * Fills mass, centroids, extents, T_o, T_i and the breakup fields of the
- * given state (b_step = 0 if the core touches the carrier in it, else -1);
- * step, t_star and the solver fields are 0. Work runs on cuda_stream (a
- * cudaStream_t; NULL = legacy default stream) and the call synchronises it.
- * Scratch: one 9.6 MiB device array inside the library, reserved on every
+ * open_x: 0 for the periodic channel, 1 for the open channel (fcd_params.open_x;
+ * the extents and the breakup neighbourhood then do not wrap in x), as the
+ * context that produced the state. Fills mass, centroids, extents, T_o, T_i
+ * and the breakup fields of the given state (b_step = 0 if the core touches
+ * the carrier in it, else -1); step, t_star and the solver fields are 0. Work
+ * runs on cuda_stream (a cudaStream_t; NULL = legacy default stream) and the
+ * call synchronises it.
+ * Scratch: one 9.5 MiB device array inside the library, reserved on every
  * GPU that loads it until the process exits; its device address is looked up
- * (cudaGetSymbolAddress) by the first call on each device, so make that first
- * call before any stream capture. All calls share that array: calls that may
- * overlap on the GPU (other streams, other host threads) race and must be
- * serialised by the caller. Allocates nothing: no cudaMalloc, cudaFree or
- * allocating library routine. */
-fcd_status fcd_observe_populations_noalloc(const double *g, int nx, int ny, void *cuda_stream,
-                                           fcd_obs *out);
+ * (cudaGetSymbolAddress) by the first call on each device and kept, so make
+ * that first call before any stream capture; after cudaDeviceReset (or any
+ * teardown of the device's primary context) the kept address is stale and
+ * this entry point must not be called again in the process. All calls share
+ * that array: calls that may overlap on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller. Allocates nothing: no
+ * cudaMalloc, cudaFree or allocating library routine. */
+fcd_status fcd_observe_populations_noalloc(const double *g, int nx, int ny, int open_x,
+                                           void *cuda_stream, fcd_obs *out);
 void fcd_destroy(fcd_ctx *ctx);
 
 #ifdef __cplusplus

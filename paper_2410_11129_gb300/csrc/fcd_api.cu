@@ -15,7 +15,19 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "fcd_adjoint.cuh"
+
+// NVTX range for the duration of a scope (visible to profilers that record
+// NVTX; a no-op otherwise). Host-side: a graph-driven step is one range, the
+// host-driven step (FCD_NO_GRAPH=1) one range per stage.
+struct NvtxScope {
+    explicit NvtxScope(const char *name) { nvtxRangePushA(name); }
+    ~NvtxScope() { nvtxRangePop(); }
+    NvtxScope(const NvtxScope &) = delete;
+    NvtxScope &operator=(const NvtxScope &) = delete;
+};
 
 namespace fcd {
 size_t observe_scratch_doubles(int nx, int ny);
@@ -191,7 +203,7 @@ struct SnapHeader {
     unsigned long long brk;
     int cur, pad;  // which level-0 potential buffer is current
 };
-static const unsigned SNAP_VERSION = 3;
+static const unsigned SNAP_VERSION = 4;
 static const unsigned SNAP_MAGIC = 0x46434453u;  // "FCDS"
 
 template <typename T>
@@ -212,6 +224,7 @@ struct Engine : fcd_ctx {
     MgCtl *ctl = nullptr;
     MgHost<T> *mg = nullptr;
     unsigned long long *brk = nullptr;
+    unsigned long long *unst = nullptr;  // first step with a non-finite collision (~0: none)
     long long *d_step = nullptr;
     double *obs_scratch = nullptr;
     ObsOut *obs_out = nullptr;
@@ -219,6 +232,7 @@ struct Engine : fcd_ctx {
     ObsOut *h_obs = nullptr;
     SnapHeader *h_snap = nullptr;  // pinned staging of snapshot headers
     unsigned long long *h_brk = nullptr;
+    unsigned long long *h_unst = nullptr;
     cudaStream_t cap = nullptr;
     cudaGraph_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
     cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
@@ -228,6 +242,14 @@ struct Engine : fcd_ctx {
     long host_kernels = 0;
     int reported_nonconv = 0;
     int copies = 1;  // plane sets per field: 1, or 1 + NT for the tangent context
+
+    // one level-0 potential buffer: psi_planes<T>() planes (FP32: hi and lo)
+    size_t psi_bytes() const { return (size_t)psi_planes<T>() * ps * sizeof(T); }
+    // FP32 contexts solving below 1e-4 hold psi' as the hi + lo pair: one FP32
+    // plane floors the residual at ~2e-5 on the paper's channels (more on
+    // larger droplets), and 1e-4 is the tightest tolerance it serves
+    static constexpr double COMP_TOL = 1e-4;
+    int comp = 0;
 
     T *dalloc(size_t bytes) {
         void *p = alloc(bytes, user);
@@ -249,6 +271,7 @@ struct Engine : fcd_ctx {
         if (h_obs) cudaFreeHost(h_obs);
         if (h_snap) cudaFreeHost(h_snap);
         if (h_brk) cudaFreeHost(h_brk);
+        if (h_unst) cudaFreeHost(h_unst);
         if (cap) cudaStreamDestroy(cap);
         for (auto e : ev)
             if (e) cudaEventDestroy(e);
@@ -261,6 +284,7 @@ struct Engine : fcd_ctx {
         pitch = (prm.nx + 31) / 32 * 32;
         ps = (long long)pitch * prm.ny;
         P = make_phys<T>(&prm, D, pitch);
+        comp = sizeof(T) == 4 && prm.mag_tol < COMP_TOL ? 1 : 0;
         const char *nog = getenv("FCD_NO_GRAPH");
         use_graph = !(nog && nog[0] == '1');
         for (int b = 0; b < 2; b++) {
@@ -270,33 +294,37 @@ struct Engine : fcd_ctx {
         phi1 = dalloc(copies * ps * sizeof(T));
         phi2 = dalloc(copies * ps * sizeof(T));
         k = dalloc(copies * ps * sizeof(T));
-        psiA = dalloc(ps * sizeof(T));
-        psiB = dalloc(ps * sizeof(T));
-        psiP = dalloc(ps * sizeof(T));
+        psiA = dalloc(psi_bytes());
+        psiB = dalloc(psi_bytes());
+        psiP = dalloc(psi_bytes());
         macro = dalloc(3 * ps * sizeof(T));
         ctl = reinterpret_cast<MgCtl *>(dalloc(sizeof(MgCtl)));
         brk = reinterpret_cast<unsigned long long *>(dalloc(sizeof(unsigned long long)));
+        unst = reinterpret_cast<unsigned long long *>(dalloc(sizeof(unsigned long long)));
         d_step = reinterpret_cast<long long *>(dalloc(sizeof(long long)));
         obs_scratch = reinterpret_cast<double *>(dalloc(observe_scratch_doubles(prm.nx, prm.ny) * sizeof(double)));
         obs_out = reinterpret_cast<ObsOut *>(dalloc(sizeof(ObsOut)));
         for (void *p : {f[0], f[1], g[0], g[1], (void *)phi1, (void *)phi2, (void *)k, (void *)psiA,
-                        (void *)psiB, (void *)psiP, (void *)macro, (void *)ctl, (void *)brk, (void *)d_step,
+                        (void *)psiB, (void *)psiP, (void *)macro, (void *)ctl, (void *)brk, (void *)unst, (void *)d_step,
                         (void *)obs_scratch, (void *)obs_out})
             if (!p) return fail(FCD_ENOMEM, "device allocation failed");
         CK(cudaMallocHost(&h_ctl, sizeof(MgCtl)));
         CK(cudaMallocHost(&h_obs, sizeof(ObsOut)));
         CK(cudaMallocHost(&h_snap, sizeof(SnapHeader)));
         CK(cudaMallocHost(&h_brk, sizeof(unsigned long long)));
+        CK(cudaMallocHost(&h_unst, sizeof(unsigned long long)));
         CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
         for (auto &e : ev) CK(cudaEventCreate(&e));
-        mg = mg_create<T>(prm.nx, prm.ny, pitch, k, psiA, psiB, ctl, alloc, release, user, err, sizeof err);
+        mg = mg_create<T>(prm.nx, prm.ny, pitch, k, psiA, psiB, ctl, alloc, release, user, err,
+                          sizeof err, comp);
         if (!mg) return FCD_ENOMEM;
         cudaStream_t s = stream;
         CK(cudaMemsetAsync(ctl, 0, sizeof(MgCtl), s));
-        CK(cudaMemsetAsync(psiA, 0, ps * sizeof(T), s));
-        CK(cudaMemsetAsync(psiB, 0, ps * sizeof(T), s));
-        CK(cudaMemsetAsync(psiP, 0, ps * sizeof(T), s));
+        CK(cudaMemsetAsync(psiA, 0, psi_bytes(), s));
+        CK(cudaMemsetAsync(psiB, 0, psi_bytes(), s));
+        CK(cudaMemsetAsync(psiP, 0, psi_bytes(), s));
         CK(cudaMemsetAsync(brk, 0xff, sizeof(unsigned long long), s));
+        CK(cudaMemsetAsync(unst, 0xff, sizeof(unsigned long long), s));
         CK(cudaMemsetAsync(d_step, 0, sizeof(long long), s));
         // padding columns of every plane stay zero
         for (int b = 0; b < 2; b++) {
@@ -329,7 +357,7 @@ struct Engine : fcd_ctx {
     // The previous potential (for the extrapolated initial guess) := current.
     fcd_status keep_history() {
         if (sync_ctl() != FCD_OK) return FCD_ECUDA;
-        CK(cudaMemcpyAsync(psiP, h_ctl->cur ? psiB : psiA, ps * sizeof(T), cudaMemcpyDeviceToDevice, stream));
+        CK(cudaMemcpyAsync(psiP, h_ctl->cur ? psiB : psiA, psi_bytes(), cudaMemcpyDeviceToDevice, stream));
         CK(cudaStreamSynchronize(stream));
         return FCD_OK;
     }
@@ -338,7 +366,7 @@ struct Engine : fcd_ctx {
     // when capturing, by host polling otherwise)
     fcd_status enqueue_pre(int c, cudaStream_t s) {
         PhaseCtl pc{ctl, magnetic() ? 1 : 0, prm.mag_tol * D.H0, prm.mag_max_iter, d_step,
-                    magnetic() ? 1 : 0, psiA, psiB, psiP};
+                    magnetic() ? 1 : 0, psiA, psiB, psiP, comp};
         launch_phase<T>(mode, P, g[c], phi1, phi2, k, pc, s);
         return FCD_OK;
     }
@@ -357,6 +385,7 @@ struct Engine : fcd_ctx {
         a.macro = store_macro ? macro : nullptr;
         a.brk = brk;
         a.step = &ctl->step_cur;
+        a.unst = unst;
         a.open_x = prm.open_x;
         launch_collide<T>(mode, a, s);
         if (prm.open_x)
@@ -508,14 +537,21 @@ struct Engine : fcd_ctx {
             host_kernels += pre_kernels() + post_kernels();
         } else {
             if (profiling) CK(cudaEventRecord(ev[0], s));
-            enqueue_pre(cur, s);
+            {
+                NvtxScope r("fcd phase recovery");
+                enqueue_pre(cur, s);
+            }
             if (profiling) CK(cudaEventRecord(ev[1], s));
             if (magnetic()) {
+                NvtxScope r("fcd potential solve");
                 fcd_status st = host_mg_loop(s);
                 if (st != FCD_OK) return st;
             }
             if (profiling) CK(cudaEventRecord(ev[2], s));
-            enqueue_post(cur, sm != 0, s);
+            {
+                NvtxScope r("fcd collide-stream");
+                enqueue_post(cur, sm != 0, s);
+            }
             if (profiling) CK(cudaEventRecord(ev[3], s));
             host_kernels += pre_kernels() + post_kernels();
             CK(cudaGetLastError());
@@ -546,9 +582,9 @@ struct Engine : fcd_ctx {
         if (max_iter <= 0) max_iter = prm.mag_max_iter;
         cudaStream_t s = stream;
         if (!magnetic()) {
-            CK(cudaMemsetAsync(psiA, 0, ps * sizeof(T), s));
-            CK(cudaMemsetAsync(psiB, 0, ps * sizeof(T), s));
-            CK(cudaMemsetAsync(psiP, 0, ps * sizeof(T), s));
+            CK(cudaMemsetAsync(psiA, 0, psi_bytes(), s));
+            CK(cudaMemsetAsync(psiB, 0, psi_bytes(), s));
+            CK(cudaMemsetAsync(psiP, 0, psi_bytes(), s));
             CK(cudaStreamSynchronize(s));
             if (iters) *iters = 0;
             if (resid) *resid = 0.0;
@@ -577,6 +613,7 @@ struct Engine : fcd_ctx {
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(h_obs, obs_out, sizeof(ObsOut), cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(h_brk, brk, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(h_unst, unst, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(h_ctl, ctl, sizeof(MgCtl), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         const ObsOut &r = *h_obs;
@@ -608,6 +645,7 @@ struct Engine : fcd_ctx {
         }
         o->mag_iters = magnetic() ? h_ctl->last_iters : 0;
         o->mag_resid = magnetic() ? h_ctl->last_resid : 0.0;
+        if (unstable_status() != FCD_OK) return FCD_EUNSTABLE;
         if (r.nonfinite) return fail(FCD_EUNSTABLE, "non-finite phase field at step %ld", step);
         if (h_ctl->nonconv_count > reported_nonconv) {
             reported_nonconv = h_ctl->nonconv_count;
@@ -615,6 +653,14 @@ struct Engine : fcd_ctx {
                         h_ctl->last_resid);
         }
         return FCD_OK;
+    }
+
+    // FCD_EUNSTABLE once a collision produced a non-finite velocity or
+    // pressure; h_unst must have been copied in the caller's synchronised batch.
+    fcd_status unstable_status() {
+        if (*h_unst == ~0ull) return FCD_OK;
+        return fail(FCD_EUNSTABLE, "non-finite velocity or pressure, first in step %llu (now at step %ld)",
+                    *h_unst, step);
     }
 
     double *staging(size_t doubles) {
@@ -643,14 +689,17 @@ struct Engine : fcd_ctx {
             host_kernels += 1;
         } else {
             if (sync_ctl() != FCD_OK) { cudaFree(st); return FCD_ECUDA; }
-            launch_plane_to_f64<T>(h_ctl->cur ? psiB : psiA, prm.nx, prm.ny, pitch, st, s);
+            launch_psi_to_f64<T>(h_ctl->cur ? psiB : psiA, prm.nx, prm.ny, pitch, st, s);
             host_kernels += 1;
         }
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaMemcpyAsync(dst, st, N * sizeof(double), cudaMemcpyDefault, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h_unst, unst, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) rc = fail(FCD_ECUDA, "get_field: %s", cudaGetErrorString(e));
         cudaFree(st);
+        if (rc == FCD_OK) rc = unstable_status();  // the field is delivered all the same
         return rc;
     }
 
@@ -661,16 +710,18 @@ struct Engine : fcd_ctx {
         if (!st) return fail(FCD_ENOMEM, "staging allocation failed");
         if (sync_ctl() != FCD_OK) { cudaFree(st); return FCD_ECUDA; }
         launch_export<T>(mode, P, f[cur], g[cur], st, st + 9 * N, s);
-        launch_plane_to_f64<T>(h_ctl->cur ? psiB : psiA, prm.nx, prm.ny, pitch, st + 27 * N, s);
+        launch_psi_to_f64<T>(h_ctl->cur ? psiB : psiA, prm.nx, prm.ny, pitch, st + 27 * N, s);
         host_kernels += 2;
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess && fo) e = cudaMemcpyAsync(fo, st, 9 * N * sizeof(double), cudaMemcpyDefault, s);
         if (e == cudaSuccess && go) e = cudaMemcpyAsync(go, st + 9 * N, 18 * N * sizeof(double), cudaMemcpyDefault, s);
         if (e == cudaSuccess && po) e = cudaMemcpyAsync(po, st + 27 * N, N * sizeof(double), cudaMemcpyDefault, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h_unst, unst, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         cudaFree(st);
         if (e != cudaSuccess) return fail(FCD_ECUDA, "get_populations: %s", cudaGetErrorString(e));
-        return FCD_OK;
+        return unstable_status();  // the populations are delivered all the same
     }
 
     fcd_status set_pops(const double *fi, const double *gi, const double *pi, long st_) override {
@@ -688,12 +739,13 @@ struct Engine : fcd_ctx {
             host_kernels++;
             if (pi) {
                 if (sync_ctl() != FCD_OK) { cudaFree(st); return FCD_ECUDA; }
-                launch_plane_from_f64<T>(st + 27 * N, prm.nx, prm.ny, pitch, h_ctl->cur ? psiB : psiA, s);
+                launch_psi_from_f64<T>(st + 27 * N, prm.nx, prm.ny, pitch, h_ctl->cur ? psiB : psiA, comp, s);
                 host_kernels++;
             }
             e = cudaGetLastError();
         }
         if (e == cudaSuccess) e = cudaMemsetAsync(brk, 0xff, sizeof(unsigned long long), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(unst, 0xff, sizeof(unsigned long long), s);
         long long s64 = st_;
         if (e == cudaSuccess) e = cudaMemcpyAsync(d_step, &s64, sizeof(long long), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -709,7 +761,7 @@ struct Engine : fcd_ctx {
     // needs to read the control block on the host: each is one stream of
     // asynchronous copies and a single synchronisation.
     size_t state_bytes() const override {
-        return sizeof(SnapHeader) + 27 * (size_t)ps * sizeof(S) + 3 * (size_t)ps * sizeof(T);
+        return sizeof(SnapHeader) + 27 * (size_t)ps * sizeof(S) + 3 * psi_bytes();
     }
 
     fcd_status get_state(void *dst, size_t bytes) override {
@@ -736,8 +788,8 @@ struct Engine : fcd_ctx {
         CK(cudaMemcpyAsync(d + off, g[cur], 18 * ps * sizeof(S), cudaMemcpyDefault, s));
         off += 18 * ps * sizeof(S);
         for (T *q : {psiA, psiB, psiP}) {
-            CK(cudaMemcpyAsync(d + off, q, ps * sizeof(T), cudaMemcpyDefault, s));
-            off += ps * sizeof(T);
+            CK(cudaMemcpyAsync(d + off, q, psi_bytes(), cudaMemcpyDefault, s));
+            off += psi_bytes();
         }
         CK(cudaStreamSynchronize(s));
         return FCD_OK;
@@ -768,12 +820,13 @@ struct Engine : fcd_ctx {
         CK(cudaMemcpyAsync(g[cur], p + off, 18 * ps * sizeof(S), cudaMemcpyDefault, s));
         off += 18 * ps * sizeof(S);
         for (T *q : {psiA, psiB, psiP}) {
-            CK(cudaMemcpyAsync(q, p + off, ps * sizeof(T), cudaMemcpyDefault, s));
-            off += ps * sizeof(T);
+            CK(cudaMemcpyAsync(q, p + off, psi_bytes(), cudaMemcpyDefault, s));
+            off += psi_bytes();
         }
         CK(cudaMemcpyAsync(&ctl->cur, &h.cur, sizeof(int), cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(brk, &h.brk, sizeof(unsigned long long), cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(d_step, &h.step, sizeof(long long), cudaMemcpyHostToDevice, s));
+        CK(cudaMemsetAsync(unst, 0xff, sizeof(unsigned long long), s));
         CK(cudaStreamSynchronize(s));
         step = (long)h.step;
         return FCD_OK;
@@ -1567,6 +1620,45 @@ struct AdjointEngine : Engine<double> {
     }
 };
 
+// ---------------------------------------------------------------- batch view
+namespace fcd {
+bool engine_view(fcd_ctx *c, EngineView *v) {
+    auto *e = dynamic_cast<Engine<float> *>(c);
+    if (!e || e->prm.open_x) return false;
+    v->mode = e->mode;
+    v->magnetic = e->magnetic() ? 1 : 0;
+    v->cur = e->cur;
+    v->P = e->P;
+    for (int b = 0; b < 2; b++) {
+        v->f[b] = e->f[b];
+        v->g[b] = e->g[b];
+    }
+    v->phi1 = e->phi1;
+    v->phi2 = e->phi2;
+    v->k = e->k;
+    v->psiA = e->psiA;
+    v->psiB = e->psiB;
+    v->psiP = e->psiP;
+    v->macro = e->macro;
+    v->ctl = e->ctl;
+    v->mg = e->mg;
+    v->brk = e->brk;
+    v->unst = e->unst;
+    v->d_step = e->d_step;
+    v->tolH0 = e->prm.mag_tol * e->D.H0;
+    v->max_iter = e->prm.mag_max_iter;
+    v->comp = e->comp;
+    return true;
+}
+
+void engine_advance(fcd_ctx *c, long steps) {
+    auto *e = dynamic_cast<Engine<float> *>(c);
+    if (!e) return;
+    if (steps & 1) e->cur ^= 1;
+    e->step += steps;
+}
+}  // namespace fcd
+
 // ---------------------------------------------------------------- C ABI
 static thread_local char g_last[512];  // reason of the last failed fcd_create on this thread
 
@@ -1686,6 +1778,7 @@ fcd_status fcd_adjoint_gradient(fcd_ctx *c, double w_T, double w_overlap, fcd_ad
     if (!c || !o) return FCD_EINVAL;
     auto *e = dynamic_cast<AdjointEngine *>(c);
     if (!e) return c->fail(FCD_EINVAL, "not an adjoint context");
+    NvtxScope r("fcd_adjoint_gradient");
     return e->gradient(w_T, w_overlap, o, df0, dg0);
 }
 
@@ -1704,14 +1797,19 @@ fcd_status fcd_set_stream(fcd_ctx *c, void *stream) {
     return FCD_OK;
 }
 
-fcd_status fcd_step(fcd_ctx *c, long n) { return c ? c->do_step(n) : FCD_EINVAL; }
+fcd_status fcd_step(fcd_ctx *c, long n) {
+    NvtxScope r("fcd_step");
+    return c ? c->do_step(n) : FCD_EINVAL;
+}
 
 fcd_status fcd_solve_magnetic(fcd_ctx *c, double tol, int max_iter, int *iters, double *resid) {
+    NvtxScope r("fcd_solve_magnetic");
     return c ? c->solve(tol, max_iter, iters, resid) : FCD_EINVAL;
 }
 
 fcd_status fcd_observables(fcd_ctx *c, fcd_obs *o) {
     if (!c || !o) return FCD_EINVAL;
+    NvtxScope r("fcd_observables");
     return c->observe(o);
 }
 
@@ -1731,10 +1829,12 @@ fcd_status fcd_set_populations(fcd_ctx *c, const double *f, const double *g, con
 size_t fcd_state_bytes(const fcd_ctx *c) { return c ? c->state_bytes() : 0; }
 
 fcd_status fcd_get_state(fcd_ctx *c, void *dst, size_t bytes) {
+    NvtxScope r("fcd_get_state");
     return c ? c->get_state(dst, bytes) : FCD_EINVAL;
 }
 
 fcd_status fcd_set_state(fcd_ctx *c, const void *src, size_t bytes) {
+    NvtxScope r("fcd_set_state");
     return c ? c->set_state(src, bytes) : FCD_EINVAL;
 }
 

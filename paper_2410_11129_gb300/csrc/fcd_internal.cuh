@@ -13,6 +13,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "fcd.h"
 #include "fcd_dual.cuh"
 
@@ -59,6 +61,24 @@ __host__ __device__ constexpr T g_off(int a) {
     return MODE == MODE_FP32_OFFSET ? -wgt<T>(a) / T(2) : T(0);
 }
 
+// Level-0 potential buffers. FP64 contexts hold psi' in one plane. FP32
+// contexts reserve two FP32 planes per buffer (the low plane one plane stride
+// after the high one): psi' itself is ~30 H0 on the channels of the paper's
+// shape, so one FP32 plane quantises it at ~2e-6 H0, and the 9-point residual
+// of that quantisation (~1e-5 H0) hides any smaller residual from the solve's
+// stopping test. A context whose tolerance is below that keeps psi' as the
+// unevaluated sum hi + lo (Level::comp); the others use the high plane alone
+// and leave the low one at 0.
+template <typename T>
+__host__ __device__ constexpr int psi_planes() { return sizeof(T) == 4 ? 2 : 1; }
+
+// Error-free FP32 sum (Knuth's TwoSum): s + e equals a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
 template <typename T>
 __device__ __forceinline__ T clamp01(T v) {
     return v < T(0) ? T(0) : (v > T(1) ? T(1) : v);
@@ -101,6 +121,10 @@ struct Level {
     // level 0 of FP64 hierarchies: the 9-point coefficients of every node, formed
     // once per solve (planes c_1..c_8, diagonal, its reciprocal, -L psi0)
     T *coef;
+    // level 0 of FP32 hierarchies: 1 when psi' is the hi + lo pair (the lo
+    // plane one plane stride after each buffer) and the residual is formed in
+    // link differences (contexts whose tolerance one FP32 plane cannot reach)
+    int comp;
 };
 
 // Device-side control block of one potential solve.
@@ -142,6 +166,7 @@ struct PhaseCtl {
     // psi_prev keeps the previous solution (buffers of the compute type)
     int extrap;
     void *psiA, *psiB, *psi_prev;
+    int comp;  // FP32: psi' is the hi + lo pair (Level::comp)
 };
 
 struct ObsOut {
@@ -178,12 +203,37 @@ struct LbmArgs {
     T *macro;                    // nullptr: do not store the macroscopic fields
     unsigned long long *brk;     // sticky breakup key (nullptr: no check)
     const long long *step;       // device step counter (breakup key)
+    // first step whose collision produced a non-finite u or p* (atomicMin of
+    // the step index; ~0ull while none; nullptr: no check)
+    unsigned long long *unst = nullptr;
     int open_x = 0;              // open channel: no wrap in x (see launch_open_bc)
 };
 
 template <typename T>
 void launch_phase(int mode, const Phys<T> &P, const void *g, T *phi1, T *phi2, T *k,
                   PhaseCtl pc, cudaStream_t s);
+
+// Batched step over many periodic channels: per instance and buffer parity,
+// the collide-stream arguments (lbm; its g_src is also what the phase kernel
+// reads) and the phase kernel's outputs and control; a work list of tiles.
+template <typename T>
+struct BatchLbm {
+    LbmArgs<T> lbm;
+    PhaseCtl pc;
+    T *phi1, *phi2, *k;
+};
+struct BatchTile {
+    int inst;    // instance
+    int x0, y0;  // tile origin in that instance's lattice
+    int lead;    // 1 for one tile per instance (the phase kernel's control-block reset)
+};
+template <typename T>
+void launch_phase_batch(int mode, const BatchLbm<T> *tab, const BatchTile *tiles, int ntiles,
+                        cudaStream_t s);  // 32 x 8 tiles
+// tile_h: 4, 8 or 16 rows per tile (the list's tiles are TX x tile_h)
+template <typename T>
+void launch_collide_batch(int mode, int tile_h, const BatchLbm<T> *tab, const BatchTile *tiles,
+                          int ntiles, cudaStream_t s);
 template <typename T>
 void launch_collide(int mode, const LbmArgs<T> &a, cudaStream_t s);
 void launch_collide_tangent(const LbmArgs<double, DualT> &a, cudaStream_t s);
@@ -211,6 +261,12 @@ void launch_plane_from_f64(const double *src, int nx, int ny, int pitch, T *dst,
 template <typename T>
 void launch_phi3_to_f64(const T *p1, const T *p2, int nx, int ny, int pitch, double *dst,
                         cudaStream_t s);
+// psi' of a level-0 buffer (psi_planes<T>() planes) to and from FP64
+template <typename T>
+void launch_psi_to_f64(const T *src, int nx, int ny, int pitch, double *dst, cudaStream_t s);
+template <typename T>
+void launch_psi_from_f64(const double *src, int nx, int ny, int pitch, T *dst, int comp,
+                         cudaStream_t s);  // comp: keep the low part (else the low plane is 0)
 
 // multigrid
 template <typename T>
@@ -218,7 +274,7 @@ struct MgHost;  // defined in fcd_mg.cu
 template <typename T>
 MgHost<T> *mg_create(int nx, int ny, int pitch, T *k0, T *psiA, T *psiB, MgCtl *ctl,
                      void *(*alloc)(size_t, void *), void (*release)(void *, void *), void *user,
-                     char *err, size_t errlen);
+                     char *err, size_t errlen, int comp = 0);
 template <typename T>
 void mg_destroy(MgHost<T> *m);
 // One V-cycle = head (lattice residual; decides whether the cycle runs) +
@@ -250,6 +306,21 @@ void mg_tangent_rhs(MgHost<double> *m, const double *dk, double H0c, double H0s,
 void mg_psi_io(MgHost<double> *m, int op, double *plane, double *prev, cudaStream_t s);
 template <typename T>
 int mg_levels(const MgHost<T> *m);
+// Batched solves of many FP32 hierarchies (one per instance; fields and
+// control blocks stay the instances' own): opening sweeps of every solve, and
+// the body of the loop that runs until every solve is done (in_graph: the
+// residual launch sets the while node's condition hw).
+struct MgBatch;
+MgBatch *mg_batch_create(const std::vector<MgHost<float> *> &ms, const std::vector<float> &H0c,
+                         const std::vector<float> &H0s, void *(*alloc)(size_t, void *),
+                         void (*release)(void *, void *), void *user, char *err, size_t errlen);
+void mg_batch_destroy(MgBatch *b);
+void mg_batch_presmooth(MgBatch *b, cudaStream_t s);
+void mg_batch_body(MgBatch *b, cudaGraphConditionalHandle hw, int in_graph, cudaStream_t s);
+int mg_batch_body_kernels(const MgBatch *b);
+// after a body launched with in_graph = 0: 1 while some solve goes on, 0 when
+// all are done, -1 on a CUDA error (synchronises s)
+int mg_batch_any(MgBatch *b, cudaStream_t s);
 
 // tangent step (FP64 primal + NT tangent copies)
 void launch_tangent_phase(const Phys<double> &P, const double *g, double *phi1, double *phi2,
@@ -309,7 +380,34 @@ void launch_adj_seed(const Phys<double> &P, const double *phi1, const double *ph
                      double wT, double wO, void *scratch, double *pb, double *ab, AdjOut *out,
                      cudaStream_t s);
 
-// observables
+// The device state of a plain FP32 periodic context (fcd_create), for the
+// batched step: the batch's kernels read and write these buffers directly.
+struct EngineView {
+    int mode;      // MODE_FP32 or MODE_FP32_OFFSET
+    int magnetic;  // a potential solve runs every step
+    int cur;       // population buffer of the current state
+    Phys<float> P;
+    void *f[2], *g[2];
+    float *phi1, *phi2, *k, *psiA, *psiB, *psiP, *macro;
+    MgCtl *ctl;
+    MgHost<float> *mg;
+    unsigned long long *brk, *unst;
+    long long *d_step;
+    double tolH0;
+    int max_iter;
+    int comp;  // psi' as the hi + lo pair
+};
+// false (and v untouched) for any other context
+bool engine_view(fcd_ctx *c, EngineView *v);
+// the host-side record of a context after `steps` steps run by the batch
+void engine_advance(fcd_ctx *c, long steps);
+
+// observables. Scratch layout of one reduction (doubles): phi_1 and phi_2
+// planes (nx * ny each, unpadded), then OBS_COLS doubles per column.
+constexpr int OBS_COLS = 12;
+constexpr size_t observe_scratch_doubles_of(long long nx, long long ny) {
+    return 2ull * (size_t)(nx * ny) + (size_t)OBS_COLS * (size_t)nx;
+}
 size_t observe_scratch_doubles(int nx, int ny);
 template <typename T>
 void launch_observe(int mode, const Phys<T> &P, const void *g, double *scratch, ObsOut *out,

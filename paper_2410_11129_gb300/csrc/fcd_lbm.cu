@@ -23,11 +23,13 @@ template <>
 struct StoreT<MODE_TANGENT> { using type = double; };
 
 // ---------------------------------------------------------------- phase
+// One 32 x 8 tile of nodes starting at (x0, y0); the lead block of the grid
+// also resets the control block and advances the step counter.
 template <typename T, int MODE>
-__global__ void __launch_bounds__(256) phase_kernel(Phys<T> P, const void *gv, T *phi1, T *phi2,
-                                                    T *k, PhaseCtl pc) {
+__device__ __forceinline__ void phase_tile(const Phys<T> &P, const void *gv, T *phi1, T *phi2,
+                                           T *k, const PhaseCtl &pc, int x0, int y0, bool lead) {
     using S = typename StoreT<MODE>::type;
-    if (pc.ctl && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
+    if (pc.ctl && lead && threadIdx.x == 0 && threadIdx.y == 0) {
         MgCtl *c = pc.ctl;
         if (pc.reset) {  // start of a potential solve
             c->norm_bits = 0ull;
@@ -48,8 +50,7 @@ __global__ void __launch_bounds__(256) phase_kernel(Phys<T> P, const void *gv, T
         }
     }
     const S *g = static_cast<const S *>(gv);
-    int x = blockIdx.x * blockDim.x + threadIdx.x;
-    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
     if (x >= P.nx || y >= P.ny) return;
     long long n = (long long)y * P.pitch + x;
     T p1 = T(0), p2 = T(0);
@@ -63,14 +64,33 @@ __global__ void __launch_bounds__(256) phase_kernel(Phys<T> P, const void *gv, T
     if (pc.extrap) {  // second-order extrapolation in time of the potential
         T *psi = static_cast<T *>(pc.ctl->cur ? pc.psiB : pc.psiA);
         T *prev = static_cast<T *>(pc.psi_prev);
-        const T now = psi[n], before = prev[n];
-        prev[n] = now;
-        psi[n] = T(2) * now - before;
+        if (psi_planes<T>() == 2 && pc.comp) {  // psi' = hi + lo (low plane one plane on)
+            const long long L = P.ps;
+            const float h = psi[n], l = psi[L + n], ph = prev[n], pl = prev[L + n];
+            prev[n] = h;
+            prev[L + n] = l;
+            float a, e, hh, ll;
+            two_sum(2.f * h, -ph, a, e);
+            two_sum(a, __fadd_rn(__fsub_rn(2.f * l, pl), e), hh, ll);
+            psi[n] = hh;
+            psi[L + n] = ll;
+        } else {
+            const T now = psi[n], before = prev[n];
+            prev[n] = now;
+            psi[n] = T(2) * now - before;
+        }
     }
     if (k) {
         T h1 = clamp01(p1), h2 = clamp01(p2), h3 = clamp01(T(1) - p1 - p2);
         k[n] = T(1) / (P.ik[0] * h1 + P.ik[1] * h2 + P.ik[2] * h3);
     }
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) phase_kernel(Phys<T> P, const void *gv, T *phi1, T *phi2,
+                                                    T *k, PhaseCtl pc) {
+    phase_tile<T, MODE>(P, gv, phi1, phi2, k, pc, blockIdx.x * blockDim.x, blockIdx.y * blockDim.y,
+                        blockIdx.x == 0 && blockIdx.y == 0);
 }
 
 // ---------------------------------------------------------------- collide
@@ -178,18 +198,17 @@ __host__ __device__ constexpr int collide_min_blocks() { return MODE == MODE_FP3
 // OPEN: the channel's x ends are an inlet and an outlet (phi-like fields
 // mirrored there, populations leaving through them dropped; psi' stays
 // periodic); otherwise x is periodic.
-template <typename T, int MODE, bool OPEN>
-__global__ void __launch_bounds__(TX *tile_y<MODE>(), collide_min_blocks<MODE>())
-    collide_kernel(LbmArgs<T, typename Compute<T, MODE>::type> A) {
+// One TX x TYM tile of nodes starting at (x0, y0), run by TX x TYM threads.
+template <typename T, int MODE, bool OPEN, int TYM = tile_y<MODE>()>
+__device__ __forceinline__ void collide_tile(const LbmArgs<T, typename Compute<T, MODE>::type> &A,
+                                             int x0, int y0) {
     using S = typename StoreT<MODE>::type;
     using R = typename Compute<T, MODE>::type;  // arithmetic type
     using B = T;                                // type of the constants
-    constexpr int TYM = tile_y<MODE>();
     __shared__ R s1[TYM + 2][TX + 2], s2[TYM + 2][TX + 2], sr[TYM + 2][TX + 2], sp[TYM + 2][TX + 2];
     const Phys<R> &P = A.P;
     const int nx = P.nx, ny = P.ny, pitch = P.pitch;
     const long long ps = P.ps;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TYM;
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
     const bool live = x < nx && y < ny;
     const long long n = (long long)y * pitch + x;
@@ -325,6 +344,11 @@ __global__ void __launch_bounds__(TX *tile_y<MODE>(), collide_min_blocks<MODE>()
         A.macro[ps + n] = value(uy);
         A.macro[2 * ps + n] = value(pst);
     }
+    // Instability record: a non-finite velocity or pressure (NaN fails the
+    // compare) marks the step in flight; the host reads it at its next
+    // synchronising call. No trap: the step completes.
+    if (A.unst && !(fabs(value(ux) + value(uy) + value(pst)) < B(1e30)))
+        atomicMin(A.unst, (unsigned long long)(*A.step));
 
     // Breakup: the core (phi_1 >= 1/2) touches the carrier (phi_3 >= 1/2) at a
     // D2Q9 neighbour inside the channel; keep the first (step, y, x).
@@ -441,6 +465,37 @@ __global__ void __launch_bounds__(TX *tile_y<MODE>(), collide_min_blocks<MODE>()
         }
         if constexpr (CONSERVE) gd[(i * 9) * ps32 + n32] = S(pre.minus(post));
     }
+}
+
+template <typename T, int MODE, bool OPEN>
+__global__ void __launch_bounds__(TX *tile_y<MODE>(), collide_min_blocks<MODE>())
+    collide_kernel(LbmArgs<T, typename Compute<T, MODE>::type> A) {
+    collide_tile<T, MODE, OPEN>(A, blockIdx.x * TX, blockIdx.y * tile_y<MODE>());
+}
+
+// ---------------------------------------------------------------- batched
+// Many periodic channels in one launch: block b takes tile tiles[b] (instance,
+// tile origin) and that instance's arguments from tab. The collide's
+// arguments are staged in shared memory (read by every thread many times).
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) phase_batch_kernel(const BatchLbm<T> *tab,
+                                                          const BatchTile *tiles) {
+    const BatchTile t = tiles[blockIdx.x];
+    const BatchLbm<T> &b = tab[t.inst];
+    phase_tile<T, MODE>(b.lbm.P, b.lbm.g_src, b.phi1, b.phi2, b.k, b.pc, t.x0, t.y0, t.lead != 0);
+}
+
+template <typename T, int MODE, int TYM, int MINB>
+__global__ void __launch_bounds__(TX *TYM, MINB) collide_batch_kernel(const BatchLbm<T> *tab,
+                                                                      const BatchTile *tiles) {
+    static_assert(sizeof(LbmArgs<T>) % sizeof(int) == 0, "argument block copied as words");
+    __shared__ __align__(16) int raw[sizeof(LbmArgs<T>) / sizeof(int)];
+    const BatchTile t = tiles[blockIdx.x];
+    const int *src = reinterpret_cast<const int *>(&tab[t.inst].lbm);
+    for (int i = threadIdx.y * TX + threadIdx.x; i < (int)(sizeof(LbmArgs<T>) / sizeof(int)); i += TX * TYM)
+        raw[i] = src[i];
+    __syncthreads();
+    collide_tile<T, MODE, false, TYM>(*reinterpret_cast<const LbmArgs<T> *>(raw), t.x0, t.y0);
 }
 
 // ---------------------------------------------------------------- open ends
@@ -606,6 +661,30 @@ __global__ void plane_from_f64(const double *src, int nx, int ny, int pitch, T *
     dst[(long long)y * pitch + x] = T(src[(long long)y * nx + x]);
 }
 
+// psi' of a level-0 buffer in the FP64 exchange layout, and back (FP32: the
+// hi + lo pair of planes; FP64: one plane).
+template <typename T>
+__global__ void psi_to_f64(const T *src, int nx, int ny, int pitch, double *dst) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= nx || y >= ny) return;
+    const long long n = (long long)y * pitch + x;
+    double v = double(src[n]);
+    if constexpr (psi_planes<T>() == 2) v += double(src[(long long)pitch * ny + n]);
+    dst[(long long)y * nx + x] = v;
+}
+
+template <typename T>
+__global__ void psi_from_f64(const double *src, int nx, int ny, int pitch, T *dst, int comp) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= nx || y >= ny) return;
+    const long long n = (long long)y * pitch + x;
+    const double v = src[(long long)y * nx + x];
+    dst[n] = T(v);
+    if constexpr (psi_planes<T>() == 2) dst[(long long)pitch * ny + n] = comp ? T(v - double(T(v))) : T(0);
+}
+
 template <typename T>
 __global__ void phi3_to_f64(const T *p1, const T *p2, int nx, int ny, int pitch, double *dst) {
     int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -646,6 +725,29 @@ void launch_collide(int mode, const LbmArgs<T> &a, cudaStream_t s) {
     dim3 b(TX, TY), gr = grid2(a.P.nx, a.P.ny, b);
     if (a.open_x) FCD_MODE_SWITCH(mode, T, (collide_kernel<T, M, true><<<gr, b, 0, s>>>(a)));
     else FCD_MODE_SWITCH(mode, T, (collide_kernel<T, M, false><<<gr, b, 0, s>>>(a)));
+}
+
+template <typename T>
+void launch_phase_batch(int mode, const BatchLbm<T> *tab, const BatchTile *tiles, int ntiles,
+                        cudaStream_t s) {
+    if (ntiles <= 0) return;
+    dim3 b(32, 8);
+    FCD_MODE_SWITCH(mode, T, (phase_batch_kernel<T, M><<<ntiles, b, 0, s>>>(tab, tiles)));
+}
+
+template <typename T>
+void launch_collide_batch(int mode, int tile_h, const BatchLbm<T> *tab, const BatchTile *tiles,
+                          int ntiles, cudaStream_t s) {
+    if (ntiles <= 0) return;
+    if (tile_h == 4)
+        FCD_MODE_SWITCH(mode, T, (collide_batch_kernel<T, M, 4, (sizeof(T) == 8 ? 2 : 8)>
+                                  <<<ntiles, dim3(TX, 4), 0, s>>>(tab, tiles)));
+    else if (tile_h == 16)
+        FCD_MODE_SWITCH(mode, T, (collide_batch_kernel<T, M, 16, (sizeof(T) == 8 ? 1 : 2)>
+                                  <<<ntiles, dim3(TX, 16), 0, s>>>(tab, tiles)));
+    else
+        FCD_MODE_SWITCH(mode, T, (collide_batch_kernel<T, M, 8, (sizeof(T) == 8 ? 1 : 4)>
+                                  <<<ntiles, dim3(TX, 8), 0, s>>>(tab, tiles)));
 }
 
 void launch_collide_tangent(const LbmArgs<double, DualT> &a, cudaStream_t s) {
@@ -703,6 +805,19 @@ void launch_plane_from_f64(const double *src, int nx, int ny, int pitch, T *dst,
 }
 
 template <typename T>
+void launch_psi_to_f64(const T *src, int nx, int ny, int pitch, double *dst, cudaStream_t s) {
+    dim3 b(32, 8);
+    psi_to_f64<T><<<grid2(nx, ny, b), b, 0, s>>>(src, nx, ny, pitch, dst);
+}
+
+template <typename T>
+void launch_psi_from_f64(const double *src, int nx, int ny, int pitch, T *dst, int comp,
+                         cudaStream_t s) {
+    dim3 b(32, 8);
+    psi_from_f64<T><<<grid2(nx, ny, b), b, 0, s>>>(src, nx, ny, pitch, dst, comp);
+}
+
+template <typename T>
 void launch_phi3_to_f64(const T *p1, const T *p2, int nx, int ny, int pitch, double *dst,
                         cudaStream_t s) {
     dim3 b(32, 8);
@@ -712,6 +827,10 @@ void launch_phi3_to_f64(const T *p1, const T *p2, int nx, int ny, int pitch, dou
 #define FCD_INST(T)                                                                           \
     template void launch_phase<T>(int, const Phys<T> &, const void *, T *, T *, T *,          \
                                   PhaseCtl, cudaStream_t);                                    \
+    template void launch_phase_batch<T>(int, const BatchLbm<T> *, const BatchTile *, int,      \
+                                        cudaStream_t);                                         \
+    template void launch_collide_batch<T>(int, int, const BatchLbm<T> *, const BatchTile *,    \
+                                          int, cudaStream_t);                                  \
     template void launch_collide<T>(int, const LbmArgs<T> &, cudaStream_t);                    \
     template void launch_open_bc<T>(int, const Phys<T> &, const void *, const void *, void *,    \
                                     void *, double, double, cudaStream_t);                      \
@@ -724,7 +843,9 @@ void launch_phi3_to_f64(const T *p1, const T *p2, int nx, int ny, int pitch, dou
     template void launch_plane_to_f64<T>(const T *, int, int, int, double *, cudaStream_t);    \
     template void launch_plane_from_f64<T>(const double *, int, int, int, T *, cudaStream_t);  \
     template void launch_phi3_to_f64<T>(const T *, const T *, int, int, int, double *,         \
-                                        cudaStream_t);
+                                        cudaStream_t);                                         \
+    template void launch_psi_to_f64<T>(const T *, int, int, int, double *, cudaStream_t);      \
+    template void launch_psi_from_f64<T>(const double *, int, int, int, T *, int, cudaStream_t);
 FCD_INST(float)
 FCD_INST(double)
 

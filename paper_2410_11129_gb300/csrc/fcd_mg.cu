@@ -123,6 +123,70 @@ __device__ __forceinline__ T off9(const Node9<T> &n, PF pat, int y, int ny) {
     return s;
 }
 
+// FP32 level 0 with psi' = hi + lo (see psi_planes): the right-hand side and
+// the residual written per opposite link pair (a, opp a), a in {1, 2, 5, 6}:
+//   b = sum_pairs (c_a - c_opp)(e_a . H0 e_alpha)
+//   sum_a c_a d_a = sum_pairs [c_a (d_a + d_opp) + (c_opp - c_a) d_opp]
+// with d_a = psi'~_a - psi'_0 formed from the hi and lo parts separately.
+// Neighbouring values of psi' differ little, so the hi differences are exact
+// (Sterbenz) and every term scales with the local variation of psi' and k,
+// not with |psi'|; in a uniform medium c_opp - c_a and b are exactly 0. The
+// rounding of the residual is then ~1e-7 H0 instead of ~1e-5 H0.
+// first link of each opposite pair: 1, 2, 5, 6 for q = 0..3
+__host__ __device__ constexpr int pair_a(int q) { return q < 2 ? q + 1 : q + 3; }
+
+template <typename KF>
+__device__ __forceinline__ Node9<float> node9_pairs(KF kat, int y, int ny, float H0c, float H0s) {
+    Node9<float> n;
+    const float k0 = kat(0, 0);
+    n.diag = 0.f;
+#pragma unroll
+    for (int a = 1; a < 9; a++) {
+        const float ca = 3.f * wgt<float>(a) * (k0 + kat(cx(a), cy(a)));
+        n.c[a] = ca;
+        n.diag += ca;
+        const int yy = y + cy(a);
+        if ((yy < 0 || yy >= ny) && cx(a) == 0) n.diag += ca;  // psi'(ghost) = -psi'(node)
+    }
+    n.b = 0.f;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const int a = pair_a(q);
+        n.b += (n.c[a] - n.c[opp(a)]) * (float(cx(a)) * H0c + float(cy(a)) * H0s);
+    }
+    return n;
+}
+
+// b - L psi' at the node, psi' = hat + lat (accessors relative to the node).
+template <typename HF, typename LF>
+__device__ __forceinline__ float resid_pairs(const Node9<float> &n, HF hat, LF lat, int y, int ny) {
+    const float h0 = hat(0, 0), l0 = lat(0, 0);
+    auto dl = [&](int a) -> float {
+        const int yy = y + cy(a);
+        if (yy < 0 || yy >= ny) {  // mirrored ghost: psi'~ = -psi'(x + cx, y)
+            if (cx(a) == 0) return -(h0 + h0) - (l0 + l0);
+            return -(hat(cx(a), 0) + h0) - (lat(cx(a), 0) + l0);
+        }
+        return (hat(cx(a), cy(a)) - h0) + (lat(cx(a), cy(a)) - l0);
+    };
+    float sum = 0.f;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const int a = pair_a(q), o = opp(a);
+        const float da = dl(a), dop = dl(o);
+        sum += n.c[a] * (da + dop) + (n.c[o] - n.c[a]) * dop;
+    }
+    return n.b - sum;
+}
+
+// (hi, lo) += v, renormalised.
+__device__ __forceinline__ void comp_add(float &hi, float &lo, float v) {
+    float s, e;
+    two_sum(hi, __fadd_rn(lo, v), s, e);
+    hi = s;
+    lo = e;
+}
+
 // FP64 hierarchies keep the lattice level's node coefficients in COEF planes,
 // formed once per solve by coef0_kernel (k does not change within a solve):
 // the FP64 arithmetic of node9 and its division cost more than the loads on
@@ -216,31 +280,38 @@ __device__ void cycle_decide(MgCtl *ctl, cudaGraphConditionalHandle hw,
 // psi' in shared memory.
 constexpr int RX = 2 * 32 + 1 + 2, RY = 2 * 8 + 1 + 2;
 
-template <typename T>
-__global__ void __launch_bounds__(256) resid0_restrict(Level<T> L0, Level<TC> L1, T H0c, T H0s,
-                                                       MgCtl *ctl, cudaGraphConditionalHandle hw,
-                                                       cudaGraphConditionalHandle hi, int in_graph) {
+// One 32 x 8 block of level-1 cells (bx, by) of a grid of nblocks blocks;
+// grid_lead: the block that reports a solve that is already done.
+template <typename T, bool COMP>
+__device__ __forceinline__ void resid0_tile(const Level<T> &L0, const Level<TC> &L1, T H0c, T H0s,
+                                            MgCtl *ctl, cudaGraphConditionalHandle hw,
+                                            cudaGraphConditionalHandle hi, int in_graph, int bx,
+                                            int by, unsigned nblocks, bool grid_lead) {
     const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
     if (ctl->done) {
-        if (lead && blockIdx.x == 0 && blockIdx.y == 0) cycle_decide(ctl, hw, hi, in_graph);
+        if (lead && grid_lead) cycle_decide(ctl, hw, hi, in_graph);
         return;
     }
+    static_assert(!COMP || sizeof(T) == 4, "the hi + lo pair is an FP32 form");
     __shared__ T sk[RY][RX], sp[RY][RX];
+    __shared__ T sl[COMP ? RY : 1][COMP ? RX : 1];  // lo part of psi' (FP32 level 0)
     const int nx = L0.nx, ny = L0.ny, pitch = L0.pitch;
-    const int I0 = blockIdx.x * 32, J0 = blockIdx.y * 8;
+    const long long lo_off = (long long)pitch * ny;
+    const int I0 = bx * 32, J0 = by * 8;
     const int I1 = min(I0 + 32, L1.nx), J1 = min(J0 + 8, L1.ny);
     const int fx0 = L1.cx0[I0], fx1 = L1.cx0[I1], fy0 = L1.cy0[J0], fy1 = L1.cy0[J1];
     const int wx = fx1 - fx0 + 2, wy = fy1 - fy0 + 2;
     const T *psi = ctl->cur ? L0.r : L0.e;
     {  // all loads issued before the shared-memory stores
         constexpr int NL = (RX * RY + 255) / 256;
-        T kv[NL], pv[NL];
+        T kv[NL], pv[NL], lv[COMP ? NL : 1];
         const int t0 = threadIdx.y * 32 + threadIdx.x;
 #pragma unroll
         for (int q = 0; q < NL; q++) {
             const int t = t0 + q * 256;
             kv[q] = T(0);
             pv[q] = T(0);
+            if constexpr (COMP) lv[q] = T(0);
             if (t < wx * wy) {
                 const int lx = t % wx, ly = t / wx;
                 int gx = fx0 - 1 + lx;
@@ -249,6 +320,7 @@ __global__ void __launch_bounds__(256) resid0_restrict(Level<T> L0, Level<TC> L1
                 const int my = gy < 0 ? 0 : (gy >= ny ? ny - 1 : gy);
                 kv[q] = L0.k[(long long)my * pitch + gx];  // mirrored ghost rows
                 pv[q] = psi[(long long)my * pitch + gx];   // ghost rows never read
+                if constexpr (COMP) lv[q] = psi[lo_off + (long long)my * pitch + gx];
             }
         }
 #pragma unroll
@@ -257,6 +329,7 @@ __global__ void __launch_bounds__(256) resid0_restrict(Level<T> L0, Level<TC> L1
             if (t < wx * wy) {
                 sk[t / wx][t % wx] = kv[q];
                 sp[t / wx][t % wx] = pv[q];
+                if constexpr (COMP) sl[t / wx][t % wx] = lv[q];
             }
         }
     }
@@ -269,16 +342,24 @@ __global__ void __launch_bounds__(256) resid0_restrict(Level<T> L0, Level<TC> L1
             const int lx = i - fx0 + 1, ly = j - fy0 + 1;
             auto kat = [&](int dx, int dy) { return sk[ly + dy][lx + dx]; };
             auto pat = [&](int dx, int dy) { return sp[ly + dy][lx + dx]; };
-            Node9<T> nd;
-            if constexpr (keeps_coef<T>()) {
-                T inv;
-                coef_load(L0, (long long)j * pitch + i, nd, inv);
-                (void)kat;
+            T r;
+            if constexpr (COMP) {
+                auto lat = [&](int dx, int dy) { return sl[ly + dy][lx + dx]; };
+                Node9<float> nd = node9_pairs(kat, j, ny, H0c, H0s);
+                if (L0.rhs) nd.b = L0.rhs[(long long)j * pitch + i];
+                r = resid_pairs(nd, pat, lat, j, ny);
             } else {
-                nd = node9<T>(kat, j, ny, H0c, H0s);
+                Node9<T> nd;
+                if constexpr (keeps_coef<T>()) {
+                    T inv;
+                    coef_load(L0, (long long)j * pitch + i, nd, inv);
+                    (void)kat;
+                } else {
+                    nd = node9<T>(kat, j, ny, H0c, H0s);
+                }
+                const T bb = L0.rhs ? L0.rhs[(long long)j * pitch + i] : nd.b;
+                r = bb - (off9<T>(nd, pat, j, ny) - nd.diag * sp[ly][lx]);
             }
-            const T bb = L0.rhs ? L0.rhs[(long long)j * pitch + i] : nd.b;
-            const T r = bb - (off9<T>(nd, pat, j, ny) - nd.diag * sp[ly][lx]);
             sum += r;
             ksum += sk[ly][lx];
             const T ar = fabs(r);
@@ -303,12 +384,20 @@ __global__ void __launch_bounds__(256) resid0_restrict(Level<T> L0, Level<TC> L1
     __syncthreads();
     if (lead) {  // the last block to finish sees the whole norm and decides the cycle
         __threadfence();
-        if (atomicAdd(&ctl->blocks_done, 1u) == gridDim.x * gridDim.y - 1) {
+        if (atomicAdd(&ctl->blocks_done, 1u) == nblocks - 1) {
             __threadfence();
             ctl->blocks_done = 0;
             cycle_decide(ctl, hw, hi, in_graph);
         }
     }
+}
+
+template <typename T, bool COMP>
+__global__ void __launch_bounds__(256) resid0_restrict(Level<T> L0, Level<TC> L1, T H0c, T H0s,
+                                                       MgCtl *ctl, cudaGraphConditionalHandle hw,
+                                                       cudaGraphConditionalHandle hi, int in_graph) {
+    resid0_tile<T, COMP>(L0, L1, H0c, H0s, ctl, hw, hi, in_graph, blockIdx.x, blockIdx.y,
+                         gridDim.x * gridDim.y, blockIdx.x == 0 && blockIdx.y == 0);
 }
 
 __device__ void cycle_close(MgCtl *ctl);
@@ -322,27 +411,33 @@ __device__ void cycle_close(MgCtl *ctl);
 constexpr int QT = (SX / 2) * (SY / 2);  // threads of a smoothing tile
 constexpr int TILE_LOADS = ((SX + 2) * (SY + 2) + QT - 1) / QT;
 
-template <typename T>
-__global__ void __launch_bounds__(QT) smooth0(Level<T> L0, Level<TC> L1, int add_coarse,
-                                              int sweeps, T H0c, T H0s, MgCtl *ctl, int first) {
+// One 32 x 8 tile (bx, by) of a grid of nblocks tiles.
+template <typename T, bool COMP>
+__device__ __forceinline__ void smooth0_tile(const Level<T> &L0, const Level<TC> &L1,
+                                             int add_coarse, int sweeps, T H0c, T H0s, MgCtl *ctl,
+                                             int first, int bx, int by, unsigned nblocks) {
     const int tid = threadIdx.x;
     // first: the sweeps that open a solve (no residual known yet)
     if (block_skip(ctl, first != 0)) return;
+    static_assert(!COMP || sizeof(T) == 4, "the hi + lo pair is an FP32 form");
     __shared__ T sp[SY + 2][SX + 2];
+    __shared__ T sl[COMP ? SY + 2 : 1][COMP ? SX + 2 : 1];  // lo part of psi' (FP32)
     __shared__ T sk[SY + 2][SX + 2];
     const int nx = L0.nx, ny = L0.ny, pitch = L0.pitch;
-    const int x0 = blockIdx.x * SX, y0 = blockIdx.y * SY;
+    const long long lo_off = (long long)pitch * ny;
+    const int x0 = bx * SX, y0 = by * SY;
     const T *src = ctl->cur ? L0.r : L0.e;
     T *dst = ctl->cur ? L0.e : L0.r;
     __shared__ ProlongTile<T, SX + 2, SY + 2> pt;
     if (add_coarse) prolong_tile_load(pt, L0, x0 - 1, y0 - 1);
     {  // tile with its frozen one-cell ring: all loads issued before the stores
-        T kv[TILE_LOADS], pv[TILE_LOADS];
+        T kv[TILE_LOADS], pv[TILE_LOADS], lv[COMP ? TILE_LOADS : 1];
 #pragma unroll
         for (int q = 0; q < TILE_LOADS; q++) {
             const int t = tid + q * QT;
             kv[q] = T(0);
             pv[q] = T(0);
+            if constexpr (COMP) lv[q] = T(0);
             if (t < (SX + 2) * (SY + 2)) {
                 const int lx = t % (SX + 2), ly = t / (SX + 2);
                 int gx = x0 - 1 + lx;
@@ -351,7 +446,10 @@ __global__ void __launch_bounds__(QT) smooth0(Level<T> L0, Level<TC> L1, int add
                 const int gy = y0 - 1 + ly;
                 const int my = gy < 0 ? 0 : (gy >= ny ? ny - 1 : gy);
                 kv[q] = L0.k[(long long)my * pitch + gx];
-                if (gy >= 0 && gy < ny) pv[q] = src[(long long)gy * pitch + gx];
+                if (gy >= 0 && gy < ny) {
+                    pv[q] = src[(long long)gy * pitch + gx];
+                    if constexpr (COMP) lv[q] = src[lo_off + (long long)gy * pitch + gx];
+                }
             }
         }
 #pragma unroll
@@ -360,6 +458,7 @@ __global__ void __launch_bounds__(QT) smooth0(Level<T> L0, Level<TC> L1, int add
             if (t < (SX + 2) * (SY + 2)) {
                 sk[t / (SX + 2)][t % (SX + 2)] = kv[q];
                 sp[t / (SX + 2)][t % (SX + 2)] = pv[q];
+                if constexpr (COMP) sl[t / (SX + 2)][t % (SX + 2)] = lv[q];
             }
         }
     }
@@ -367,7 +466,10 @@ __global__ void __launch_bounds__(QT) smooth0(Level<T> L0, Level<TC> L1, int add
     if (add_coarse) {  // ghost rows are never read: the mirror is used instead
         for (int t = tid; t < (SX + 2) * (SY + 2); t += QT) {
             const int lx = t % (SX + 2), ly = t / (SX + 2), gy = y0 - 1 + ly;
-            if (gy >= 0 && gy < ny) sp[ly][lx] += prolong_at(pt, L1, lx, ly);
+            if (gy >= 0 && gy < ny) {
+                if constexpr (COMP) comp_add(sp[ly][lx], sl[ly][lx], prolong_at(pt, L1, lx, ly));
+                else sp[ly][lx] += prolong_at(pt, L1, lx, ly);
+            }
         }
         __syncthreads();
     }
@@ -386,7 +488,8 @@ __global__ void __launch_bounds__(QT) smooth0(Level<T> L0, Level<TC> L1, int add
                 coef_load(L0, (long long)y * pitch + x, nd[c], inv_diag[c]);
             } else {
                 auto kat = [&](int dx, int dy) { return sk[ly + dy][lx + dx]; };
-                nd[c] = node9<T>(kat, y, ny, H0c, H0s);
+                if constexpr (COMP) nd[c] = node9_pairs(kat, y, ny, H0c, H0s);
+                else nd[c] = node9<T>(kat, y, ny, H0c, H0s);
                 inv_diag[c] = T(1) / nd[c].diag;
             }
             if (L0.rhs) nd[c].b = L0.rhs[(long long)y * pitch + x];
@@ -397,25 +500,71 @@ __global__ void __launch_bounds__(QT) smooth0(Level<T> L0, Level<TC> L1, int add
         for (int c = 0; c < 4; c++) {
             const int lx = qx + (c & 1) + 1, ly = qy + (c >> 1) + 1, y = y0 + ly - 1;
             auto pat = [&](int dx, int dy) { return sp[ly + dy][lx + dx]; };
-            if (own[c]) sp[ly][lx] = (off9<T>(nd[c], pat, y, ny) - nd[c].b) * inv_diag[c];
+            if (own[c]) {
+                if constexpr (COMP) {  // correction form: dr/dpsi'_0 = diag, so psi'_0 -= r_0 / diag
+                    auto lat = [&](int dx, int dy) { return sl[ly + dy][lx + dx]; };
+                    const float r = resid_pairs(nd[c], pat, lat, y, ny);
+                    comp_add(sp[ly][lx], sl[ly][lx], -r * inv_diag[c]);
+                } else {
+                    sp[ly][lx] = (off9<T>(nd[c], pat, y, ny) - nd[c].b) * inv_diag[c];
+                }
+            }
             __syncthreads();
         }
     }
 #pragma unroll
     for (int c = 0; c < 4; c++) {
         const int lx = qx + (c & 1) + 1, ly = qy + (c >> 1) + 1;
-        if (own[c]) dst[(long long)(y0 + ly - 1) * pitch + (x0 + lx - 1)] = sp[ly][lx];
+        if (own[c]) {
+            const long long n = (long long)(y0 + ly - 1) * pitch + (x0 + lx - 1);
+            dst[n] = sp[ly][lx];
+            if constexpr (COMP) dst[lo_off + n] = sl[ly][lx];
+        }
     }
     __syncthreads();
     if (tid == 0) {
         __threadfence();
-        const unsigned total = gridDim.x * gridDim.y;
-        if (atomicAdd(&ctl->blocks_done, 1u) == total - 1) {
+        if (atomicAdd(&ctl->blocks_done, 1u) == nblocks - 1) {
             __threadfence();
             ctl->blocks_done = 0;
             cycle_close(ctl);
         }
     }
+}
+
+template <typename T, bool COMP>
+__global__ void __launch_bounds__(QT) smooth0(Level<T> L0, Level<TC> L1, int add_coarse,
+                                              int sweeps, T H0c, T H0s, MgCtl *ctl, int first) {
+    smooth0_tile<T, COMP>(L0, L1, add_coarse, sweeps, H0c, H0s, ctl, first, blockIdx.x, blockIdx.y,
+                          gridDim.x * gridDim.y);
+}
+
+// Host-side dispatch on the lattice level's form (FP32: one plane or the pair).
+template <typename T>
+static void launch_smooth0(const Level<T> &L0, const Level<TC> &L1, int add, int sweeps, T H0c,
+                           T H0s, MgCtl *ctl, int first, cudaStream_t s) {
+    const dim3 g((L0.nx + SX - 1) / SX, (L0.ny + SY - 1) / SY);
+    if constexpr (sizeof(T) == 4) {
+        if (L0.comp) {
+            smooth0<T, true><<<g, QT, 0, s>>>(L0, L1, add, sweeps, H0c, H0s, ctl, first);
+            return;
+        }
+    }
+    smooth0<T, false><<<g, QT, 0, s>>>(L0, L1, add, sweeps, H0c, H0s, ctl, first);
+}
+
+template <typename T>
+static void launch_resid0(const Level<T> &L0, const Level<TC> &L1, T H0c, T H0s, MgCtl *ctl,
+                          cudaGraphConditionalHandle hw, cudaGraphConditionalHandle hi, int in_graph,
+                          cudaStream_t s) {
+    const dim3 b(32, 8), g((L1.nx + 31) / 32, (L1.ny + 7) / 8);
+    if constexpr (sizeof(T) == 4) {
+        if (L0.comp) {
+            resid0_restrict<T, true><<<g, b, 0, s>>>(L0, L1, H0c, H0s, ctl, hw, hi, in_graph);
+            return;
+        }
+    }
+    resid0_restrict<T, false><<<g, b, 0, s>>>(L0, L1, H0c, H0s, ctl, hw, hi, in_graph);
 }
 
 // ------------------------------------------------------------- coarse levels
@@ -469,14 +618,14 @@ __device__ __forceinline__ T fv_resid_global(const Level<T> &L, const T *e, int 
 // coarse correction, output to L.e. KIND 2 (two-grid solve): zero initial
 // guess, output to L.e.
 template <typename T, int KIND>
-__global__ void __launch_bounds__(SX *SY) fv_smooth(Level<T> L, Level<T> C, int sweeps,
-                                                    MgCtl *ctl) {
+__device__ __forceinline__ void fv_smooth_tile(const Level<T> &L, const Level<T> &C, int sweeps,
+                                               MgCtl *ctl, int bx, int by) {
     constexpr bool POST = KIND == 1;
     if (block_skip(ctl)) return;
     __shared__ T se[SY + 2][SX + 2];
     __shared__ T sk[SY + 2][SX + 2];
     const int nx = L.nx, ny = L.ny, p = L.pitch;
-    const int x0 = blockIdx.x * SX, y0 = blockIdx.y * SY;
+    const int x0 = bx * SX, y0 = by * SY;
     __shared__ ProlongTile<T, SX + 2, SY + 2> pt;
     if (POST) prolong_tile_load(pt, L, x0 - 1, y0 - 1);
     for (int t = threadIdx.y * SX + threadIdx.x; t < (SX + 2) * (SY + 2); t += SX * SY) {
@@ -527,12 +676,19 @@ __global__ void __launch_bounds__(SX *SY) fv_smooth(Level<T> L, Level<T> C, int 
     if (own) (KIND == 0 ? L.r : L.e)[(long long)J * p + I] = se[ly][lx];
 }
 
+template <typename T, int KIND>
+__global__ void __launch_bounds__(SX *SY) fv_smooth(Level<T> L, Level<T> C, int sweeps,
+                                                    MgCtl *ctl) {
+    fv_smooth_tile<T, KIND>(L, C, sweeps, ctl, blockIdx.x, blockIdx.y);
+}
+
 // Residual of a grid-wide level (pre-smoothed iterate in F.r) summed onto the
 // next level, and the next level's permeability (area-weighted mean).
 template <typename T>
-__global__ void __launch_bounds__(256) fv_resid_restrict(Level<T> F, Level<T> C, MgCtl *ctl) {
+__device__ __forceinline__ void fv_resid_tile(const Level<T> &F, const Level<T> &C, MgCtl *ctl,
+                                              int bx, int by) {
     if (cycle_skip(ctl)) return;
-    const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y;
+    const int I = bx * 32 + threadIdx.x, J = by * 8 + threadIdx.y;
     if (I >= C.nx || J >= C.ny) return;
     T sr = T(0), sk = T(0);
     for (int j = C.cy0[J]; j < C.cy0[J + 1]; j++)
@@ -542,6 +698,11 @@ __global__ void __launch_bounds__(256) fv_resid_restrict(Level<T> F, Level<T> C,
         }
     C.b[(long long)J * C.pitch + I] = sr;
     C.k[(long long)J * C.pitch + I] = sk / (C.wx[I] * C.wy[J]);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) fv_resid_restrict(Level<T> F, Level<T> C, MgCtl *ctl) {
+    fv_resid_tile<T>(F, C, ctl, blockIdx.x, blockIdx.y);
 }
 
 // ---- levels lc .. nl-1 inside one block, resident in shared memory.
@@ -583,8 +744,7 @@ __device__ __forceinline__ void cta_gs(const Level<T> &L, const CtaView<T> &V, i
 }
 
 template <typename T>
-__global__ void __launch_bounds__(CTA_THREADS) coarse_cta(const Level<T> *lv, int lc, int nl,
-                                                         MgCtl *ctl) {
+__device__ __forceinline__ void coarse_cta_block(const Level<T> *lv, int lc, int nl, MgCtl *ctl) {
     if (cycle_skip(ctl)) return;
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ Level<T> L[MAX_LEVELS];
@@ -689,6 +849,12 @@ __global__ void __launch_bounds__(CTA_THREADS) coarse_cta(const Level<T> *lv, in
         const int nx = L[lc].nx, n = nx * L[lc].ny;
         for (int t = tid; t < n; t += nthr) L[lc].e[(long long)(t / nx) * L[lc].pitch + t % nx] = V.e[t];
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(CTA_THREADS) coarse_cta(const Level<T> *lv, int lc, int nl,
+                                                         MgCtl *ctl) {
+    coarse_cta_block<T>(lv, lc, nl, ctl);
 }
 
 // Start of a cycle (one thread, after the lattice residual is complete):
@@ -810,7 +976,7 @@ static void interp_table(const std::vector<double> &fine, const std::vector<doub
 template <typename T>
 MgHost<T> *mg_create(int nx, int ny, int pitch, T *k0, T *psiA, T *psiB, MgCtl *ctl,
                      void *(*alloc)(size_t, void *), void (*release)(void *, void *), void *user,
-                     char *err, size_t errlen) {
+                     char *err, size_t errlen, int comp) {
     MgHost<T> *m = new MgHost<T>();
     m->alloc = alloc;
     m->release = release;
@@ -923,6 +1089,7 @@ MgHost<T> *mg_create(int nx, int ny, int pitch, T *k0, T *psiA, T *psiB, MgCtl *
         L.k = k0;
         L.e = psiA;
         L.r = psiB;
+        L.comp = sizeof(T) == 4 && comp ? 1 : 0;
         if (keeps_coef<T>()) L.coef = up.put<T>(nullptr, (size_t)COEF * pitch * ny * sizeof(T));
     }
     for (int l = 0; l < m->nl; l++) {
@@ -960,10 +1127,8 @@ static dim3 g2(int nx, int ny, dim3 b) { return dim3((nx + b.x - 1) / b.x, (ny +
 template <typename T>
 void mg_cycle_head(MgHost<T> *m, T H0c, T H0s, cudaGraphConditionalHandle hw,
                    cudaGraphConditionalHandle hi, int in_graph, cudaStream_t s) {
-    dim3 b(32, 8);
     const std::vector<Level<TC>> &lv = m->lv;
-    resid0_restrict<T><<<g2(lv[1].nx, lv[1].ny, b), b, 0, s>>>(m->L0, lv[1], H0c, H0s, m->ctl,
-                                                               hw, hi, in_graph);
+    launch_resid0<T>(m->L0, lv[1], H0c, H0s, m->ctl, hw, hi, in_graph, s);
 }
 
 template <typename T>
@@ -977,28 +1142,23 @@ void mg_cycle_rest(MgHost<T> *m, T H0c, T H0s, cudaStream_t s) {
     coarse_cta<TC><<<1, CTA_THREADS, m->cta_smem, s>>>(m->d_lv, m->lc, m->nl, m->ctl);
     for (int l = m->lc - 1; l >= 1; l--)
         fv_smooth<TC, 1><<<g2(lv[l].nx, lv[l].ny, bs), bs, 0, s>>>(lv[l], lv[l + 1], NU_POST, m->ctl);
-    smooth0<T><<<g2(m->L0.nx, m->L0.ny, bs), QT, 0, s>>>(m->L0, lv[1], 1, NU_FINE, H0c, H0s, m->ctl,
-                                                          0);
+    launch_smooth0<T>(m->L0, lv[1], 1, NU_FINE, H0c, H0s, m->ctl, 0, s);
 }
 
 template <typename T>
 void mg_cycle_smooth(MgHost<T> *m, T H0c, T H0s, cudaStream_t s) {
-    dim3 bs(SX, SY);
     const std::vector<Level<TC>> &lv = m->lv;
-    smooth0<T><<<g2(m->L0.nx, m->L0.ny, bs), QT, 0, s>>>(m->L0, lv[1], 0, NU_SMOOTH_ONLY, H0c, H0s,
-                                                          m->ctl, 0);
+    launch_smooth0<T>(m->L0, lv[1], 0, NU_SMOOTH_ONLY, H0c, H0s, m->ctl, 0, s);
 }
 
 template <typename T>
 void mg_presmooth(MgHost<T> *m, T H0c, T H0s, cudaStream_t s) {
-    dim3 bs(SX, SY);
     const std::vector<Level<TC>> &lv = m->lv;
     if (keeps_coef<T>()) {  // the solve's node coefficients, before its first sweep
         dim3 b(32, 8);
         coef0_kernel<T><<<g2(m->L0.nx, m->L0.ny, b), b, 0, s>>>(m->L0, H0c, H0s);
     }
-    smooth0<T><<<g2(m->L0.nx, m->L0.ny, bs), QT, 0, s>>>(m->L0, lv[1], 0, NU_SMOOTH_ONLY, H0c, H0s,
-                                                          m->ctl, 1);
+    launch_smooth0<T>(m->L0, lv[1], 0, NU_SMOOTH_ONLY, H0c, H0s, m->ctl, 1, s);
 }
 
 template <typename T>
@@ -1006,8 +1166,7 @@ void mg_cycle_twogrid(MgHost<T> *m, T H0c, T H0s, cudaStream_t s) {
     dim3 bs(SX, SY);
     const std::vector<Level<TC>> &lv = m->lv;
     fv_smooth<TC, 2><<<g2(lv[1].nx, lv[1].ny, bs), bs, 0, s>>>(lv[1], lv[1], NU_TWOGRID, m->ctl);
-    smooth0<T><<<g2(m->L0.nx, m->L0.ny, bs), QT, 0, s>>>(m->L0, lv[1], 1, NU_FINE, H0c, H0s, m->ctl,
-                                                          0);
+    launch_smooth0<T>(m->L0, lv[1], 1, NU_FINE, H0c, H0s, m->ctl, 0, s);
 }
 
 template <typename T>
@@ -1015,6 +1174,231 @@ int mg_kernels_per_cycle(const MgHost<T> *m) { return 2 + 3 * (m->lc - 1); }  //
 
 template <typename T>
 int mg_levels(const MgHost<T> *m) { return m->nl; }
+
+// ------------------------------------------------------------ batched solves
+// The potential solves of many FP32 channels driven by one fixed set of
+// kernels: each kernel runs over a work list of (instance, tile) entries that
+// spans every instance, and each block does its instance's part of the cycle
+// its instance's control block chose (blocks of instances in another mode, or
+// already converged, return at once). Per-instance completion is counted per
+// control block against the instance's own tile count; the last block of the
+// whole residual launch keeps the batch's loop going while any solve is.
+struct MgBatchInst {
+    Level<float> L0;
+    const Level<TC> *lv;  // the instance's device level table (entry 0 unused)
+    int nl, lc;
+    MgCtl *ctl;
+    float H0c, H0s;
+    unsigned n0;  // level-0 smoothing tiles
+    unsigned n1;  // residual blocks (32 x 8 level-1 cells)
+};
+struct MgBatchTile {
+    int inst, bx, by, lvl;
+};
+struct MgBatchCtl {
+    unsigned blocks_done;
+    unsigned any;  // after a residual launch: 1 while some solve goes on
+};
+
+constexpr int BS_FIRST = 0;  // the sweeps that open every solve
+constexpr int BS_CYCLE = 1;  // the lattice part that ends every cycle
+
+__global__ void __launch_bounds__(QT) smooth0_batch(const MgBatchInst *tab, const MgBatchTile *tiles,
+                                                    int kind) {
+    const MgBatchTile t = tiles[blockIdx.x];
+    const MgBatchInst &I = tab[t.inst];
+    int add = 0, sweeps = NU_SMOOTH_ONLY;
+    if (kind == BS_CYCLE) {  // V-cycle and two-grid cycle: coarse correction; else sweeps only
+        const int m = I.ctl->mode;
+        add = m == 0 || m == 2;
+        sweeps = add ? NU_FINE : NU_SMOOTH_ONLY;
+    }
+    if (I.L0.comp)
+        smooth0_tile<float, true>(I.L0, I.lv[1], add, sweeps, I.H0c, I.H0s, I.ctl, kind == BS_FIRST,
+                                  t.bx, t.by, I.n0);
+    else
+        smooth0_tile<float, false>(I.L0, I.lv[1], add, sweeps, I.H0c, I.H0s, I.ctl, kind == BS_FIRST,
+                                   t.bx, t.by, I.n0);
+}
+
+__global__ void __launch_bounds__(256) resid0_batch(const MgBatchInst *tab, const MgBatchTile *tiles,
+                                                    MgBatchCtl *bc, int ninst,
+                                                    cudaGraphConditionalHandle hw, int in_graph) {
+    const MgBatchTile t = tiles[blockIdx.x];
+    const MgBatchInst &I = tab[t.inst];
+    if (I.L0.comp)
+        resid0_tile<float, true>(I.L0, I.lv[1], I.H0c, I.H0s, I.ctl, 0, 0, 0, t.bx, t.by, I.n1, false);
+    else
+        resid0_tile<float, false>(I.L0, I.lv[1], I.H0c, I.H0s, I.ctl, 0, 0, 0, t.bx, t.by, I.n1, false);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        __threadfence();
+        if (atomicAdd(&bc->blocks_done, 1u) == gridDim.x - 1) {
+            __threadfence();
+            bc->blocks_done = 0;
+            unsigned any = 0;
+            for (int i = 0; i < ninst; i++) any |= ((volatile MgCtl *)tab[i].ctl)->done ? 0u : 1u;
+            bc->any = any;
+            if (in_graph) cudaGraphSetConditional(hw, any);
+        }
+    }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(SX *SY) fv_smooth_batch(const MgBatchInst *tab,
+                                                          const MgBatchTile *tiles, int sweeps) {
+    const MgBatchTile t = tiles[blockIdx.x];
+    const MgBatchInst &I = tab[t.inst];
+    if (I.ctl->mode != (KIND == 2 ? 2 : 0)) return;
+    const Level<TC> &L = I.lv[t.lvl];
+    fv_smooth_tile<TC, KIND>(L, KIND == 2 ? L : I.lv[t.lvl + 1], sweeps, I.ctl, t.bx, t.by);
+}
+
+__global__ void __launch_bounds__(256) fv_resid_batch(const MgBatchInst *tab, const MgBatchTile *tiles) {
+    const MgBatchTile t = tiles[blockIdx.x];
+    const MgBatchInst &I = tab[t.inst];
+    if (I.ctl->mode != 0) return;
+    fv_resid_tile<TC>(I.lv[t.lvl], I.lv[t.lvl + 1], I.ctl, t.bx, t.by);
+}
+
+__global__ void __launch_bounds__(CTA_THREADS) coarse_batch(const MgBatchInst *tab, const int *inst) {
+    const MgBatchInst &I = tab[inst[blockIdx.x]];
+    if (I.ctl->mode != 0) return;
+    coarse_cta_block<TC>(I.lv, I.lc, I.nl, I.ctl);
+}
+
+struct MgBatch {
+    int ninst = 0, maxlc = 1;
+    MgBatchInst *d_tab = nullptr;
+    MgBatchCtl *d_ctl = nullptr;
+    int *d_inst = nullptr;                     // every instance (coarse blocks)
+    MgBatchTile *d_t0 = nullptr, *d_t1 = nullptr, *d_tl1 = nullptr;
+    int n_t0 = 0, n_t1 = 0, n_tl1 = 0;         // level-0 tiles, residual blocks, level-1 fv tiles
+    std::vector<MgBatchTile *> d_fvs, d_fvr;   // per level l >= 1: fv tiles of l, restriction to l + 1
+    std::vector<int> n_fvs, n_fvr;
+    size_t cta_smem = 0;
+    std::vector<void *> mem;
+    void (*release)(void *, void *) = nullptr;
+    void *user = nullptr;
+};
+
+MgBatch *mg_batch_create(const std::vector<MgHost<float> *> &ms, const std::vector<float> &H0c,
+                         const std::vector<float> &H0s, void *(*alloc)(size_t, void *),
+                         void (*release)(void *, void *), void *user, char *err, size_t errlen) {
+    MgBatch *b = new MgBatch();
+    b->release = release;
+    b->user = user;
+    b->ninst = (int)ms.size();
+    Uploader up{alloc, user, &b->mem};
+    std::vector<MgBatchInst> tab;
+    std::vector<MgBatchTile> t0, t1, tl1;
+    std::vector<int> ids;
+    for (int i = 0; i < b->ninst; i++) {
+        const MgHost<float> *m = ms[i];
+        MgBatchInst I;
+        std::memset(&I, 0, sizeof I);
+        I.L0 = m->L0;
+        I.lv = m->d_lv;
+        I.nl = m->nl;
+        I.lc = m->lc;
+        I.ctl = m->ctl;
+        I.H0c = H0c[i];
+        I.H0s = H0s[i];
+        const int gx0 = (m->L0.nx + SX - 1) / SX, gy0 = (m->L0.ny + SY - 1) / SY;
+        const int gx1 = (m->lv[1].nx + 31) / 32, gy1 = (m->lv[1].ny + 7) / 8;
+        const int gxl = (m->lv[1].nx + SX - 1) / SX, gyl = (m->lv[1].ny + SY - 1) / SY;
+        I.n0 = (unsigned)(gx0 * gy0);
+        I.n1 = (unsigned)(gx1 * gy1);
+        tab.push_back(I);
+        ids.push_back(i);
+        for (int y = 0; y < gy0; y++)
+            for (int x = 0; x < gx0; x++) t0.push_back({i, x, y, 0});
+        for (int y = 0; y < gy1; y++)
+            for (int x = 0; x < gx1; x++) t1.push_back({i, x, y, 1});
+        for (int y = 0; y < gyl; y++)
+            for (int x = 0; x < gxl; x++) tl1.push_back({i, x, y, 1});
+        b->maxlc = std::max(b->maxlc, m->lc);
+        b->cta_smem = std::max(b->cta_smem, m->cta_smem);
+    }
+    b->d_fvs.assign(b->maxlc, nullptr);
+    b->d_fvr.assign(b->maxlc, nullptr);
+    b->n_fvs.assign(b->maxlc, 0);
+    b->n_fvr.assign(b->maxlc, 0);
+    for (int l = 1; l < b->maxlc; l++) {
+        std::vector<MgBatchTile> fs, fr;
+        for (int i = 0; i < b->ninst; i++) {
+            const MgHost<float> *m = ms[i];
+            if (m->lc <= l) continue;  // level l runs inside this instance's coarse block
+            const Level<TC> &L = m->lv[l], &C = m->lv[l + 1];
+            for (int y = 0; y < (L.ny + SY - 1) / SY; y++)
+                for (int x = 0; x < (L.nx + SX - 1) / SX; x++) fs.push_back({i, x, y, l});
+            for (int y = 0; y < (C.ny + 7) / 8; y++)
+                for (int x = 0; x < (C.nx + 31) / 32; x++) fr.push_back({i, x, y, l});
+        }
+        b->n_fvs[l] = (int)fs.size();
+        b->n_fvr[l] = (int)fr.size();
+        b->d_fvs[l] = up.put<MgBatchTile>(fs.data(), fs.size() * sizeof(MgBatchTile));
+        b->d_fvr[l] = up.put<MgBatchTile>(fr.data(), fr.size() * sizeof(MgBatchTile));
+    }
+    b->d_tab = up.put<MgBatchInst>(tab.data(), tab.size() * sizeof(MgBatchInst));
+    b->d_inst = up.put<int>(ids.data(), ids.size() * sizeof(int));
+    b->d_t0 = up.put<MgBatchTile>(t0.data(), t0.size() * sizeof(MgBatchTile));
+    b->d_t1 = up.put<MgBatchTile>(t1.data(), t1.size() * sizeof(MgBatchTile));
+    b->d_tl1 = up.put<MgBatchTile>(tl1.data(), tl1.size() * sizeof(MgBatchTile));
+    MgBatchCtl zero{0u, 0u};
+    b->d_ctl = up.put<MgBatchCtl>(&zero, sizeof zero);
+    b->n_t0 = (int)t0.size();
+    b->n_t1 = (int)t1.size();
+    b->n_tl1 = (int)tl1.size();
+    if (cudaFuncSetAttribute(coarse_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)CTA_SMEM_MAX) != cudaSuccess) {
+        snprintf(err, errlen, "batched multigrid: cannot reserve the coarse levels' shared memory");
+        mg_batch_destroy(b);
+        return nullptr;
+    }
+    if (!up.ok) {
+        snprintf(err, errlen, "batched multigrid: device allocation or upload failed");
+        mg_batch_destroy(b);
+        return nullptr;
+    }
+    return b;
+}
+
+void mg_batch_destroy(MgBatch *b) {
+    if (!b) return;
+    for (void *p : b->mem) b->release(p, b->user);
+    delete b;
+}
+
+void mg_batch_presmooth(MgBatch *b, cudaStream_t s) {
+    smooth0_batch<<<b->n_t0, QT, 0, s>>>(b->d_tab, b->d_t0, BS_FIRST);
+}
+
+// One pass of the loop body: every instance's cycle head, then the kernels of
+// each kind of cycle (V-cycle, two-grid cycle, lattice sweeps), each acting
+// only for the instances whose head chose it.
+void mg_batch_body(MgBatch *b, cudaGraphConditionalHandle hw, int in_graph, cudaStream_t s) {
+    dim3 b2(32, 8);
+    resid0_batch<<<b->n_t1, b2, 0, s>>>(b->d_tab, b->d_t1, b->d_ctl, b->ninst, hw, in_graph);
+    for (int l = 1; l < b->maxlc; l++) {
+        fv_smooth_batch<0><<<b->n_fvs[l], dim3(SX, SY), 0, s>>>(b->d_tab, b->d_fvs[l], NU_PRE);
+        fv_resid_batch<<<b->n_fvr[l], b2, 0, s>>>(b->d_tab, b->d_fvr[l]);
+    }
+    coarse_batch<<<b->ninst, CTA_THREADS, b->cta_smem, s>>>(b->d_tab, b->d_inst);
+    for (int l = b->maxlc - 1; l >= 1; l--)
+        fv_smooth_batch<1><<<b->n_fvs[l], dim3(SX, SY), 0, s>>>(b->d_tab, b->d_fvs[l], NU_POST);
+    fv_smooth_batch<2><<<b->n_tl1, dim3(SX, SY), 0, s>>>(b->d_tab, b->d_tl1, NU_TWOGRID);
+    smooth0_batch<<<b->n_t0, QT, 0, s>>>(b->d_tab, b->d_t0, BS_CYCLE);
+}
+
+int mg_batch_body_kernels(const MgBatch *b) { return 4 + 3 * (b->maxlc - 1); }
+
+int mg_batch_any(MgBatch *b, cudaStream_t s) {
+    MgBatchCtl c;
+    if (cudaMemcpyAsync(&c, b->d_ctl, sizeof c, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return -1;
+    return c.any ? 1 : 0;
+}
 
 // ------------------------------------------------------------ tangent solves
 template <typename T>
@@ -1115,7 +1499,7 @@ void mg_psi_io(MgHost<double> *m, int op, double *plane, double *prev, cudaStrea
 #define FCD_MG_INST(T)                                                                          \
     template MgHost<T> *mg_create<T>(int, int, int, T *, T *, T *, MgCtl *,                     \
                                      void *(*)(size_t, void *), void (*)(void *, void *), void *, \
-                                     char *, size_t);                                           \
+                                     char *, size_t, int);                                      \
     template void mg_destroy<T>(MgHost<T> *);                                                   \
     template void mg_cycle_head<T>(MgHost<T> *, T, T, cudaGraphConditionalHandle,                \
                                    cudaGraphConditionalHandle, int, cudaStream_t);              \

@@ -20,10 +20,14 @@ namespace {
 
 constexpr long long NOALLOC_MAX_NODES = 1ll << 19;  // 524,288 lattice nodes
 constexpr int NOALLOC_MAX_NX = 16384;
-constexpr int OBS_COLS = 12;  // per-column record of the observables reduction
 constexpr size_t OBSOUT_DOUBLES = (sizeof(ObsOut) + sizeof(double) - 1) / sizeof(double);
-constexpr size_t NOALLOC_DOUBLES =
-    2 * NOALLOC_MAX_NODES + (size_t)OBS_COLS * NOALLOC_MAX_NX + OBSOUT_DOUBLES;  // 9.6 MiB
+// The reduction's layout (phase planes, then column records) for the largest
+// admitted lattice, followed by the result block: 9.5 MiB.
+constexpr size_t NOALLOC_REDUCE_DOUBLES = 2ull * NOALLOC_MAX_NODES + (size_t)OBS_COLS * NOALLOC_MAX_NX;
+constexpr size_t NOALLOC_DOUBLES = NOALLOC_REDUCE_DOUBLES + OBSOUT_DOUBLES;
+static_assert(observe_scratch_doubles_of(NOALLOC_MAX_NX, NOALLOC_MAX_NODES / NOALLOC_MAX_NX) <=
+                  NOALLOC_REDUCE_DOUBLES,
+              "every admitted lattice's reduction scratch fits in front of the result block");
 
 // Scratch shared by every call: phase planes, column records, result block.
 static __device__ __align__(256) double noalloc_scratch[NOALLOC_DOUBLES];
@@ -45,10 +49,11 @@ fcd_status noalloc_fail(fcd_status st, const char *msg) {
 
 using namespace fcd;
 
-extern "C" fcd_status fcd_observe_populations_noalloc(const double *g, int nx, int ny,
+extern "C" fcd_status fcd_observe_populations_noalloc(const double *g, int nx, int ny, int open_x,
                                                       void *cuda_stream, fcd_obs *out) {
     if (!g || !out) return noalloc_fail(FCD_EINVAL, "null population or output pointer");
     if (nx < 4 || ny < 2) return noalloc_fail(FCD_EINVAL, "need nx >= 4 and ny >= 2");
+    if (open_x != 0 && open_x != 1) return noalloc_fail(FCD_EINVAL, "open_x must be 0 or 1");
     if (nx > NOALLOC_MAX_NX || (long long)nx * ny > NOALLOC_MAX_NODES)
         return noalloc_fail(FCD_EINVAL,
                             "lattice larger than the static scratch (nx <= 16384, nx*ny <= 524288)");
@@ -72,11 +77,11 @@ extern "C" fcd_status fcd_observe_populations_noalloc(const double *g, int nx, i
     P.ny = ny;
     P.pitch = nx;  // the FP64 exchange layout is unpadded
     P.ps = (long long)nx * ny;
-    const long long N = P.ps;
-    ObsOut *res = reinterpret_cast<ObsOut *>(scratch + 2 * N + (size_t)OBS_COLS * nx);
+    ObsOut *res = reinterpret_cast<ObsOut *>(scratch + observe_scratch_doubles_of(nx, ny));
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    // launch_observe clears the result block before its kernels run
-    launch_observe<double>(MODE_FP64, P, g, scratch, res, s);
+    // launch_observe clears the result block before its kernels run; open_x
+    // selects the open channel's frame (no periodic seam, no wrap in x)
+    launch_observe<double>(MODE_FP64, P, g, scratch, res, s, open_x);
     ObsOut r;
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(&r, res, sizeof r, cudaMemcpyDeviceToHost, s);

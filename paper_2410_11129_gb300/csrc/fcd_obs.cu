@@ -10,7 +10,7 @@
 
 namespace fcd {
 
-constexpr int COLS = 12;  // per-column record: see obs_columns
+constexpr int COLS = OBS_COLS;  // per-column record: see obs_columns
 
 template <int MODE>
 struct StoreO { using type = float; };
@@ -245,7 +245,7 @@ void launch_observe(int mode, const Phys<T> &P, const void *g, double *scratch, 
     obs_final<<<1, FIN, 0, s>>>(P.nx, col, out, open_x);
 }
 
-size_t observe_scratch_doubles(int nx, int ny) { return 2ull * nx * ny + (size_t)COLS * nx; }
+size_t observe_scratch_doubles(int nx, int ny) { return observe_scratch_doubles_of(nx, ny); }
 
 template void launch_observe<float>(int, const Phys<float> &, const void *, double *, ObsOut *,
                                     cudaStream_t, int);

@@ -108,13 +108,16 @@ _SIGS = {
     "fcd_set_profiling": (C.c_int, [C.c_void_p, C.c_int]),
     "fcd_last_step_profile": (C.c_int, [C.c_void_p, DP]),
     "fcd_last_error": (C.c_char_p, [C.c_void_p]),
-    "fcd_observe_populations_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p,
-                                                   C.POINTER(fcd_obs)]),
+    "fcd_observe_populations_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int,
+                                                   C.c_void_p, C.POINTER(fcd_obs)]),
     "fcd_batch_create": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),
     "fcd_batch_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
     "fcd_batch_step": (C.c_int, [C.c_void_p, C.c_long]),
     "fcd_batch_observables": (C.c_int, [C.c_void_p, C.POINTER(fcd_obs)]),
     "fcd_batch_size": (C.c_int, [C.c_void_p]),
+    "fcd_batch_set_mode": (C.c_int, [C.c_void_p, C.c_int]),
+    "fcd_batch_tuning": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                   C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_int]),
     "fcd_batch_instance": (C.c_void_p, [C.c_void_p, C.c_int]),
     "fcd_batch_last_error": (C.c_char_p, [C.c_void_p]),
     "fcd_batch_destroy": (None, [C.c_void_p]),
@@ -500,6 +503,7 @@ def _final_state_function():
                 ch.close()
                 raise
             ctx.ch = ch
+            ctx.theta_device = theta.device
             return torch.from_numpy(f), torch.from_numpy(g)
 
         @staticmethod
@@ -511,7 +515,8 @@ def _final_state_function():
             finally:
                 ch.close()
                 ctx.ch = None
-            return torch.tensor(o["grad"], dtype=torch.float64), None, None, None
+            return (torch.tensor(o["grad"], dtype=torch.float64, device=ctx.theta_device),
+                    None, None, None)
 
     return FinalState
 
@@ -593,6 +598,21 @@ class Batch:
         if st != FCD_OK and st not in allow:
             raise FcdError(st, load().fcd_batch_last_error(self.h).decode())
         return [o.as_dict() for o in out]
+
+    def tuning(self):
+        """{"mode": 1 batched kernels, 0 instance streams, -1 still timing;
+        "batched": instances on the batched kernels; "groups"; "tile_h": the
+        collide tile height per group}."""
+        md, nb, ng, th = C.c_int(0), C.c_int(0), C.c_int(0), (C.c_int * 64)()
+        load().fcd_batch_tuning(self.h, C.byref(md), C.byref(nb), C.byref(ng), th, 64)
+        return {"mode": md.value, "batched": nb.value, "groups": ng.value,
+                "tile_h": list(th)[:ng.value]}
+
+    def set_mode(self, mode):
+        """1: batched kernels, 0: every instance on its own stream, -1: time both again."""
+        st = load().fcd_batch_set_mode(self.h, int(mode))
+        if st != FCD_OK:
+            raise FcdError(st, load().fcd_batch_last_error(self.h).decode())
 
     def close(self):
         if getattr(self, "h", None):

@@ -282,6 +282,13 @@ def test_final_state_autograd_against_cpu_adjoint(fcd, orc):
     assert abs(loss.item() - lc.item()) <= 1e-10 * max(1.0, abs(lc.item()))
     ref, got = theta.grad.numpy(), th.grad.numpy()
     assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max(), (got, ref)
+    # a GPU-resident theta gets its gradient on its own device
+    thd = torch.tensor(fcd.parameters_of(cfg), dtype=torch.float64, device="cuda",
+                       requires_grad=True)
+    f, g = fcd.final_state(thd, cfg, STEPS, checkpoint=8)
+    ((f * S).sum() + (g * R).sum()).backward()
+    assert thd.grad.device == thd.device
+    assert np.abs(thd.grad.cpu().numpy() - got).max() <= 1e-12 * np.abs(got).max()
 
 
 def test_adjoint_alpha_derivative_vanishes_by_symmetry(fcd):

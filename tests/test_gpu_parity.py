@@ -138,7 +138,10 @@ def test_open_channel_poiseuille_gpu(fcd):
 @pytest.mark.parametrize("prec", ["fp32", "fp32_offset"])
 @pytest.mark.parametrize("open_x", [0, 1])
 def test_fp32_forms_against_fp64_oracle(orc, fcd, prec, open_x):
-    cfg = parity_cfg(mag_tol=1e-5, open_x=open_x)
+    """Both FP32 storage forms within 1e-4 of the FP64 oracle after 200 steps:
+    phase fields absolute, velocity relative to its maximum, observables. The
+    FP32 potential (hi + lo pair) is solved to 1e-6."""
+    cfg = parity_cfg(mag_tol=1e-6, open_x=open_x)
     sim = orc.Sim(dict(cfg, mag_tol=1e-13))
     from paper_2410_11129_gb300 import fcd as F
     ch = F.Channel(dict(cfg, precision=prec))
@@ -150,18 +153,20 @@ def test_fp32_forms_against_fp64_oracle(orc, fcd, prec, open_x):
     err_u = np.abs(ch.field("ux") - sim.macro[0]).max() / umax
     ob, oo = ch.observe(), sim.observe()
     print(prec, "phi", err_phi, "u_rel", err_u, {k: ob[k] - oo[k] for k in ("T_o", "T_i", "xc_shell")})
-    assert err_phi <= 1e-4 and err_u <= 1e-3
+    assert err_phi <= 1e-4 and err_u <= 1e-4
     for k in ("T_o", "T_i", "xc_core", "yc_core", "xc_shell", "yc_shell"):
         assert abs(ob[k] - oo[k]) <= 1e-4 * max(1.0, abs(oo[k])), k
     ch.close()
 
 
 def test_mass_conservation_gpu(fcd):
-    """FP64: exact to round-off. FP32 storage rounds every population every
-    step, with a bias that does not average out in a quasi-steady state; the
-    drift (about 1e-5 over 300 steps here) is reported and bounded by 1e-4."""
+    """FP64: exact to round-off. The plain FP32 form rounds every stored
+    population every step, with a bias that does not average out in a
+    quasi-steady state (about 1e-5 over these 300 steps); the offset form's
+    rest population takes each node's exact remainder, which leaves one
+    rounding per node and step (about 1e-6 here)."""
     from paper_2410_11129_gb300 import fcd as F
-    for prec, tol in (("fp64", 1e-12), ("fp32", 1e-4), ("fp32_offset", 1e-4)):
+    for prec, tol in (("fp64", 1e-12), ("fp32", 3e-5), ("fp32_offset", 2e-6)):
         ch = F.Channel(dict(parity_cfg(mag_tol=1e-6 if prec != "fp64" else 1e-10), precision=prec))
         m0 = np.array(ch.observe()["mass"])
         ch.step(300)
@@ -270,31 +275,131 @@ def test_full_size_1600x200_fp32_sampled(orc, fcd):
     ch.step(3)
     sim.step(3)
     phi = np.stack([ch.field("phi1"), ch.field("phi2")])
-    assert np.abs(phi - sim.phi()[:2]).max() <= 1e-4
+    err_phi = np.abs(phi - sim.phi()[:2]).max()
     umax = np.abs(sim.macro[:2]).max()
-    assert np.abs(ch.field("ux") - sim.macro[0]).max() <= 1e-3 * umax
+    err_u = np.abs(ch.field("ux") - sim.macro[0]).max() / umax
+    print("1600x200 FP32 after 3 steps: phi", err_phi, "u_rel", err_u)
+    assert err_phi <= 1e-4 and err_u <= 1e-4
     ob = ch.observe()
     assert ob["mag_resid"] <= cfg["mag_tol"] and ob["mag_iters"] >= 0
     ch.close()
 
 
-def test_batch_matches_individual_runs(fcd):
-    """Batched stepping (own stream and graphs per instance) is bit-identical to
-    stepping each instance alone; instances differ in size and physics."""
-    from paper_2410_11129_gb300 import fcd as F
-    cfgs = [dict(parity_cfg(mag_tol=1e-4), precision="fp32"),
-            dict(parity_cfg(nx=64, ny=24, xc=20.0, ferro="core", chi_ferro=2.0, mag_tol=1e-4),
-                 precision="fp32_offset"),
-            dict(parity_cfg(nx=38, ny=13, xc=11.0, yc=6.3, mag_tol=1e-10), precision="fp64")]
+BATCH_CFGS = [
+    dict(precision="fp32", mag_tol=1e-6),
+    dict(precision="fp32_offset", nx=64, ny=24, xc=20.0, ferro="core", chi_ferro=2.0, mag_tol=1e-4),
+    dict(precision="fp64", nx=38, ny=13, xc=11.0, yc=6.3, mag_tol=1e-10),
+    dict(precision="fp32", nx=256, ny=64, r1=8.0, r2=16.0, xc=60.0, mag_tol=1e-6),
+    dict(precision="fp32", Bo_m=0.0),
+    dict(precision="fp32_offset", nx=96, ny=28, xc=30.0, alpha=0.5, mag_tol=1e-5),
+]
+
+
+def _batch_cfgs():
+    out = []
+    for kw in BATCH_CFGS:
+        kw = dict(kw)
+        prec = kw.pop("precision")
+        out.append(dict(parity_cfg(**kw), precision=prec))
+    return out
+
+
+def _batch_vs_alone(F, mode, same, groups=2):
+    """30 batch steps, then one instance stepped alone (its group falls out of
+    phase and steps instance by instance) and 5 more batch steps; each
+    instance against the same steps run alone: same(a, b) on every array."""
+    cfgs = _batch_cfgs()
     b = F.Batch(cfgs)
+    b.set_mode(mode)
+    t = b.tuning()
+    assert t["batched"] == 5 and t["groups"] == groups and all(h in (4, 8, 16) for h in t["tile_h"])
     b.step(30)
     got = [inst.populations() for inst in b.instances]
     obs = b.observe()
+    b.instances[1].step(1)
+    b.step(5)
+    got2 = [inst.populations() for inst in b.instances]
     b.close()
-    for cfg, (fb, gb, pb), ob in zip(cfgs, got, obs):
+    for k, (cfg, g1, ob, g2) in enumerate(zip(cfgs, got, obs, got2)):
         ch = F.Channel(cfg)
         ch.step(30)
-        fa, ga, pa = ch.populations()
-        assert np.array_equal(fa, fb) and np.array_equal(ga, gb) and np.array_equal(pa, pb)
-        assert ch.observe()["T_o"] == ob["T_o"] and ob["step"] == 30
+        for x, y in zip(ch.populations(), g1):
+            same(x, y, k)
+        assert ob["step"] == 30
+        ch.step(6 if k == 1 else 5)
+        for x, y in zip(ch.populations(), g2):
+            same(x, y, k)
         ch.close()
+
+
+def test_batch_on_instance_streams_is_bitwise_alone(fcd):
+    """Mode 0 (every instance's own graph on its own stream) is bit-identical
+    to stepping each instance alone; the instances differ in size, physics
+    and form."""
+    from paper_2410_11129_gb300 import fcd as F
+
+    def same(x, y, k):
+        assert np.array_equal(x, y), k
+    _batch_vs_alone(F, 0, same)
+
+
+@pytest.mark.parametrize("split", [0, 2])
+def test_batched_kernels_match_instances_alone(fcd, monkeypatch, split):
+    """Mode 1 (one launch per kernel over a work list spanning the instances
+    of a storage form, one multigrid loop for all, the 256 x 64 instance with
+    a grid-wide coarse level) against each instance alone: the same arithmetic
+    up to the fused multiply-adds of each compiled kernel variant, so equal to
+    FP32 round-off (FP64 instances step alone: bitwise). split = 2 puts each
+    storage form's instances into two groups on two streams."""
+    from paper_2410_11129_gb300 import fcd as F
+    if split:
+        monkeypatch.setenv("FCD_BATCH_GROUPS", str(split))
+
+    def same(x, y, k):
+        scale = max(np.abs(x).max(), 1e-30)
+        assert np.abs(x - y).max() <= 1e-5 * scale, (k, np.abs(x - y).max(), scale)
+        if k == 2:
+            assert np.array_equal(x, y)
+    _batch_vs_alone(F, 1, same, 4 if split else 2)
+
+
+def test_batch_times_both_modes_then_keeps_one(fcd, monkeypatch):
+    monkeypatch.delenv("FCD_BATCH_MODE", raising=False)
+    from paper_2410_11129_gb300 import fcd as F
+    b = F.Batch(_batch_cfgs()[:2])
+    assert b.tuning()["mode"] == -1
+    b.step(4)
+    assert b.tuning()["mode"] == -1
+    b.step(3)
+    assert b.tuning()["mode"] in (0, 1)
+    assert all(o["step"] == 7 for o in b.observe())
+    b.close()
+
+
+def test_batched_instances_against_fp64_oracle(orc, fcd):
+    """Two batched FP32 instances of different sizes and physics (the larger
+    with a grid-wide coarse multigrid level) against the FP64 oracle, after
+    120 steps: phase fields and velocity within 1e-4, as the plain FP32 form."""
+    from paper_2410_11129_gb300 import fcd as F
+    cfgs = [parity_cfg(mag_tol=1e-6),
+            parity_cfg(nx=256, ny=64, r1=8.0, r2=16.0, xc=60.0, ferro="core", chi_ferro=2.0,
+                       alpha=np.pi / 2, mag_tol=1e-6)]
+    b = F.Batch([dict(c, precision="fp32_offset") for c in cfgs])
+    b.set_mode(1)
+    assert b.tuning()["batched"] == 2
+    b.step(120)
+    orc.set_threads(orc.max_threads())
+    try:
+        for cfg, inst in zip(cfgs, b.instances):
+            sim = orc.Sim(dict(cfg, mag_tol=1e-13))
+            sim.step(120)
+            phi = np.stack([inst.field("phi1"), inst.field("phi2")])
+            err_phi = np.abs(phi - sim.phi()[:2]).max()
+            umax = np.abs(sim.macro[:2]).max()
+            err_u = max(np.abs(inst.field("ux") - sim.macro[0]).max(),
+                        np.abs(inst.field("uy") - sim.macro[1]).max()) / umax
+            print("batched", cfg["nx"], "x", cfg["ny"], "phi", err_phi, "u_rel", err_u)
+            assert err_phi <= 1e-4 and err_u <= 1e-4
+    finally:
+        orc.set_threads(1)
+        b.close()

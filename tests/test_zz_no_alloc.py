@@ -18,13 +18,16 @@ KEYS = ("T_o", "T_i", "lx_o", "ly_o", "lx_i", "ly_i", "xc_core", "yc_core", "xc_
         "yc_shell")
 
 
-def test_noalloc_observables_match_context_twice():
+@pytest.mark.parametrize("open_x", [0, 1])
+def test_noalloc_observables_match_context_twice(open_x):
+    """Periodic channel, and the open channel (inlet and outlet, no wrap in x)
+    with the droplet near the outlet so that a wrapped frame would differ."""
     import torch
     assert torch.cuda.is_available()
     from paper_2410_11129_gb300 import fcd
     L = fcd.load()
-    cfg = W.small(nx=96, ny=40, r1=6.0, r2=12.0, xc=30.0, xi=4.0, Bo_m=2.0, ferro="shell",
-                  mag_tol=1e-10, mag_max_iter=300)
+    cfg = W.small(nx=96, ny=40, r1=6.0, r2=12.0, xc=80.0 if open_x else 30.0, xi=4.0, Bo_m=2.0,
+                  ferro="shell", mag_tol=1e-10, mag_max_iter=300, open_x=open_x)
     ch = fcd.Channel(dict(cfg, precision="fp64"))
     stream = torch.cuda.current_stream()
     for _ in range(2):  # two calls in a row: the shared scratch is reused
@@ -34,7 +37,8 @@ def test_noalloc_observables_match_context_twice():
         g_dev = torch.from_numpy(g).to("cuda")
         out = fcd.fcd_obs()
         st = L.fcd_observe_populations_noalloc(C.c_void_p(g_dev.data_ptr()), ch.nx, ch.ny,
-                                                C.c_void_p(stream.cuda_stream), C.byref(out))
+                                                open_x, C.c_void_p(stream.cuda_stream),
+                                                C.byref(out))
         assert st == fcd.FCD_OK
         got = out.as_dict()
         for k in KEYS:
@@ -50,7 +54,9 @@ def test_noalloc_rejects_oversized_lattice():
     from paper_2410_11129_gb300 import fcd
     L = fcd.load()
     out = fcd.fcd_obs()
-    dummy = C.c_void_p(1)  # never dereferenced: the size check comes first
-    assert L.fcd_observe_populations_noalloc(dummy, 20000, 40, None, C.byref(out)) == fcd.FCD_EINVAL
-    assert L.fcd_observe_populations_noalloc(dummy, 1024, 1024, None, C.byref(out)) == fcd.FCD_EINVAL
-    assert L.fcd_observe_populations_noalloc(None, 64, 32, None, C.byref(out)) == fcd.FCD_EINVAL
+    dummy = C.c_void_p(1)  # never dereferenced: the argument checks come first
+    call = L.fcd_observe_populations_noalloc
+    assert call(dummy, 20000, 40, 0, None, C.byref(out)) == fcd.FCD_EINVAL
+    assert call(dummy, 1024, 1024, 0, None, C.byref(out)) == fcd.FCD_EINVAL
+    assert call(dummy, 64, 32, 2, None, C.byref(out)) == fcd.FCD_EINVAL
+    assert call(None, 64, 32, 0, None, C.byref(out)) == fcd.FCD_EINVAL
