@@ -13,6 +13,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <typeinfo>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -1649,6 +1650,13 @@ bool engine_view(fcd_ctx *c, EngineView *v) {
     v->max_iter = e->prm.mag_max_iter;
     v->comp = e->comp;
     return true;
+}
+
+fcd_status engine_step1(fcd_ctx *c, int store_macro) {
+    // plain contexts only: the tangent and adjoint contexts keep their own step
+    if (typeid(*c) == typeid(Engine<float>)) return static_cast<Engine<float> *>(c)->one_step(store_macro);
+    if (typeid(*c) == typeid(Engine<double>)) return static_cast<Engine<double> *>(c)->one_step(store_macro);
+    return fcd_step(c, 1);
 }
 
 void engine_advance(fcd_ctx *c, long steps) {

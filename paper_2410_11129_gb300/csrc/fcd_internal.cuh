@@ -151,6 +151,7 @@ struct MgCtl {
     int twogrid_left;              // two-grid cycles still allowed in this solve
     long long smooth_cycles;       // cumulative lattice-sweep cycles (launch accounting)
     long long twogrid_cycles;      // cumulative two-grid cycles (launch accounting)
+    unsigned batch_visits;         // batched solves: blocks of the current residual launch seen
 };
 
 // What the phase kernel does besides Eq. 32: reset the solve's control block
@@ -308,15 +309,23 @@ template <typename T>
 int mg_levels(const MgHost<T> *m);
 // Batched solves of many FP32 hierarchies (one per instance; fields and
 // control blocks stay the instances' own): opening sweeps of every solve, and
-// the body of the loop that runs until every solve is done (in_graph: the
-// residual launch sets the while node's condition hw).
+// the body of the loop that runs until every solve is done.
 struct MgBatch;
 MgBatch *mg_batch_create(const std::vector<MgHost<float> *> &ms, const std::vector<float> &H0c,
                          const std::vector<float> &H0s, void *(*alloc)(size_t, void *),
                          void (*release)(void *, void *), void *user, char *err, size_t errlen);
 void mg_batch_destroy(MgBatch *b);
 void mg_batch_presmooth(MgBatch *b, cudaStream_t s);
-void mg_batch_body(MgBatch *b, cudaGraphConditionalHandle hw, int in_graph, cudaStream_t s);
+// one pass of the loop body launched from the host (no graph conditions set)
+void mg_batch_body(MgBatch *b, cudaStream_t s);
+// the body in parts, for a graph whose while node (hw) holds them: the head
+// sets hw when in_graph != 0, and with in_graph == 1 also the conditions of IF
+// nodes around the V-cycle (hv) and the two-grid cycle (ht)
+void mg_batch_head(MgBatch *b, cudaGraphConditionalHandle hw, cudaGraphConditionalHandle hv,
+                   cudaGraphConditionalHandle ht, int in_graph, cudaStream_t s);
+void mg_batch_vcycle(MgBatch *b, cudaStream_t s);
+void mg_batch_twogrid(MgBatch *b, cudaStream_t s);
+void mg_batch_close(MgBatch *b, cudaStream_t s);
 int mg_batch_body_kernels(const MgBatch *b);
 // after a body launched with in_graph = 0: 1 while some solve goes on, 0 when
 // all are done, -1 on a CUDA error (synchronises s)
@@ -401,6 +410,8 @@ struct EngineView {
 bool engine_view(fcd_ctx *c, EngineView *v);
 // the host-side record of a context after `steps` steps run by the batch
 void engine_advance(fcd_ctx *c, long steps);
+// one step of a context on its own stream; store_macro: also store u and p*
+fcd_status engine_step1(fcd_ctx *c, int store_macro);
 
 // observables. Scratch layout of one reduction (doubles): phi_1 and phi_2
 // planes (nx * ny each, unpadded), then OBS_COLS doubles per column.

@@ -1191,13 +1191,20 @@ struct MgBatchInst {
     float H0c, H0s;
     unsigned n0;  // level-0 smoothing tiles
     unsigned n1;  // residual blocks (32 x 8 level-1 cells)
+    int gx0, gx1; // tiles per row of the two
 };
+// A work-list entry: cnt consecutive tiles (row-major from (bx, by)) of one
+// instance at level lvl. The lists hold CHUNK tiles per entry (measured on the
+// 96-channel sweep: 8 tiles per block made the batched step 10% slower than 1).
 struct MgBatchTile {
-    int inst, bx, by, lvl;
+    int inst, bx, by, lvl, cnt;
 };
+constexpr int CHUNK = 1;
 struct MgBatchCtl {
-    unsigned blocks_done;
-    unsigned any;  // after a residual launch: 1 while some solve goes on
+    unsigned blocks_done;  // instances whose residual blocks have all run
+    unsigned any;   // after a residual launch: 1 while some solve goes on
+    unsigned any_v; // ... some instance runs a V-cycle in this pass
+    unsigned any_t; // ... some instance runs a two-grid cycle in this pass
 };
 
 constexpr int BS_FIRST = 0;  // the sweeps that open every solve
@@ -1210,35 +1217,68 @@ __global__ void __launch_bounds__(QT) smooth0_batch(const MgBatchInst *tab, cons
     int add = 0, sweeps = NU_SMOOTH_ONLY;
     if (kind == BS_CYCLE) {  // V-cycle and two-grid cycle: coarse correction; else sweeps only
         const int m = I.ctl->mode;
+        if (m == 3) return;  // this solve is over (uniform across the block)
         add = m == 0 || m == 2;
         sweeps = add ? NU_FINE : NU_SMOOTH_ONLY;
     }
-    if (I.L0.comp)
-        smooth0_tile<float, true>(I.L0, I.lv[1], add, sweeps, I.H0c, I.H0s, I.ctl, kind == BS_FIRST,
-                                  t.bx, t.by, I.n0);
-    else
-        smooth0_tile<float, false>(I.L0, I.lv[1], add, sweeps, I.H0c, I.H0s, I.ctl, kind == BS_FIRST,
-                                   t.bx, t.by, I.n0);
+    const int q0 = t.by * I.gx0 + t.bx;
+    for (int q = q0; q < q0 + t.cnt; q++) {
+        if (I.L0.comp)
+            smooth0_tile<float, true>(I.L0, I.lv[1], add, sweeps, I.H0c, I.H0s, I.ctl, kind == BS_FIRST,
+                                      q % I.gx0, q / I.gx0, I.n0);
+        else
+            smooth0_tile<float, false>(I.L0, I.lv[1], add, sweeps, I.H0c, I.H0s, I.ctl,
+                                       kind == BS_FIRST, q % I.gx0, q / I.gx0, I.n0);
+        __syncthreads();  // the tile's shared arrays are reused by the next one
+    }
 }
 
 __global__ void __launch_bounds__(256) resid0_batch(const MgBatchInst *tab, const MgBatchTile *tiles,
                                                     MgBatchCtl *bc, int ninst,
-                                                    cudaGraphConditionalHandle hw, int in_graph) {
+                                                    cudaGraphConditionalHandle hw,
+                                                    cudaGraphConditionalHandle hv,
+                                                    cudaGraphConditionalHandle ht, int in_graph) {
     const MgBatchTile t = tiles[blockIdx.x];
     const MgBatchInst &I = tab[t.inst];
-    if (I.L0.comp)
-        resid0_tile<float, true>(I.L0, I.lv[1], I.H0c, I.H0s, I.ctl, 0, 0, 0, t.bx, t.by, I.n1, false);
-    else
-        resid0_tile<float, false>(I.L0, I.lv[1], I.H0c, I.H0s, I.ctl, 0, 0, 0, t.bx, t.by, I.n1, false);
+    if (!I.ctl->done) {  // uniform across the block
+        const int q0 = t.by * I.gx1 + t.bx;
+        for (int q = q0; q < q0 + t.cnt; q++) {
+            if (I.L0.comp)
+                resid0_tile<float, true>(I.L0, I.lv[1], I.H0c, I.H0s, I.ctl, 0, 0, 0, q % I.gx1,
+                                         q / I.gx1, I.n1, false);
+            else
+                resid0_tile<float, false>(I.L0, I.lv[1], I.H0c, I.H0s, I.ctl, 0, 0, 0, q % I.gx1,
+                                          q / I.gx1, I.n1, false);
+            __syncthreads();  // the tile's shared arrays are reused by the next one
+        }
+    }
+    // Completion is counted per instance (its control block), and the last block
+    // of each instance counts the instance on the batch: one contended counter
+    // update per instance, not per block.
     if (threadIdx.x == 0 && threadIdx.y == 0) {
         __threadfence();
-        if (atomicAdd(&bc->blocks_done, 1u) == gridDim.x - 1) {
+        if (atomicAdd(&I.ctl->batch_visits, (unsigned)t.cnt) + (unsigned)t.cnt != I.n1) return;
+        I.ctl->batch_visits = 0;
+        __threadfence();
+        if (atomicAdd(&bc->blocks_done, 1u) == (unsigned)ninst - 1) {
             __threadfence();
             bc->blocks_done = 0;
-            unsigned any = 0;
-            for (int i = 0; i < ninst; i++) any |= ((volatile MgCtl *)tab[i].ctl)->done ? 0u : 1u;
+            unsigned any = 0, any_v = 0, any_t = 0;
+            for (int i = 0; i < ninst; i++) {
+                const volatile MgCtl *c = tab[i].ctl;
+                if (c->done) continue;
+                any = 1u;
+                any_v |= c->mode == 0 ? 1u : 0u;
+                any_t |= c->mode == 2 ? 1u : 0u;
+            }
             bc->any = any;
-            if (in_graph) cudaGraphSetConditional(hw, any);
+            bc->any_v = any_v;
+            bc->any_t = any_t;
+            if (in_graph) cudaGraphSetConditional(hw, any);  // the batch's loop
+            if (in_graph == 1) {  // IF nodes around the V-cycle and two-grid kernels
+                cudaGraphSetConditional(hv, any_v);
+                cudaGraphSetConditional(ht, any_t);
+            }
         }
     }
 }
@@ -1308,14 +1348,16 @@ MgBatch *mg_batch_create(const std::vector<MgHost<float> *> &ms, const std::vect
         const int gxl = (m->lv[1].nx + SX - 1) / SX, gyl = (m->lv[1].ny + SY - 1) / SY;
         I.n0 = (unsigned)(gx0 * gy0);
         I.n1 = (unsigned)(gx1 * gy1);
+        I.gx0 = gx0;
+        I.gx1 = gx1;
         tab.push_back(I);
         ids.push_back(i);
-        for (int y = 0; y < gy0; y++)
-            for (int x = 0; x < gx0; x++) t0.push_back({i, x, y, 0});
-        for (int y = 0; y < gy1; y++)
-            for (int x = 0; x < gx1; x++) t1.push_back({i, x, y, 1});
+        for (int q = 0; q < gx0 * gy0; q += CHUNK)
+            t0.push_back({i, q % gx0, q / gx0, 0, std::min(CHUNK, gx0 * gy0 - q)});
+        for (int q = 0; q < gx1 * gy1; q += CHUNK)
+            t1.push_back({i, q % gx1, q / gx1, 1, std::min(CHUNK, gx1 * gy1 - q)});
         for (int y = 0; y < gyl; y++)
-            for (int x = 0; x < gxl; x++) tl1.push_back({i, x, y, 1});
+            for (int x = 0; x < gxl; x++) tl1.push_back({i, x, y, 1, 1});
         b->maxlc = std::max(b->maxlc, m->lc);
         b->cta_smem = std::max(b->cta_smem, m->cta_smem);
     }
@@ -1330,9 +1372,9 @@ MgBatch *mg_batch_create(const std::vector<MgHost<float> *> &ms, const std::vect
             if (m->lc <= l) continue;  // level l runs inside this instance's coarse block
             const Level<TC> &L = m->lv[l], &C = m->lv[l + 1];
             for (int y = 0; y < (L.ny + SY - 1) / SY; y++)
-                for (int x = 0; x < (L.nx + SX - 1) / SX; x++) fs.push_back({i, x, y, l});
+                for (int x = 0; x < (L.nx + SX - 1) / SX; x++) fs.push_back({i, x, y, l, 1});
             for (int y = 0; y < (C.ny + 7) / 8; y++)
-                for (int x = 0; x < (C.nx + 31) / 32; x++) fr.push_back({i, x, y, l});
+                for (int x = 0; x < (C.nx + 31) / 32; x++) fr.push_back({i, x, y, l, 1});
         }
         b->n_fvs[l] = (int)fs.size();
         b->n_fvr[l] = (int)fr.size();
@@ -1344,7 +1386,7 @@ MgBatch *mg_batch_create(const std::vector<MgHost<float> *> &ms, const std::vect
     b->d_t0 = up.put<MgBatchTile>(t0.data(), t0.size() * sizeof(MgBatchTile));
     b->d_t1 = up.put<MgBatchTile>(t1.data(), t1.size() * sizeof(MgBatchTile));
     b->d_tl1 = up.put<MgBatchTile>(tl1.data(), tl1.size() * sizeof(MgBatchTile));
-    MgBatchCtl zero{0u, 0u};
+    MgBatchCtl zero{0u, 0u, 0u, 0u};
     b->d_ctl = up.put<MgBatchCtl>(&zero, sizeof zero);
     b->n_t0 = (int)t0.size();
     b->n_t1 = (int)t1.size();
@@ -1373,21 +1415,42 @@ void mg_batch_presmooth(MgBatch *b, cudaStream_t s) {
     smooth0_batch<<<b->n_t0, QT, 0, s>>>(b->d_tab, b->d_t0, BS_FIRST);
 }
 
-// One pass of the loop body: every instance's cycle head, then the kernels of
-// each kind of cycle (V-cycle, two-grid cycle, lattice sweeps), each acting
-// only for the instances whose head chose it.
-void mg_batch_body(MgBatch *b, cudaGraphConditionalHandle hw, int in_graph, cudaStream_t s) {
-    dim3 b2(32, 8);
-    resid0_batch<<<b->n_t1, b2, 0, s>>>(b->d_tab, b->d_t1, b->d_ctl, b->ninst, hw, in_graph);
+// One pass of the loop body, in three parts: every instance's cycle head
+// (mg_batch_head); the coarse-level kernels of the V-cycle (mg_batch_vcycle)
+// and of the two-grid cycle (mg_batch_twogrid), each acting only for the
+// instances whose head chose it; and the lattice part that ends every cycle
+// (mg_batch_close). In a graph the middle two sit in IF nodes whose conditions
+// the head sets (hv, ht): a pass in which no instance chose that cycle skips
+// their launches.
+void mg_batch_head(MgBatch *b, cudaGraphConditionalHandle hw, cudaGraphConditionalHandle hv,
+                   cudaGraphConditionalHandle ht, int in_graph, cudaStream_t s) {
+    resid0_batch<<<b->n_t1, dim3(32, 8), 0, s>>>(b->d_tab, b->d_t1, b->d_ctl, b->ninst, hw, hv, ht,
+                                                 in_graph);
+}
+
+void mg_batch_vcycle(MgBatch *b, cudaStream_t s) {
     for (int l = 1; l < b->maxlc; l++) {
         fv_smooth_batch<0><<<b->n_fvs[l], dim3(SX, SY), 0, s>>>(b->d_tab, b->d_fvs[l], NU_PRE);
-        fv_resid_batch<<<b->n_fvr[l], b2, 0, s>>>(b->d_tab, b->d_fvr[l]);
+        fv_resid_batch<<<b->n_fvr[l], dim3(32, 8), 0, s>>>(b->d_tab, b->d_fvr[l]);
     }
     coarse_batch<<<b->ninst, CTA_THREADS, b->cta_smem, s>>>(b->d_tab, b->d_inst);
     for (int l = b->maxlc - 1; l >= 1; l--)
         fv_smooth_batch<1><<<b->n_fvs[l], dim3(SX, SY), 0, s>>>(b->d_tab, b->d_fvs[l], NU_POST);
+}
+
+void mg_batch_twogrid(MgBatch *b, cudaStream_t s) {
     fv_smooth_batch<2><<<b->n_tl1, dim3(SX, SY), 0, s>>>(b->d_tab, b->d_tl1, NU_TWOGRID);
+}
+
+void mg_batch_close(MgBatch *b, cudaStream_t s) {
     smooth0_batch<<<b->n_t0, QT, 0, s>>>(b->d_tab, b->d_t0, BS_CYCLE);
+}
+
+void mg_batch_body(MgBatch *b, cudaStream_t s) {
+    mg_batch_head(b, 0, 0, 0, 0, s);
+    mg_batch_vcycle(b, s);
+    mg_batch_twogrid(b, s);
+    mg_batch_close(b, s);
 }
 
 int mg_batch_body_kernels(const MgBatch *b) { return 4 + 3 * (b->maxlc - 1); }
