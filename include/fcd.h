@@ -199,14 +199,16 @@ const char *fcd_last_error(const fcd_ctx *ctx);
 
 /* ---- Batched form: many independent channels (the Bo_m x Ca regime map of
  * Sec. 3.7 is a grid of separate runs). Each instance is a full context (its
- * own state; every fcd_* call works on it). The periodic FP32 instances of
- * one storage form are advanced together by one fixed set of kernels per
- * step, each launched once over a work list of tiles that spans all of them:
- * phase recovery, a single loop of batched multigrid kernels in which every
- * instance runs the cycle its own residual chose, and the fused
- * collide-stream, whose tile height an autotuner picks at create by timing.
- * Other instances (FP64, open channels) step on their own streams beside
- * them. fcd_batch_step then makes the caller's stream wait for everything.
+ * own state; every fcd_* call works on it). Two ways to step them (see
+ * fcd_batch_tuning): the periodic FP32 instances of one storage form advanced
+ * together by one fixed set of kernels per step, each launched once over a
+ * work list of tiles that spans them (phase recovery, a single loop of
+ * batched multigrid kernels in which every instance runs the cycle its own
+ * residual chose, and the fused collide-stream, whose tile height an
+ * autotuner picks at create by timing), the other instances (FP64, open
+ * channels) on their own streams beside them; or every instance's own step
+ * graph on its own stream. The first steps time both and keep the faster.
+ * fcd_batch_step then makes the caller's stream wait for everything.
  * On their own streams (mode 0 of fcd_batch_tuning) the instances' results
  * are bit-identical to stepping each alone; the batched kernels agree with
  * them to the rounding of contracted multiply-adds. */

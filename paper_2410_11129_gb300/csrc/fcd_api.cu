@@ -1007,8 +1007,10 @@ struct TangentEngine : Engine<double> {
     // Hierarchies of the tangent solves, made once the primal one exists.
     fcd_status make_tangent_mg() {
         for (int c = 0; c < NT && !mgt[c]; c++) {
+            // every tangent solve of a step has the primal solve's k, and the
+            // primal solve forms the lattice coefficients first: share them
             mgt[c] = mg_create<double>(prm.nx, prm.ny, pitch, k, tA[c], tB[c], ctlt[c], alloc,
-                                       release, user, err, sizeof err);
+                                       release, user, err, sizeof err, 0, mg);
             if (!mgt[c]) return FCD_ENOMEM;
             mg_set_rhs<double>(mgt[c], rhst[c]);
         }
@@ -1053,10 +1055,11 @@ struct TangentEngine : Engine<double> {
     }
 
     // kernels of one step outside the multigrid cycles (those are counted on
-    // the device): two phase kernels, per direction the right-hand side, two
-    // copies and the reset, the potential copy and the collision
+    // the device): two phase kernels, the primal solve's coefficient kernel and
+    // per direction the right-hand side, two copies and the reset, the
+    // potential copy and the collision
     long step_kernels() const {
-        return 2 + (magnetic() ? 5 * NT + 1 : 0) + 2 + (prm.open_x ? 1 : 0);  // + coefficient kernels
+        return 2 + (magnetic() ? 4 * NT + 1 : 0) + 2 + (prm.open_x ? 1 : 0);
     }
 
     long launches() const override {
@@ -1077,7 +1080,7 @@ struct TangentEngine : Engine<double> {
         const fcd_status st = Engine<double>::solve(tol, max_iter, iters, resid);
         if (st != FCD_OK && st != FCD_ENOCONV) return st;
         launch_tangent_phase(P, static_cast<const double *>(g[cur]), phi1, phi2, k, stream);
-        host_kernels += 1 + (magnetic() ? 5 * NT : 0);  // + one coefficient kernel per solve
+        host_kernels += 1 + (magnetic() ? 4 * NT : 0);  // the tangent phase; per direction 4
         const fcd_status st2 = tangent_solves(false, tol, max_iter, stream, false);
         return st2 != FCD_OK ? st2 : st;
     }

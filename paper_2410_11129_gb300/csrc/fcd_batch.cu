@@ -537,12 +537,14 @@ static fcd_status batch_steps(fcd_batch *b, int mode, long n, bool macro) {
             if (b->no_graph) {
                 e = group_host_step(g, c, sm);
             } else {
-                // the groups form a chain: a group's solves start when the
-                // previous group's have finished, and so run beside that
-                // group's collide-stream
+                // the groups start staggered: in the first step of a call a
+                // group's solves wait for the previous group's, after which the
+                // groups run free on their streams, so that one group's solves
+                // run beside another's collide-stream
                 e = group_graph_a(g, c);
                 if (e == cudaSuccess) e = group_graph_b(g, c, sm);
-                if (e == cudaSuccess && prev_solved) e = cudaStreamWaitEvent(g.stream, prev_solved, 0);
+                if (e == cudaSuccess && prev_solved && s == 0)
+                    e = cudaStreamWaitEvent(g.stream, prev_solved, 0);
                 if (e == cudaSuccess) e = cudaGraphLaunch(g.execA[c], g.stream);
                 if (e == cudaSuccess) e = cudaEventRecord(g.solved, g.stream);
                 if (e == cudaSuccess) e = cudaGraphLaunch(g.execB[c][sm], g.stream);

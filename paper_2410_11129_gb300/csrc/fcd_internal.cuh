@@ -275,7 +275,8 @@ struct MgHost;  // defined in fcd_mg.cu
 template <typename T>
 MgHost<T> *mg_create(int nx, int ny, int pitch, T *k0, T *psiA, T *psiB, MgCtl *ctl,
                      void *(*alloc)(size_t, void *), void (*release)(void *, void *), void *user,
-                     char *err, size_t errlen, int comp = 0);
+                     char *err, size_t errlen, int comp = 0,
+                     const MgHost<T> *share_coef = nullptr);  // FP64: use its coefficient planes
 template <typename T>
 void mg_destroy(MgHost<T> *m);
 // One V-cycle = head (lattice residual; decides whether the cycle runs) +

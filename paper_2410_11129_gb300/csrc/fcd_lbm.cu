@@ -119,7 +119,35 @@ struct FSum {
         d.add(-o.hi);
         return __fadd_rn(d.hi, __fadd_rn(d.lo, __fsub_rn(lo, o.lo)));
     }
+    // (this - o) rounded to FP32 without bias: rounded to the nearest value v
+    // with its exact error e, then moved one unit toward e with probability
+    // |e| / unit (u01: a uniform number in [0, 1)), so that the stored value's
+    // expectation is the difference itself. Round-to-nearest alone repeats the
+    // same rounding at a node whose remainder changes little between steps.
+    __device__ __forceinline__ float minus_unbiased(const FSum &o, float u01) const {
+        FSum d;
+        d.hi = hi;
+        d.add(-o.hi);
+        float v, e;
+        two_sum(d.hi, __fadd_rn(d.lo, __fsub_rn(lo, o.lo)), v, e);
+        if (e != 0.0f) {
+            const float next = nextafterf(v, e > 0.0f ? INFINITY : -INFINITY);
+            if (u01 * fabsf(__fsub_rn(next, v)) < fabsf(e)) v = next;
+        }
+        return v;
+    }
 };
+
+// Uniform number in [0, 1) from a 32-bit key: a multiply-xorshift integer
+// hash (the constants of the "lowbias32" mixer), top 24 bits.
+__device__ __forceinline__ float hash_u01(unsigned h) {
+    h ^= h >> 16;
+    h *= 0x7feb352du;
+    h ^= h >> 15;
+    h *= 0x846ca68bu;
+    h ^= h >> 16;
+    return float(h >> 8) * (1.0f / 16777216.0f);
+}
 
 template <typename R, typename B>
 struct Stencil {
@@ -463,7 +491,11 @@ __device__ __forceinline__ void collide_tile(const LbmArgs<T, typename Compute<T
                 else if (!leaves(a)) st_pop(gd, i * 9 + a, 18, ps32, dest(a), out);
             }
         }
-        if constexpr (CONSERVE) gd[(i * 9) * ps32 + n32] = S(pre.minus(post));
+        if constexpr (CONSERVE) {  // key: node, step, phase (reproducible)
+            const unsigned key = (unsigned)n32 * 0x9E3779B1u ^ (unsigned)(*A.step) * 0x85EBCA77u ^
+                                 (unsigned)(i + 1) * 0xC2B2AE3Du;
+            gd[(i * 9) * ps32 + n32] = S(pre.minus_unbiased(post, hash_u01(key)));
+        }
     }
 }
 

@@ -909,6 +909,7 @@ __device__ void cycle_close(MgCtl *ctl) {
 template <typename T>
 struct MgHost {
     int nl = 0, lc = 1;
+    bool coef_shared = false;   // level-0 coefficient planes are another hierarchy's
     Level<T> L0;                // the lattice level
     std::vector<Level<TC>> lv;  // levels 1 .. nl-1 (entry 0 unused)
     Level<TC> *d_lv = nullptr;
@@ -976,7 +977,7 @@ static void interp_table(const std::vector<double> &fine, const std::vector<doub
 template <typename T>
 MgHost<T> *mg_create(int nx, int ny, int pitch, T *k0, T *psiA, T *psiB, MgCtl *ctl,
                      void *(*alloc)(size_t, void *), void (*release)(void *, void *), void *user,
-                     char *err, size_t errlen, int comp) {
+                     char *err, size_t errlen, int comp, const MgHost<T> *share_coef) {
     MgHost<T> *m = new MgHost<T>();
     m->alloc = alloc;
     m->release = release;
@@ -1090,7 +1091,14 @@ MgHost<T> *mg_create(int nx, int ny, int pitch, T *k0, T *psiA, T *psiB, MgCtl *
         L.e = psiA;
         L.r = psiB;
         L.comp = sizeof(T) == 4 && comp ? 1 : 0;
-        if (keeps_coef<T>()) L.coef = up.put<T>(nullptr, (size_t)COEF * pitch * ny * sizeof(T));
+        if (keeps_coef<T>()) {
+            if (share_coef) {  // same lattice and k: the other hierarchy forms them
+                L.coef = share_coef->L0.coef;
+                m->coef_shared = true;
+            } else {
+                L.coef = up.put<T>(nullptr, (size_t)COEF * pitch * ny * sizeof(T));
+            }
+        }
     }
     for (int l = 0; l < m->nl; l++) {
         Level<TC> &L = m->lv[l];
@@ -1154,7 +1162,7 @@ void mg_cycle_smooth(MgHost<T> *m, T H0c, T H0s, cudaStream_t s) {
 template <typename T>
 void mg_presmooth(MgHost<T> *m, T H0c, T H0s, cudaStream_t s) {
     const std::vector<Level<TC>> &lv = m->lv;
-    if (keeps_coef<T>()) {  // the solve's node coefficients, before its first sweep
+    if (keeps_coef<T>() && !m->coef_shared) {  // the solve's node coefficients, before its first sweep
         dim3 b(32, 8);
         coef0_kernel<T><<<g2(m->L0.nx, m->L0.ny, b), b, 0, s>>>(m->L0, H0c, H0s);
     }
@@ -1562,7 +1570,7 @@ void mg_psi_io(MgHost<double> *m, int op, double *plane, double *prev, cudaStrea
 #define FCD_MG_INST(T)                                                                          \
     template MgHost<T> *mg_create<T>(int, int, int, T *, T *, T *, MgCtl *,                     \
                                      void *(*)(size_t, void *), void (*)(void *, void *), void *, \
-                                     char *, size_t, int);                                      \
+                                     char *, size_t, int, const MgHost<T> *);                   \
     template void mg_destroy<T>(MgHost<T> *);                                                   \
     template void mg_cycle_head<T>(MgHost<T> *, T, T, cudaGraphConditionalHandle,                \
                                    cudaGraphConditionalHandle, int, cudaStream_t);              \

@@ -163,10 +163,10 @@ def test_mass_conservation_gpu(fcd):
     """FP64: exact to round-off. The plain FP32 form rounds every stored
     population every step, with a bias that does not average out in a
     quasi-steady state (about 1e-5 over these 300 steps); the offset form's
-    rest population takes each node's exact remainder, which leaves one
-    rounding per node and step (about 1e-6 here)."""
+    rest population takes each node's exact remainder, rounded without bias,
+    which leaves a random walk of one rounding per node and step (5e-8 here)."""
     from paper_2410_11129_gb300 import fcd as F
-    for prec, tol in (("fp64", 1e-12), ("fp32", 3e-5), ("fp32_offset", 2e-6)):
+    for prec, tol in (("fp64", 1e-12), ("fp32", 3e-5), ("fp32_offset", 3e-7)):
         ch = F.Channel(dict(parity_cfg(mag_tol=1e-6 if prec != "fp64" else 1e-10), precision=prec))
         m0 = np.array(ch.observe()["mass"])
         ch.step(300)
@@ -187,9 +187,10 @@ def test_fp64_parity_total_spreading(orc, fcd, case):
 
 def test_offset_form_conserves_phase_mass(fcd):
     """The FP32 offset form stores each node's rest population as the exact
-    remainder of its pre-collision sum, so its phase masses drift only by one
-    rounding per node and step; the plain FP32 form, which rounds every stored
-    population, drifts coherently (1.7e-4 over 5000 steps on this channel)."""
+    remainder of its pre-collision sum, rounded without bias, so its phase
+    masses only random-walk by one rounding per node and step (measured 5e-8
+    over these 5000 steps); the plain FP32 form, which rounds every stored
+    population, drifts coherently (1.7e-4 on this channel)."""
     from paper_2410_11129_gb300 import fcd as F
     drift = {}
     for prec in ("fp32", "fp32_offset"):
@@ -200,8 +201,8 @@ def test_offset_form_conserves_phase_mass(fcd):
         ch.close()
         drift[prec] = np.abs(m1 - m0) / np.abs(m0)
     print("relative drift of phi_1, phi_2 over 5000 steps", drift)
-    assert np.all(drift["fp32_offset"] <= 2e-5), drift
-    assert np.all(drift["fp32_offset"] <= 0.1 * drift["fp32"]), drift
+    assert np.all(drift["fp32_offset"] <= 5e-7), drift
+    assert np.all(drift["fp32_offset"] <= 0.01 * drift["fp32"]), drift
 
 
 def test_checkpoint_resume_bitwise(fcd):
