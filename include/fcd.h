@@ -55,6 +55,13 @@ typedef enum {
     FCD_ESTATE = 6      /* snapshot does not match this context */
 } fcd_status;
 
+/* Storage forms of the populations. FP64; FP32 storing f + w_a and g as they
+ * are; FP32 "offset" storing f (an offset from the weights in this
+ * velocity-based form) and g - w_a/2, with each node's rest population g_0 set
+ * to the exact remainder of its pre-collision sum, rounded to FP32 without
+ * bias (reproducibly, from a hash of node, step and phase), so that the phase
+ * masses only random-walk by one rounding per node and step. FP32 contexts
+ * created with mag_tol below 1e-4 also hold psi' as a hi + lo pair. */
 typedef enum { FCD_FP64 = 0, FCD_FP32 = 1, FCD_FP32_OFFSET = 2 } fcd_precision;
 
 /* Problem statement of Sec. 2.5 in lattice units. Phases: 1 core, 2 shell,
