@@ -37,12 +37,14 @@ FALLBACK_HBM_GBS = 6800.0
 # stored u_x, u_y, p* (12).
 COLLIDE_BYTES_PER_NODE_F32 = 240
 # DRAM bytes (read + write) per collide launch measured by ncu, keyed by the hash
-# of the kernel source they were taken on and the workload (null once the source
-# changes). On 1600x200 the 37 MB of output stays in L2 when the launch ends, so
-# only the reads reach DRAM inside the launch.
+# of the kernel source they were taken on, the workload and the collide's tile
+# rows (null once the source changes). On 1600x200 the 37 MB of output stays in
+# L2 when the launch ends, so only the reads reach DRAM inside the launch.
 NCU_TRAFFIC = {
-    ("b9c674376c35c298", "1600x200"): 38433792 + 233472,
-    ("b9c674376c35c298", "9600x1200"): 1383384832 + 1204647936,
+    ("84445247c1db9588", "1600x200", 4): 38429952 + 254464,
+    ("84445247c1db9588", "1600x200", 8): 38432512 + 216064,
+    ("84445247c1db9588", "9600x1200", 4): 1383042560 + 1204710912,
+    ("84445247c1db9588", "9600x1200", 8): 1383297792 + 1204674048,
 }
 
 
@@ -230,6 +232,7 @@ def measure_large(steps, warmup, peak, peak_kind):
         torch.cuda.synchronize()
         total += a.elapsed_time(z)
     st1 = ch.solver_stats()
+    tile_h = ch.collide_tile_height()
     ch.close()
     coll = stage["collide"]
     bpn = COLLIDE_BYTES_PER_NODE_F32
@@ -241,8 +244,9 @@ def measure_large(steps, warmup, peak, peak_kind):
             "roofline": {"bound": "hbm", "kernel": "collide_kernel (fp32)", "achieved": achieved,
                          "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": achieved / peak,
-                         "traffic": NCU_TRAFFIC.get((kernel_source_hash(), "9600x1200")),
-                         "algorithmic_bytes_per_launch": bpn * N, "launch_ms": coll / steps}}
+                         "traffic": NCU_TRAFFIC.get((kernel_source_hash(), "9600x1200", tile_h)),
+                         "algorithmic_bytes_per_launch": bpn * N, "launch_ms": coll / steps,
+                         "collide_tile_height": tile_h}}
 
 
 def oracle_rate(cfg, min_seconds, max_steps, warmup=1, threads=1):
@@ -393,12 +397,14 @@ def run_ours(args):
     bpn = COLLIDE_BYTES_PER_NODE_F32 * (2 if cfg["precision"] == "fp64" else 1)
     achieved = bpn * N / (coll_ms * 1e-3) / 1e9
     h = kernel_source_hash()
-    traffic = NCU_TRAFFIC.get((h, args.workload))
+    tile_h = ch.collide_tile_height()
+    traffic = NCU_TRAFFIC.get((h, args.workload, tile_h))
     roofline = {"bound": "hbm", "kernel": "collide_kernel (%s)" % cfg["precision"],
                 "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                 "frac": achieved / peak,
                 "traffic": traffic,
-                "algorithmic_bytes_per_launch": bpn * N, "launch_ms": coll_ms}
+                "algorithmic_bytes_per_launch": bpn * N, "launch_ms": coll_ms,
+                "collide_tile_height": tile_h}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,

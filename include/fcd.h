@@ -193,6 +193,14 @@ long fcd_kernel_launches(const fcd_ctx *ctx);
  * solves stopped at the cycle cap] (synchronises). */
 fcd_status fcd_solver_stats(fcd_ctx *ctx, long long *out5);
 
+/* Rows per tile of the fused collide-stream kernel (Sec. 2.2-2.4 update,
+ * 32 nodes wide). FP32 contexts time 4 and 8 rows at create on their own grid
+ * and keep the faster (both do the same arithmetic per node, so the results do
+ * not depend on the choice); the environment variable FCD_COLLIDE_TILE_H=4 or 8,
+ * set before create, fixes it. FP64 and tangent contexts use 8 and 4.
+ * FCD_EINVAL for a null argument. */
+fcd_status fcd_collide_tile_height(const fcd_ctx *ctx, int *rows);
+
 /* Timing of the stages of a step with CUDA events recorded on the context's
  * stream (inside the step graph): enable, run fcd_step, then read
  * ms4 = [phase recovery + coarse permeabilities, potential solve,

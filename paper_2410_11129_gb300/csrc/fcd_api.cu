@@ -6,6 +6,7 @@
 // multigrid V-cycles until the device-side control block reports convergence
 // or the cycle cap -> fused collide-stream -> step counter. fcd_step(n)
 // launches n such graphs; nothing synchronises with the host in between.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstddef>
@@ -182,6 +183,7 @@ struct fcd_ctx {
     virtual fcd_status solver_stats(long long *out5) = 0;
     virtual fcd_status set_profiling(int on) = 0;
     virtual fcd_status profile(double *ms) = 0;
+    virtual int collide_tile_h() const = 0;
     fcd_status fail(fcd_status s, const char *fmt, ...) {
         va_list ap;
         va_start(ap, fmt);
@@ -243,6 +245,8 @@ struct Engine : fcd_ctx {
     long host_kernels = 0;
     int reported_nonconv = 0;
     int copies = 1;  // plane sets per field: 1, or 1 + NT for the tangent context
+    int tile_h = TY;  // rows per collide tile (FP32: chosen at create, tune_collide)
+    int collide_tile_h() const override { return tile_h; }
 
     // one level-0 potential buffer: psi_planes<T>() planes (FP32: hi and lo)
     size_t psi_bytes() const { return (size_t)psi_planes<T>() * ps * sizeof(T); }
@@ -352,7 +356,43 @@ struct Engine : fcd_ctx {
         double res;
         fcd_status st = solve(prm.mag_tol, prm.mag_max_iter > 100 ? prm.mag_max_iter : 100, &it, &res);
         if (st != FCD_OK && st != FCD_ENOCONV) return st;
+        st = tune_collide();
+        if (st != FCD_OK) return st;
         return keep_history();
+    }
+
+    // FP32 forms: the collide tile height (4 or 8 rows) that runs this grid
+    // faster, timed with events on the context's stream (the best of three
+    // launches each, after one untimed launch of each). The two heights do the
+    // same arithmetic per node. The timed launches write the idle population
+    // buffers, which the first step overwrites, and record neither breakup nor
+    // instability. FCD_COLLIDE_TILE_H=4 or 8 fixes the height instead.
+    fcd_status tune_collide() {
+        if (sizeof(T) != 4) return FCD_OK;
+        const char *env = getenv("FCD_COLLIDE_TILE_H");
+        if (env && (atoi(env) == 4 || atoi(env) == 8)) {
+            tile_h = atoi(env);
+            return FCD_OK;
+        }
+        LbmArgs<T> a = collide_args(cur, false);
+        a.brk = nullptr;
+        a.unst = nullptr;
+        const int hs[2] = {4, 8};
+        float best[2] = {1e30f, 1e30f};
+        cudaStream_t s = stream;
+        for (int r = 0; r < 4; r++)
+            for (int v = 0; v < 2; v++) {
+                CK(cudaEventRecord(ev[0], s));
+                launch_collide<T>(mode, hs[v], a, s);
+                CK(cudaEventRecord(ev[1], s));
+                CK(cudaEventSynchronize(ev[1]));
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+                if (r > 0) best[v] = std::min(best[v], ms);
+            }
+        host_kernels += 8;
+        tile_h = best[0] < best[1] ? 4 : 8;
+        return FCD_OK;
     }
 
     // The previous potential (for the extrapolated initial guess) := current.
@@ -371,7 +411,7 @@ struct Engine : fcd_ctx {
         launch_phase<T>(mode, P, g[c], phi1, phi2, k, pc, s);
         return FCD_OK;
     }
-    void enqueue_post(int c, bool store_macro, cudaStream_t s) {
+    LbmArgs<T> collide_args(int c, bool store_macro) const {
         LbmArgs<T> a;
         a.P = P;
         a.f_src = f[c];
@@ -388,7 +428,10 @@ struct Engine : fcd_ctx {
         a.step = &ctl->step_cur;
         a.unst = unst;
         a.open_x = prm.open_x;
-        launch_collide<T>(mode, a, s);
+        return a;
+    }
+    void enqueue_post(int c, bool store_macro, cudaStream_t s) {
+        launch_collide<T>(mode, tile_h, collide_args(c, store_macro), s);
         if (prm.open_x)
             launch_open_bc<T>(mode, P, f[c], g[c], f[c ^ 1], g[c ^ 1], prm.u_max, D.u_avg, s);
     }
@@ -939,6 +982,7 @@ static Phys<DualT> tangent_phys(const fcd_params *p, const Phys<double> &P) {
 // FP64 context whose plane sets carry NT tangent copies (see fcd.h). The
 // potential solves run with the host loop of the plain context.
 struct TangentEngine : Engine<double> {
+    int collide_tile_h() const override { return 4; }  // the dual tiles are larger
     Phys<DualT> PT;
     double *psiT = nullptr;   // 1 + NT planes: the step's potential, then its derivatives
     double *dpsiP = nullptr;  // NT planes: derivatives at the previous step (extrapolation)
@@ -1880,6 +1924,12 @@ long fcd_kernel_launches(const fcd_ctx *c) { return c ? c->launches() : -1; }
 fcd_status fcd_solver_stats(fcd_ctx *c, long long *out5) {
     if (!c || !out5) return FCD_EINVAL;
     return c->solver_stats(out5);
+}
+
+fcd_status fcd_collide_tile_height(const fcd_ctx *c, int *rows) {
+    if (!c || !rows) return FCD_EINVAL;
+    *rows = c->collide_tile_h();
+    return FCD_OK;
 }
 
 fcd_status fcd_set_profiling(fcd_ctx *c, int enable) { return c ? c->set_profiling(enable) : FCD_EINVAL; }

@@ -235,8 +235,10 @@ void launch_phase_batch(int mode, const BatchLbm<T> *tab, const BatchTile *tiles
 template <typename T>
 void launch_collide_batch(int mode, int tile_h, const BatchLbm<T> *tab, const BatchTile *tiles,
                           int ntiles, cudaStream_t s);
+// tile_h: rows per collide tile, 4 or 8 for the FP32 forms (the same
+// arithmetic per node; the faster one depends on the grid); FP64 uses 8.
 template <typename T>
-void launch_collide(int mode, const LbmArgs<T> &a, cudaStream_t s);
+void launch_collide(int mode, int tile_h, const LbmArgs<T> &a, cudaStream_t s);
 void launch_collide_tangent(const LbmArgs<double, DualT> &a, cudaStream_t s);
 void launch_open_bc_tangent(const Phys<double> &P, const void *f_src, const void *g_src,
                             void *f_dst, void *g_dst, double u_max, double u_avg, cudaStream_t s);

@@ -499,10 +499,12 @@ __device__ __forceinline__ void collide_tile(const LbmArgs<T, typename Compute<T
     }
 }
 
-template <typename T, int MODE, bool OPEN>
-__global__ void __launch_bounds__(TX *tile_y<MODE>(), collide_min_blocks<MODE>())
+// TYM rows per tile; MINB resident blocks per SM bound the registers (FP32:
+// 64 per thread at either height).
+template <typename T, int MODE, bool OPEN, int TYM = tile_y<MODE>(), int MINB = collide_min_blocks<MODE>()>
+__global__ void __launch_bounds__(TX *TYM, MINB)
     collide_kernel(LbmArgs<T, typename Compute<T, MODE>::type> A) {
-    collide_tile<T, MODE, OPEN>(A, blockIdx.x * TX, blockIdx.y * tile_y<MODE>());
+    collide_tile<T, MODE, OPEN, TYM>(A, blockIdx.x * TX, blockIdx.y * TYM);
 }
 
 // ---------------------------------------------------------------- batched
@@ -753,7 +755,16 @@ void launch_phase(int mode, const Phys<T> &P, const void *g, T *phi1, T *phi2, T
 }
 
 template <typename T>
-void launch_collide(int mode, const LbmArgs<T> &a, cudaStream_t s) {
+void launch_collide(int mode, int tile_h, const LbmArgs<T> &a, cudaStream_t s) {
+    if constexpr (sizeof(T) == 4) {
+        if (tile_h == 4) {
+            dim3 b(TX, 4), gr = grid2(a.P.nx, a.P.ny, b);
+            if (a.open_x) FCD_MODE_SWITCH(mode, T, (collide_kernel<T, M, true, 4, 8><<<gr, b, 0, s>>>(a)));
+            else FCD_MODE_SWITCH(mode, T, (collide_kernel<T, M, false, 4, 8><<<gr, b, 0, s>>>(a)));
+            return;
+        }
+    }
+    (void)tile_h;
     dim3 b(TX, TY), gr = grid2(a.P.nx, a.P.ny, b);
     if (a.open_x) FCD_MODE_SWITCH(mode, T, (collide_kernel<T, M, true><<<gr, b, 0, s>>>(a)));
     else FCD_MODE_SWITCH(mode, T, (collide_kernel<T, M, false><<<gr, b, 0, s>>>(a)));
@@ -863,7 +874,7 @@ void launch_phi3_to_f64(const T *p1, const T *p2, int nx, int ny, int pitch, dou
                                         cudaStream_t);                                         \
     template void launch_collide_batch<T>(int, int, const BatchLbm<T> *, const BatchTile *,    \
                                           int, cudaStream_t);                                  \
-    template void launch_collide<T>(int, const LbmArgs<T> &, cudaStream_t);                    \
+    template void launch_collide<T>(int, int, const LbmArgs<T> &, cudaStream_t);               \
     template void launch_open_bc<T>(int, const Phys<T> &, const void *, const void *, void *,    \
                                     void *, double, double, cudaStream_t);                      \
     template void launch_init<T>(int, const Phys<T> &, double, double, double, double, double, \

@@ -105,6 +105,7 @@ _SIGS = {
     "fcd_derive_params": (C.c_int, [C.POINTER(fcd_params), DP]),
     "fcd_kernel_launches": (C.c_long, [C.c_void_p]),
     "fcd_solver_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong)]),
+    "fcd_collide_tile_height": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "fcd_set_profiling": (C.c_int, [C.c_void_p, C.c_int]),
     "fcd_last_step_profile": (C.c_int, [C.c_void_p, DP]),
     "fcd_last_error": (C.c_char_p, [C.c_void_p]),
@@ -311,6 +312,12 @@ class Channel:
         out = (C.c_longlong * 5)()
         self.check(load().fcd_solver_stats(self.h, out))
         return dict(zip(["heads", "vcycles", "twogrid", "sweeps", "capped"], list(out)))
+
+    def collide_tile_height(self):
+        """Rows per tile of the collide-stream kernel (FP32: timed at create)."""
+        out = C.c_int(0)
+        self.check(load().fcd_collide_tile_height(self.h, C.byref(out)))
+        return out.value
 
     def set_profiling(self, on=True):
         self.check(load().fcd_set_profiling(self.h, 1 if on else 0))

@@ -239,6 +239,32 @@ def test_graph_and_host_loop_agree(fcd, monkeypatch):
     b.close()
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp32_offset"])
+@pytest.mark.parametrize("open_x", [0, 1])
+def test_collide_tile_heights_agree_bitwise(fcd, monkeypatch, prec, open_x):
+    """The FP32 collide's two tile heights (4 and 8 rows) do the same arithmetic
+    per node: the state after 60 steps is the same to the bit, so the height
+    timed at create cannot change a result. 38 x 13 leaves ragged tiles in both
+    directions for both heights."""
+    from paper_2410_11129_gb300 import fcd as F
+    cfg = dict(parity_cfg(nx=38, ny=13, xc=11.0, yc=6.3, alpha=0.6, mag_tol=1e-6, open_x=open_x),
+               precision=prec)
+    out = []
+    for h in (4, 8):
+        monkeypatch.setenv("FCD_COLLIDE_TILE_H", str(h))
+        ch = F.Channel(cfg)
+        assert ch.collide_tile_height() == h
+        ch.step(60)
+        out.append(ch.populations() + (ch.field("ux"), ch.field("pstar")))
+        ch.close()
+    for x, y in zip(*out):
+        assert np.array_equal(x, y)
+    monkeypatch.delenv("FCD_COLLIDE_TILE_H")
+    ch = F.Channel(cfg)  # timed at create: one of the two
+    assert ch.collide_tile_height() in (4, 8)
+    ch.close()
+
+
 def test_poiseuille_magic_parameter_gpu(fcd):
     """tau = 3/8 puts the half-way wall exactly: the parabola to round-off."""
     from paper_2410_11129_gb300 import fcd as F
