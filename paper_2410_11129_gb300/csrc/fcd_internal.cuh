@@ -103,6 +103,15 @@ struct Phys {
 // the 9-point link operator; levels >= 1 are merged tensor grids carrying a
 // 5-point finite-volume operator. Coordinates are in lattice units with the
 // walls at y = 0 and y = ny0 (cell faces) and period nx0 along x.
+// Completion counters of the level-0 kernels: tile t of a launch reports to
+// group t % MG_GROUPS, the last tile of each group to the control block.
+constexpr unsigned MG_GROUPS = 64;
+struct alignas(128) MgGroup {
+    unsigned count;               // tiles of this group done in the current launch
+    unsigned pad_;
+    unsigned long long max_bits;  // their max |r| (bits of a double >= 0)
+};
+
 template <typename T>
 struct Level {
     using value_type = T;
@@ -125,6 +134,7 @@ struct Level {
     // plane one plane stride after each buffer) and the residual is formed in
     // link differences (contexts whose tolerance one FP32 plane cannot reach)
     int comp;
+    MgGroup *grp;  // level 0: MG_GROUPS completion groups (zero between launches)
 };
 
 // Device-side control block of one potential solve.

@@ -79,6 +79,41 @@ __device__ __forceinline__ void atomic_max_nonneg(unsigned long long *p, double 
     atomicMax(p, (unsigned long long)__double_as_longlong(v));
 }
 
+// Thread 0 of a level-0 tile, after the tile's writes: true for the last of the
+// launch's nblocks tiles to finish (lin: the tile's index in the launch).
+// mx_bits (the tile's max |r| as double bits, 0 for none) goes to
+// ctl->norm_bits on the way. Updates of one counter serialise (about 0.9 ns each
+// on this GPU, measured with a grid barrier), so a launch of GROUPED_TILES tiles
+// or more reports through MG_GROUPS group counters in separate lines: no counter
+// takes more than ceil(nblocks / MG_GROUPS) or MG_GROUPS updates. Smaller
+// launches keep one counter, whose chain is shorter than the second level's
+// latency (measured on the 1600 x 200 channel: 4 us per step slower grouped).
+// The group counters are back at zero when the launch ends.
+constexpr unsigned GROUPED_TILES = 8192;
+__device__ __forceinline__ bool tile_done(MgCtl *ctl, MgGroup *grp, unsigned lin, unsigned nblocks,
+                                          unsigned long long mx_bits) {
+    __threadfence();
+    unsigned arrivals = nblocks;
+    if (grp && nblocks >= GROUPED_TILES) {
+        const unsigned g = lin % MG_GROUPS;
+        MgGroup &G = grp[g];
+        const unsigned gsize = nblocks / MG_GROUPS + (g < nblocks % MG_GROUPS ? 1u : 0u);
+        if (mx_bits) atomicMax(&G.max_bits, mx_bits);
+        __threadfence();
+        if (atomicAdd(&G.count, 1u) != gsize - 1) return false;
+        __threadfence();
+        G.count = 0;
+        mx_bits = atomicExch(&G.max_bits, 0ull);
+        arrivals = MG_GROUPS;
+    }
+    if (mx_bits) atomicMax(&ctl->norm_bits, mx_bits);
+    __threadfence();
+    if (atomicAdd(&ctl->blocks_done, 1u) != arrivals - 1) return false;
+    __threadfence();
+    ctl->blocks_done = 0;
+    return true;
+}
+
 // ------------------------------------------------------------------ level 0
 // Coefficients of the 9-point operator at lattice node (x, y); neighbours in
 // ghost rows mirror k and negate psi'.
@@ -89,7 +124,9 @@ struct Node9 {
     T b;          // right-hand side -L psi0
 };
 
-template <typename T, typename KF>
+// W: the node may lie on a wall row (y = 0 or ny - 1), whose ghost neighbours
+// follow the mirror rules; W = false (a tile without wall rows) drops the test.
+template <typename T, bool W = true, typename KF>
 __device__ __forceinline__ Node9<T> node9(KF kat, int y, int ny, T H0c, T H0s) {
     Node9<T> n;
     const T k0 = kat(0, 0);
@@ -101,24 +138,28 @@ __device__ __forceinline__ Node9<T> node9(KF kat, int y, int ny, T H0c, T H0s) {
         n.c[a] = ca;
         n.diag += ca;
         n.b += ca * (T(cx(a)) * H0c + T(cy(a)) * H0s);
-        const int yy = y + cy(a);
-        if ((yy < 0 || yy >= ny) && cx(a) == 0) n.diag += ca;  // psi'(ghost) = -psi'(node)
+        if constexpr (W) {
+            const int yy = y + cy(a);
+            if ((yy < 0 || yy >= ny) && cx(a) == 0) n.diag += ca;  // psi'(ghost) = -psi'(node)
+        }
     }
     return n;
 }
 
 // sum of c_a * psi~_a over neighbours that are not the node itself
-template <typename T, typename PF>
+template <typename T, bool W = true, typename PF>
 __device__ __forceinline__ T off9(const Node9<T> &n, PF pat, int y, int ny) {
     T s = T(0);
 #pragma unroll
     for (int a = 1; a < 9; a++) {
-        const int yy = y + cy(a);
-        if (yy < 0 || yy >= ny) {
-            if (cx(a) != 0) s -= n.c[a] * pat(cx(a), 0);  // mirror of a diagonal ghost
-        } else {
-            s += n.c[a] * pat(cx(a), cy(a));
+        if constexpr (W) {
+            const int yy = y + cy(a);
+            if (yy < 0 || yy >= ny) {
+                if (cx(a) != 0) s -= n.c[a] * pat(cx(a), 0);  // mirror of a diagonal ghost
+                continue;
+            }
         }
+        s += n.c[a] * pat(cx(a), cy(a));
     }
     return s;
 }
@@ -135,7 +176,7 @@ __device__ __forceinline__ T off9(const Node9<T> &n, PF pat, int y, int ny) {
 // first link of each opposite pair: 1, 2, 5, 6 for q = 0..3
 __host__ __device__ constexpr int pair_a(int q) { return q < 2 ? q + 1 : q + 3; }
 
-template <typename KF>
+template <bool W = true, typename KF>
 __device__ __forceinline__ Node9<float> node9_pairs(KF kat, int y, int ny, float H0c, float H0s) {
     Node9<float> n;
     const float k0 = kat(0, 0);
@@ -145,8 +186,10 @@ __device__ __forceinline__ Node9<float> node9_pairs(KF kat, int y, int ny, float
         const float ca = 3.f * wgt<float>(a) * (k0 + kat(cx(a), cy(a)));
         n.c[a] = ca;
         n.diag += ca;
-        const int yy = y + cy(a);
-        if ((yy < 0 || yy >= ny) && cx(a) == 0) n.diag += ca;  // psi'(ghost) = -psi'(node)
+        if constexpr (W) {
+            const int yy = y + cy(a);
+            if ((yy < 0 || yy >= ny) && cx(a) == 0) n.diag += ca;  // psi'(ghost) = -psi'(node)
+        }
     }
     n.b = 0.f;
 #pragma unroll
@@ -158,14 +201,16 @@ __device__ __forceinline__ Node9<float> node9_pairs(KF kat, int y, int ny, float
 }
 
 // b - L psi' at the node, psi' = hat + lat (accessors relative to the node).
-template <typename HF, typename LF>
+template <bool W = true, typename HF, typename LF>
 __device__ __forceinline__ float resid_pairs(const Node9<float> &n, HF hat, LF lat, int y, int ny) {
     const float h0 = hat(0, 0), l0 = lat(0, 0);
     auto dl = [&](int a) -> float {
-        const int yy = y + cy(a);
-        if (yy < 0 || yy >= ny) {  // mirrored ghost: psi'~ = -psi'(x + cx, y)
-            if (cx(a) == 0) return -(h0 + h0) - (l0 + l0);
-            return -(hat(cx(a), 0) + h0) - (lat(cx(a), 0) + l0);
+        if constexpr (W) {
+            const int yy = y + cy(a);
+            if (yy < 0 || yy >= ny) {  // mirrored ghost: psi'~ = -psi'(x + cx, y)
+                if (cx(a) == 0) return -(h0 + h0) - (l0 + l0);
+                return -(hat(cx(a), 0) + h0) - (lat(cx(a), 0) + l0);
+            }
         }
         return (hat(cx(a), cy(a)) - h0) + (lat(cx(a), cy(a)) - l0);
     };
@@ -281,8 +326,9 @@ __device__ void cycle_decide(MgCtl *ctl, cudaGraphConditionalHandle hw,
 constexpr int RX = 2 * 32 + 1 + 2, RY = 2 * 8 + 1 + 2;
 
 // One 32 x 8 block of level-1 cells (bx, by) of a grid of nblocks blocks;
-// grid_lead: the block that reports a solve that is already done.
-template <typename T, bool COMP>
+// grid_lead: the block that reports a solve that is already done. SPLIT as
+// for the smoothing tiles.
+template <typename T, bool COMP, bool SPLIT = true>
 __device__ __forceinline__ void resid0_tile(const Level<T> &L0, const Level<TC> &L1, T H0c, T H0s,
                                             MgCtl *ctl, cudaGraphConditionalHandle hw,
                                             cudaGraphConditionalHandle hi, int in_graph, int bx,
@@ -302,41 +348,55 @@ __device__ __forceinline__ void resid0_tile(const Level<T> &L0, const Level<TC> 
     const int fx0 = L1.cx0[I0], fx1 = L1.cx0[I1], fy0 = L1.cy0[J0], fy1 = L1.cy0[J1];
     const int wx = fx1 - fx0 + 2, wy = fy1 - fy0 + 2;
     const T *psi = ctl->cur ? L0.r : L0.e;
-    {  // all loads issued before the shared-memory stores
-        constexpr int NL = (RX * RY + 255) / 256;
-        T kv[NL], pv[NL], lv[COMP ? NL : 1];
-        const int t0 = threadIdx.y * 32 + threadIdx.x;
+    {  // all loads issued before the shared-memory stores: warp w takes footprint
+       // rows w, w + 8, w + 16, lane l columns l, l + 32, l + 64
+        constexpr int NR = (RY + 7) / 8, NC = (RX + 31) / 32;
+        const int lane = threadIdx.x, warp = threadIdx.y;
+        int gxs[NC];
 #pragma unroll
-        for (int q = 0; q < NL; q++) {
-            const int t = t0 + q * 256;
-            kv[q] = T(0);
-            pv[q] = T(0);
-            if constexpr (COMP) lv[q] = T(0);
-            if (t < wx * wy) {
-                const int lx = t % wx, ly = t / wx;
-                int gx = fx0 - 1 + lx;
-                gx = gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx);
-                const int gy = fy0 - 1 + ly;
-                const int my = gy < 0 ? 0 : (gy >= ny ? ny - 1 : gy);
-                kv[q] = L0.k[(long long)my * pitch + gx];  // mirrored ghost rows
-                pv[q] = psi[(long long)my * pitch + gx];   // ghost rows never read
-                if constexpr (COMP) lv[q] = psi[lo_off + (long long)my * pitch + gx];
+        for (int c = 0; c < NC; c++) {
+            int gx = fx0 - 1 + lane + 32 * c;
+            gx = gx < 0 ? gx + nx : gx;
+            while (gx >= nx) gx -= nx;
+            gxs[c] = gx;
+        }
+        T kv[NR][NC], pv[NR][NC], lv[COMP ? NR : 1][COMP ? NC : 1];
+#pragma unroll
+        for (int r = 0; r < NR; r++) {
+            const int ly = warp + 8 * r, gy = fy0 - 1 + ly;
+            const int my = gy < 0 ? 0 : (gy >= ny ? ny - 1 : gy);
+#pragma unroll
+            for (int c = 0; c < NC; c++) {
+                kv[r][c] = T(0);
+                pv[r][c] = T(0);
+                if constexpr (COMP) lv[r][c] = T(0);
+                if (ly < wy && lane + 32 * c < wx) {
+                    const long long m = (long long)my * pitch + gxs[c];
+                    kv[r][c] = L0.k[m];  // mirrored ghost rows
+                    pv[r][c] = psi[m];   // ghost rows never read
+                    if constexpr (COMP) lv[r][c] = psi[lo_off + m];
+                }
             }
         }
 #pragma unroll
-        for (int q = 0; q < NL; q++) {
-            const int t = t0 + q * 256;
-            if (t < wx * wy) {
-                sk[t / wx][t % wx] = kv[q];
-                sp[t / wx][t % wx] = pv[q];
-                if constexpr (COMP) sl[t / wx][t % wx] = lv[q];
+        for (int r = 0; r < NR; r++)
+#pragma unroll
+            for (int c = 0; c < NC; c++) {
+                const int ly = warp + 8 * r, lx = lane + 32 * c;
+                if (ly < wy && lx < wx) {
+                    sk[ly][lx] = kv[r][c];
+                    sp[ly][lx] = pv[r][c];
+                    if constexpr (COMP) sl[ly][lx] = lv[r][c];
+                }
             }
-        }
     }
     __syncthreads();
     const int I = I0 + threadIdx.x, J = J0 + threadIdx.y;
     T mxt = T(0);  // a max is exact in the compute type; only the reduction is FP64
-    if (I < L1.nx && J < L1.ny) {
+    // W: the footprint holds a wall row, whose nodes take the ghost rules
+    auto cells = [&](auto wall) {
+        constexpr bool W = decltype(wall)::value;
+        if (!(I < L1.nx && J < L1.ny)) return;
         T sum = T(0), ksum = T(0);
         auto child = [&](int i, int j) {
             const int lx = i - fx0 + 1, ly = j - fy0 + 1;
@@ -345,9 +405,9 @@ __device__ __forceinline__ void resid0_tile(const Level<T> &L0, const Level<TC> 
             T r;
             if constexpr (COMP) {
                 auto lat = [&](int dx, int dy) { return sl[ly + dy][lx + dx]; };
-                Node9<float> nd = node9_pairs(kat, j, ny, H0c, H0s);
+                Node9<float> nd = node9_pairs<W>(kat, j, ny, H0c, H0s);
                 if (L0.rhs) nd.b = L0.rhs[(long long)j * pitch + i];
-                r = resid_pairs(nd, pat, lat, j, ny);
+                r = resid_pairs<W>(nd, pat, lat, j, ny);
             } else {
                 Node9<T> nd;
                 if constexpr (keeps_coef<T>()) {
@@ -355,10 +415,10 @@ __device__ __forceinline__ void resid0_tile(const Level<T> &L0, const Level<TC> 
                     coef_load(L0, (long long)j * pitch + i, nd, inv);
                     (void)kat;
                 } else {
-                    nd = node9<T>(kat, j, ny, H0c, H0s);
+                    nd = node9<T, W>(kat, j, ny, H0c, H0s);
                 }
                 const T bb = L0.rhs ? L0.rhs[(long long)j * pitch + i] : nd.b;
-                r = bb - (off9<T>(nd, pat, j, ny) - nd.diag * sp[ly][lx]);
+                r = bb - (off9<T, W>(nd, pat, j, ny) - nd.diag * sp[ly][lx]);
             }
             sum += r;
             ksum += sk[ly][lx];
@@ -377,18 +437,21 @@ __device__ __forceinline__ void resid0_tile(const Level<T> &L0, const Level<TC> 
         }
         L1.b[(long long)J * L1.pitch + I] = TC(sum);
         L1.k[(long long)J * L1.pitch + I] = TC(ksum / (T(L1.wx[I]) * T(L1.wy[J])));  // unit lattice cells
-    }
+    };
+    if (!SPLIT || fy0 == 0 || fy1 >= ny) cells(std::true_type{});
+    else cells(std::false_type{});
     for (int o = 16; o > 0; o >>= 1) mxt = fmax(mxt, __shfl_xor_sync(0xffffffffu, mxt, o));
-    const double mx = (double)mxt;
-    if ((threadIdx.x & 31) == 0 && mx > 0.0) atomic_max_nonneg(&ctl->norm_bits, mx);
+    __shared__ T wmax[8];  // one per warp (blockDim 32 x 8)
+    if (threadIdx.x == 0) wmax[threadIdx.y] = mxt;
     __syncthreads();
     if (lead) {  // the last block to finish sees the whole norm and decides the cycle
-        __threadfence();
-        if (atomicAdd(&ctl->blocks_done, 1u) == nblocks - 1) {
-            __threadfence();
-            ctl->blocks_done = 0;
-            cycle_decide(ctl, hw, hi, in_graph);
-        }
+        T m = wmax[0];
+#pragma unroll
+        for (int w = 1; w < 8; w++) m = fmax(m, wmax[w]);
+        const double mx = (double)m;
+        const unsigned long long bits = mx > 0.0 ? (unsigned long long)__double_as_longlong(mx) : 0ull;
+        const unsigned lin = (unsigned)(by * ((L1.nx + 31) / 32) + bx);
+        if (tile_done(ctl, L0.grp, lin, nblocks, bits)) cycle_decide(ctl, hw, hi, in_graph);
     }
 }
 
@@ -409,10 +472,13 @@ __device__ void cycle_close(MgCtl *ctl);
 // Same-colour nodes are not 9-point neighbours, so the result does not depend
 // on the order within a phase.
 constexpr int QT = (SX / 2) * (SY / 2);  // threads of a smoothing tile
-constexpr int TILE_LOADS = ((SX + 2) * (SY + 2) + QT - 1) / QT;
+static_assert(QT % 32 == 0 && 2 * (SY + 2) <= QT, "tile load layout");
+constexpr int TILE_ROWS = (SY + 2 + QT / 32 - 1) / (QT / 32);  // ring rows per warp
 
-// One 32 x 8 tile (bx, by) of a grid of nblocks tiles.
-template <typename T, bool COMP>
+// One 32 x 8 tile (bx, by) of a grid of nblocks tiles. SPLIT: tiles without a
+// wall row take a second copy of the sweeps that skips the ghost tests (fewer
+// instructions; the batched kernels keep one copy to bound their registers).
+template <typename T, bool COMP, bool SPLIT = true>
 __device__ __forceinline__ void smooth0_tile(const Level<T> &L0, const Level<TC> &L1,
                                              int add_coarse, int sweeps, T H0c, T H0s, MgCtl *ctl,
                                              int first, int bx, int by, unsigned nblocks) {
@@ -430,19 +496,28 @@ __device__ __forceinline__ void smooth0_tile(const Level<T> &L0, const Level<TC>
     T *dst = ctl->cur ? L0.e : L0.r;
     __shared__ ProlongTile<T, SX + 2, SY + 2> pt;
     if (add_coarse) prolong_tile_load(pt, L0, x0 - 1, y0 - 1);
-    {  // tile with its frozen one-cell ring: all loads issued before the stores
-        T kv[TILE_LOADS], pv[TILE_LOADS], lv[COMP ? TILE_LOADS : 1];
+    {  // tile with its frozen one-cell ring, all loads issued before the stores: warp w
+       // takes ring rows w, w + QT/32, ..., lane l column l; the two last columns
+       // (2 (SY + 2) values) go to threads 0 .. 2 SY + 3
+        const int lane = tid & 31, warp = tid >> 5;
+        auto wrap = [&](int gx) {
+            if (gx < 0) gx += nx;
+            while (gx >= nx) gx -= nx;
+            return gx;
+        };
+        const int gxa = wrap(x0 - 1 + lane);
+        const bool extra = tid < 2 * (SY + 2);
+        const int ey = tid >> 1, ex = SX + (tid & 1), gxe = wrap(x0 - 1 + ex);
+        T kv[TILE_ROWS + 1], pv[TILE_ROWS + 1], lv[COMP ? TILE_ROWS + 1 : 1];
 #pragma unroll
-        for (int q = 0; q < TILE_LOADS; q++) {
-            const int t = tid + q * QT;
+        for (int q = 0; q <= TILE_ROWS; q++) {
+            const int ly = q < TILE_ROWS ? warp + q * (QT / 32) : ey;
+            const int gx = q < TILE_ROWS ? gxa : gxe;
+            const bool act = q < TILE_ROWS ? ly < SY + 2 : extra;
             kv[q] = T(0);
             pv[q] = T(0);
             if constexpr (COMP) lv[q] = T(0);
-            if (t < (SX + 2) * (SY + 2)) {
-                const int lx = t % (SX + 2), ly = t / (SX + 2);
-                int gx = x0 - 1 + lx;
-                if (gx < 0) gx += nx;
-                while (gx >= nx) gx -= nx;
+            if (act) {
                 const int gy = y0 - 1 + ly;
                 const int my = gy < 0 ? 0 : (gy >= ny ? ny - 1 : gy);
                 kv[q] = L0.k[(long long)my * pitch + gx];
@@ -453,12 +528,13 @@ __device__ __forceinline__ void smooth0_tile(const Level<T> &L0, const Level<TC>
             }
         }
 #pragma unroll
-        for (int q = 0; q < TILE_LOADS; q++) {
-            const int t = tid + q * QT;
-            if (t < (SX + 2) * (SY + 2)) {
-                sk[t / (SX + 2)][t % (SX + 2)] = kv[q];
-                sp[t / (SX + 2)][t % (SX + 2)] = pv[q];
-                if constexpr (COMP) sl[t / (SX + 2)][t % (SX + 2)] = lv[q];
+        for (int q = 0; q <= TILE_ROWS; q++) {
+            const int ly = q < TILE_ROWS ? warp + q * (QT / 32) : ey;
+            const int lx = q < TILE_ROWS ? lane : ex;
+            if (q < TILE_ROWS ? ly < SY + 2 : extra) {
+                sk[ly][lx] = kv[q];
+                sp[ly][lx] = pv[q];
+                if constexpr (COMP) sl[ly][lx] = lv[q];
             }
         }
     }
@@ -474,61 +550,63 @@ __device__ __forceinline__ void smooth0_tile(const Level<T> &L0, const Level<TC>
         __syncthreads();
     }
     const int qx = 2 * (tid % (SX / 2)), qy = 2 * (tid / (SX / 2));
-    Node9<T> nd[4];
-    T inv_diag[4];
-    bool own[4];
+    // W: the tile holds a wall row, whose nodes take the ghost rules
+    auto sweep_tile = [&](auto wall) {
+        constexpr bool W = decltype(wall)::value;
+        Node9<T> nd[4];
+        T inv_diag[4];
+        bool own[4];
 #pragma unroll
-    for (int c = 0; c < 4; c++) {  // colour c = (x & 1) + 2 (y & 1) is quad node (c & 1, c >> 1)
-        const int lx = qx + (c & 1) + 1, ly = qy + (c >> 1) + 1;
-        const int x = x0 + lx - 1, y = y0 + ly - 1;
-        own[c] = x < nx && y < ny;
-        inv_diag[c] = T(0);
-        if (own[c]) {
-            if constexpr (keeps_coef<T>()) {
-                coef_load(L0, (long long)y * pitch + x, nd[c], inv_diag[c]);
-            } else {
-                auto kat = [&](int dx, int dy) { return sk[ly + dy][lx + dx]; };
-                if constexpr (COMP) nd[c] = node9_pairs(kat, y, ny, H0c, H0s);
-                else nd[c] = node9<T>(kat, y, ny, H0c, H0s);
-                inv_diag[c] = T(1) / nd[c].diag;
+        for (int c = 0; c < 4; c++) {  // colour c = (x & 1) + 2 (y & 1) is quad node (c & 1, c >> 1)
+            const int lx = qx + (c & 1) + 1, ly = qy + (c >> 1) + 1;
+            const int x = x0 + lx - 1, y = y0 + ly - 1;
+            own[c] = x < nx && y < ny;
+            inv_diag[c] = T(0);
+            if (own[c]) {
+                if constexpr (keeps_coef<T>()) {
+                    coef_load(L0, (long long)y * pitch + x, nd[c], inv_diag[c]);
+                } else {
+                    auto kat = [&](int dx, int dy) { return sk[ly + dy][lx + dx]; };
+                    if constexpr (COMP) nd[c] = node9_pairs<W>(kat, y, ny, H0c, H0s);
+                    else nd[c] = node9<T, W>(kat, y, ny, H0c, H0s);
+                    inv_diag[c] = T(1) / nd[c].diag;
+                }
+                if (L0.rhs) nd[c].b = L0.rhs[(long long)y * pitch + x];
             }
-            if (L0.rhs) nd[c].b = L0.rhs[(long long)y * pitch + x];
         }
-    }
-    for (int s = 0; s < sweeps; s++) {
+        for (int s = 0; s < sweeps; s++) {
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                const int lx = qx + (c & 1) + 1, ly = qy + (c >> 1) + 1, y = y0 + ly - 1;
+                auto pat = [&](int dx, int dy) { return sp[ly + dy][lx + dx]; };
+                if (own[c]) {
+                    if constexpr (COMP) {  // correction form: dr/dpsi'_0 = diag, so psi'_0 -= r_0 / diag
+                        auto lat = [&](int dx, int dy) { return sl[ly + dy][lx + dx]; };
+                        const float r = resid_pairs<W>(nd[c], pat, lat, y, ny);
+                        comp_add(sp[ly][lx], sl[ly][lx], -r * inv_diag[c]);
+                    } else {
+                        sp[ly][lx] = (off9<T, W>(nd[c], pat, y, ny) - nd[c].b) * inv_diag[c];
+                    }
+                }
+                __syncthreads();
+            }
+        }
 #pragma unroll
         for (int c = 0; c < 4; c++) {
-            const int lx = qx + (c & 1) + 1, ly = qy + (c >> 1) + 1, y = y0 + ly - 1;
-            auto pat = [&](int dx, int dy) { return sp[ly + dy][lx + dx]; };
+            const int lx = qx + (c & 1) + 1, ly = qy + (c >> 1) + 1;
             if (own[c]) {
-                if constexpr (COMP) {  // correction form: dr/dpsi'_0 = diag, so psi'_0 -= r_0 / diag
-                    auto lat = [&](int dx, int dy) { return sl[ly + dy][lx + dx]; };
-                    const float r = resid_pairs(nd[c], pat, lat, y, ny);
-                    comp_add(sp[ly][lx], sl[ly][lx], -r * inv_diag[c]);
-                } else {
-                    sp[ly][lx] = (off9<T>(nd[c], pat, y, ny) - nd[c].b) * inv_diag[c];
-                }
+                const long long n = (long long)(y0 + ly - 1) * pitch + (x0 + lx - 1);
+                dst[n] = sp[ly][lx];
+                if constexpr (COMP) dst[lo_off + n] = sl[ly][lx];
             }
-            __syncthreads();
         }
-    }
-#pragma unroll
-    for (int c = 0; c < 4; c++) {
-        const int lx = qx + (c & 1) + 1, ly = qy + (c >> 1) + 1;
-        if (own[c]) {
-            const long long n = (long long)(y0 + ly - 1) * pitch + (x0 + lx - 1);
-            dst[n] = sp[ly][lx];
-            if constexpr (COMP) dst[lo_off + n] = sl[ly][lx];
-        }
-    }
+    };
+    if (!SPLIT || y0 == 0 || y0 + SY >= ny) sweep_tile(std::true_type{});
+    else sweep_tile(std::false_type{});
     __syncthreads();
     if (tid == 0) {
-        __threadfence();
-        if (atomicAdd(&ctl->blocks_done, 1u) == nblocks - 1) {
-            __threadfence();
-            ctl->blocks_done = 0;
-            cycle_close(ctl);
-        }
+        const unsigned lin = (unsigned)(by * ((nx + SX - 1) / SX) + bx);
+        if (tile_done(ctl, L0.grp, lin, nblocks, 0ull)) cycle_close(ctl);
     }
 }
 
@@ -1091,6 +1169,10 @@ MgHost<T> *mg_create(int nx, int ny, int pitch, T *k0, T *psiA, T *psiB, MgCtl *
         L.e = psiA;
         L.r = psiB;
         L.comp = sizeof(T) == 4 && comp ? 1 : 0;
+        {
+            const std::vector<MgGroup> zero(MG_GROUPS, MgGroup{});
+            L.grp = up.put<MgGroup>(zero.data(), MG_GROUPS * sizeof(MgGroup));
+        }
         if (keeps_coef<T>()) {
             if (share_coef) {  // same lattice and k: the other hierarchy forms them
                 L.coef = share_coef->L0.coef;
@@ -1232,10 +1314,10 @@ __global__ void __launch_bounds__(QT) smooth0_batch(const MgBatchInst *tab, cons
     const int q0 = t.by * I.gx0 + t.bx;
     for (int q = q0; q < q0 + t.cnt; q++) {
         if (I.L0.comp)
-            smooth0_tile<float, true>(I.L0, I.lv[1], add, sweeps, I.H0c, I.H0s, I.ctl, kind == BS_FIRST,
+            smooth0_tile<float, true, false>(I.L0, I.lv[1], add, sweeps, I.H0c, I.H0s, I.ctl, kind == BS_FIRST,
                                       q % I.gx0, q / I.gx0, I.n0);
         else
-            smooth0_tile<float, false>(I.L0, I.lv[1], add, sweeps, I.H0c, I.H0s, I.ctl,
+            smooth0_tile<float, false, false>(I.L0, I.lv[1], add, sweeps, I.H0c, I.H0s, I.ctl,
                                        kind == BS_FIRST, q % I.gx0, q / I.gx0, I.n0);
         __syncthreads();  // the tile's shared arrays are reused by the next one
     }
@@ -1252,10 +1334,10 @@ __global__ void __launch_bounds__(256) resid0_batch(const MgBatchInst *tab, cons
         const int q0 = t.by * I.gx1 + t.bx;
         for (int q = q0; q < q0 + t.cnt; q++) {
             if (I.L0.comp)
-                resid0_tile<float, true>(I.L0, I.lv[1], I.H0c, I.H0s, I.ctl, 0, 0, 0, q % I.gx1,
+                resid0_tile<float, true, false>(I.L0, I.lv[1], I.H0c, I.H0s, I.ctl, 0, 0, 0, q % I.gx1,
                                          q / I.gx1, I.n1, false);
             else
-                resid0_tile<float, false>(I.L0, I.lv[1], I.H0c, I.H0s, I.ctl, 0, 0, 0, q % I.gx1,
+                resid0_tile<float, false, false>(I.L0, I.lv[1], I.H0c, I.H0s, I.ctl, 0, 0, 0, q % I.gx1,
                                           q / I.gx1, I.n1, false);
             __syncthreads();  // the tile's shared arrays are reused by the next one
         }
