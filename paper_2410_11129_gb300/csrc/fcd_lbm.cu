@@ -149,6 +149,17 @@ __device__ __forceinline__ float hash_u01(unsigned h) {
     return float(h >> 8) * (1.0f / 16777216.0f);
 }
 
+// e_a . (vx, vy) for the D2Q9 velocity e_a, written without the products by a
+// zero component (IEEE arithmetic keeps 0 * v, which is not 0 for every v).
+template <typename R>
+__device__ __forceinline__ R edot(int a, const R &vx, const R &vy) {
+    const int ex = cx(a), ey = cy(a);
+    if (ex == 0 && ey == 0) return R(0);
+    if (ex == 0) return ey > 0 ? vy : -vy;
+    if (ey == 0) return ex > 0 ? vx : -vx;
+    return (ex > 0 ? vx : -vx) + (ey > 0 ? vy : -vy);
+}
+
 template <typename R, typename B>
 struct Stencil {
     R c, e, w, n, s, ne, nw, sw, se;
@@ -417,7 +428,7 @@ __device__ __forceinline__ void collide_tile(const LbmArgs<T, typename Compute<T
     R dev[9];
 #pragma unroll
     for (int a = 0; a < 9; a++) {
-        const R eu = B(cx(a)) * ux + B(cy(a)) * uy;
+        const R eu = edot(a, ux, uy);
         dev[a] = B(3) * eu + B(4.5) * eu * eu - uu;
     }
 
@@ -431,10 +442,12 @@ __device__ __forceinline__ void collide_tile(const LbmArgs<T, typename Compute<T
 #pragma unroll
     for (int a = 0; a < 9; a++) {
         const B w = wgt<B>(a);
-        R v = w * ((pst + dev[a]) + (B(cx(a)) * Ftx + B(cy(a)) * Fty));
-        const B rxx = (a == 1 || a == 3) ? B(1) : ((a == 2 || a == 4) ? B(-1) : B(0));
-        const B rxy = (a == 5 || a == 7) ? B(1) : ((a == 6 || a == 8) ? B(-1) : B(0));
-        v += rel * (rxx * dxx + rxy * dxy);
+        R v = w * (a == 0 ? pst + dev[a] : (pst + dev[a]) + edot(a, Ftx, Fty));
+        // rows of p_xx (+1 on 1, 3; -1 on 2, 4) and p_xy (+1 on 5, 7; -1 on 6, 8)
+        if (a == 1 || a == 3) v += rel * dxx;
+        else if (a == 2 || a == 4) v += rel * -dxx;
+        else if (a == 5 || a == 7) v += rel * dxy;
+        else if (a == 6 || a == 8) v += rel * -dxy;
         if (walled(a)) st_pop(fd, opp(a), 9, ps32, n32, v + f_off<MODE, B>(opp(a)));
         else if (!leaves(a)) st_pop(fd, a, 9, ps32, dest(a), v + f_off<MODE, B>(a));
     }
@@ -479,7 +492,8 @@ __device__ __forceinline__ void collide_tile(const LbmArgs<T, typename Compute<T
             R gv;
             if constexpr (EARLY) gv = R(gpre[i * 9 + a]) - g_off<MODE, B>(a);
             else gv = ld_pop<R>(gs, i * 9 + a, 18, ps32, n32) - g_off<MODE, B>(a);
-            const R v = P.keep_phi * gv + w * (ophi * (B(1) + dev[a]) + (B(cx(a)) * sqx + B(cy(a)) * sqy));
+            const R v = P.keep_phi * gv +
+                        w * (a == 0 ? ophi * (B(1) + dev[a]) : ophi * (B(1) + dev[a]) + edot(a, sqx, sqy));
             const R out = v + g_off<MODE, B>(walled(a) ? opp(a) : a);
             if constexpr (CONSERVE) {
                 const S sv = S(out);

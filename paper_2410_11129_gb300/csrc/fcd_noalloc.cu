@@ -10,7 +10,6 @@
 // device array reserved when the library is loaded.
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 
 #include "fcd_internal.cuh"
 
@@ -32,11 +31,6 @@ static_assert(observe_scratch_doubles_of(NOALLOC_MAX_NX, NOALLOC_MAX_NODES / NOA
 // Scratch shared by every call: phase planes, column records, result block.
 static __device__ __align__(256) double noalloc_scratch[NOALLOC_DOUBLES];
 
-// Device address of the scratch array, resolved once per device.
-constexpr int MAX_DEVICES = 64;
-static double *scratch_addr[MAX_DEVICES];
-static std::mutex scratch_mutex;
-
 // A rejected call returns its status and states the reason on stderr.
 fcd_status noalloc_fail(fcd_status st, const char *msg) {
     fprintf(stderr, "fcd_observe_populations_noalloc: %s\n", msg);
@@ -57,20 +51,15 @@ extern "C" fcd_status fcd_observe_populations_noalloc(const double *g, int nx, i
     if (nx > NOALLOC_MAX_NX || (long long)nx * ny > NOALLOC_MAX_NODES)
         return noalloc_fail(FCD_EINVAL,
                             "lattice larger than the static scratch (nx <= 16384, nx*ny <= 524288)");
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES)
-        return noalloc_fail(FCD_ECUDA, "cannot query the current device");
-    double *scratch = nullptr;
+    // The array's address in the current device's context, looked up on every
+    // call (a host-side query that allocates nothing), so that it stays right
+    // after the context is torn down and created again.
+    void *sym = nullptr;
     {
-        std::lock_guard<std::mutex> lock(scratch_mutex);
-        if (!scratch_addr[dev]) {
-            void *p = nullptr;
-            const cudaError_t e = cudaGetSymbolAddress(&p, noalloc_scratch);
-            if (e != cudaSuccess) return noalloc_fail(FCD_ECUDA, cudaGetErrorString(e));
-            scratch_addr[dev] = static_cast<double *>(p);
-        }
-        scratch = scratch_addr[dev];
+        const cudaError_t e = cudaGetSymbolAddress(&sym, noalloc_scratch);
+        if (e != cudaSuccess) return noalloc_fail(FCD_ECUDA, cudaGetErrorString(e));
     }
+    double *scratch = static_cast<double *>(sym);
     Phys<double> P;
     memset(&P, 0, sizeof P);
     P.nx = nx;
