@@ -2,7 +2,8 @@
 // sweep of arXiv 2410.11129, Sec. 3.7: Bo_m x Ca grids of separate runs).
 //
 // Every instance is a full context (its own state, observables, snapshots).
-// Periodic FP32 instances of one storage form make a group that one fixed
+// Periodic FP32 instances of one storage form (and one level-0 form of the
+// potential) make a group that one fixed
 // set of batched kernels advances, one CUDA graph per step:
 //   - the phase recovery of every instance in one launch over a work list of
 //     32 x 8 tiles spanning all instances;
@@ -396,7 +397,8 @@ fcd_status fcd_batch_create(const fcd_params *params, int n, fcd_batch **out) {
         b->inst.push_back(c);
         fcd_set_stream(c, s);
     }
-    // group the periodic FP32 instances by storage form, and split each form
+    // group the periodic FP32 instances by storage form and level-0 form of the
+    // potential (one FP32 plane or the hi + lo pair), and split each such set
     // into about one group per GROUP_NODES lattice nodes (at most MAX_SPLIT),
     // balanced by nodes: every group has its own stream, so the latency-bound
     // solve kernels of one group overlap the bandwidth-bound launches of
@@ -407,12 +409,14 @@ fcd_status fcd_batch_create(const fcd_params *params, int n, fcd_batch **out) {
     const int MAX_SPLIT = 8;
     int forced = 0;
     if (const char *gs = getenv("FCD_BATCH_GROUPS")) forced = atoi(gs);
-    for (int form : {MODE_FP32, MODE_FP32_OFFSET}) {
+    for (int key = 0; key < 4; key++) {  // storage form x level-0 form of the potential
+        const int form = key < 2 ? MODE_FP32 : MODE_FP32_OFFSET, comp = key & 1;
         std::vector<std::pair<long long, int>> mem;  // (nodes, instance), largest first
         std::vector<EngineView> views(n);
         double total = 0.0;
         for (int i = 0; i < n; i++) {
-            if (!engine_view(b->inst[i], &views[i]) || views[i].mode != form) continue;
+            if (!engine_view(b->inst[i], &views[i]) || views[i].mode != form || views[i].comp != comp)
+                continue;
             const long long nodes = (long long)views[i].P.nx * views[i].P.ny;
             mem.push_back({nodes, i});
             total += (double)nodes;

@@ -1324,6 +1324,7 @@ struct MgBatchCtl {
 constexpr int BS_FIRST = 0;  // the sweeps that open every solve
 constexpr int BS_CYCLE = 1;  // the lattice part that ends every cycle
 
+template <bool COMP>
 __global__ void __launch_bounds__(QT) smooth0_batch(const MgBatchInst *tab, const MgBatchTile *tiles,
                                                     int kind) {
     const MgBatchTile t = tiles[blockIdx.x];
@@ -1337,16 +1338,13 @@ __global__ void __launch_bounds__(QT) smooth0_batch(const MgBatchInst *tab, cons
     }
     const int q0 = t.by * I.gx0 + t.bx;
     for (int q = q0; q < q0 + t.cnt; q++) {
-        if (I.L0.comp)
-            smooth0_tile<float, true, false>(I.L0, I.lv[1], add, sweeps, I.H0c, I.H0s, I.ctl, kind == BS_FIRST,
-                                      q % I.gx0, q / I.gx0, I.n0);
-        else
-            smooth0_tile<float, false, false>(I.L0, I.lv[1], add, sweeps, I.H0c, I.H0s, I.ctl,
-                                       kind == BS_FIRST, q % I.gx0, q / I.gx0, I.n0);
+        smooth0_tile<float, COMP>(I.L0, I.lv[1], add, sweeps, I.H0c, I.H0s, I.ctl, kind == BS_FIRST,
+                                  q % I.gx0, q / I.gx0, I.n0);
         __syncthreads();  // the tile's shared arrays are reused by the next one
     }
 }
 
+template <bool COMP>
 __global__ void __launch_bounds__(256) resid0_batch(const MgBatchInst *tab, const MgBatchTile *tiles,
                                                     MgBatchCtl *bc, int ninst,
                                                     cudaGraphConditionalHandle hw,
@@ -1357,12 +1355,8 @@ __global__ void __launch_bounds__(256) resid0_batch(const MgBatchInst *tab, cons
     if (!I.ctl->done) {  // uniform across the block
         const int q0 = t.by * I.gx1 + t.bx;
         for (int q = q0; q < q0 + t.cnt; q++) {
-            if (I.L0.comp)
-                resid0_tile<float, true, false>(I.L0, I.lv[1], I.H0c, I.H0s, I.ctl, 0, 0, 0, q % I.gx1,
-                                         q / I.gx1, I.n1, false);
-            else
-                resid0_tile<float, false, false>(I.L0, I.lv[1], I.H0c, I.H0s, I.ctl, 0, 0, 0, q % I.gx1,
-                                          q / I.gx1, I.n1, false);
+            resid0_tile<float, COMP>(I.L0, I.lv[1], I.H0c, I.H0s, I.ctl, 0, 0, 0, q % I.gx1, q / I.gx1,
+                                     I.n1, false);
             __syncthreads();  // the tile's shared arrays are reused by the next one
         }
     }
@@ -1422,6 +1416,7 @@ __global__ void __launch_bounds__(CTA_THREADS) coarse_batch(const MgBatchInst *t
 
 struct MgBatch {
     int ninst = 0, maxlc = 1;
+    int comp = 0;  // the instances' level-0 form (one for the whole batch)
     MgBatchInst *d_tab = nullptr;
     MgBatchCtl *d_ctl = nullptr;
     int *d_inst = nullptr;                     // every instance (coarse blocks)
@@ -1442,6 +1437,13 @@ MgBatch *mg_batch_create(const std::vector<MgHost<float> *> &ms, const std::vect
     b->release = release;
     b->user = user;
     b->ninst = (int)ms.size();
+    b->comp = ms.empty() ? 0 : ms[0]->L0.comp;
+    for (const MgHost<float> *m : ms)
+        if (m->L0.comp != b->comp) {
+            snprintf(err, errlen, "multigrid batch: instances of both level-0 forms");
+            delete b;
+            return nullptr;
+        }
     Uploader up{alloc, user, &b->mem};
     std::vector<MgBatchInst> tab;
     std::vector<MgBatchTile> t0, t1, tl1;
@@ -1526,7 +1528,8 @@ void mg_batch_destroy(MgBatch *b) {
 }
 
 void mg_batch_presmooth(MgBatch *b, cudaStream_t s) {
-    smooth0_batch<<<b->n_t0, QT, 0, s>>>(b->d_tab, b->d_t0, BS_FIRST);
+    if (b->comp) smooth0_batch<true><<<b->n_t0, QT, 0, s>>>(b->d_tab, b->d_t0, BS_FIRST);
+    else smooth0_batch<false><<<b->n_t0, QT, 0, s>>>(b->d_tab, b->d_t0, BS_FIRST);
 }
 
 // One pass of the loop body, in three parts: every instance's cycle head
@@ -1538,8 +1541,12 @@ void mg_batch_presmooth(MgBatch *b, cudaStream_t s) {
 // their launches.
 void mg_batch_head(MgBatch *b, cudaGraphConditionalHandle hw, cudaGraphConditionalHandle hv,
                    cudaGraphConditionalHandle ht, int in_graph, cudaStream_t s) {
-    resid0_batch<<<b->n_t1, dim3(32, 8), 0, s>>>(b->d_tab, b->d_t1, b->d_ctl, b->ninst, hw, hv, ht,
-                                                 in_graph);
+    if (b->comp)
+        resid0_batch<true><<<b->n_t1, dim3(32, 8), 0, s>>>(b->d_tab, b->d_t1, b->d_ctl, b->ninst, hw,
+                                                           hv, ht, in_graph);
+    else
+        resid0_batch<false><<<b->n_t1, dim3(32, 8), 0, s>>>(b->d_tab, b->d_t1, b->d_ctl, b->ninst, hw,
+                                                            hv, ht, in_graph);
 }
 
 void mg_batch_vcycle(MgBatch *b, cudaStream_t s) {
@@ -1557,7 +1564,8 @@ void mg_batch_twogrid(MgBatch *b, cudaStream_t s) {
 }
 
 void mg_batch_close(MgBatch *b, cudaStream_t s) {
-    smooth0_batch<<<b->n_t0, QT, 0, s>>>(b->d_tab, b->d_t0, BS_CYCLE);
+    if (b->comp) smooth0_batch<true><<<b->n_t0, QT, 0, s>>>(b->d_tab, b->d_t0, BS_CYCLE);
+    else smooth0_batch<false><<<b->n_t0, QT, 0, s>>>(b->d_tab, b->d_t0, BS_CYCLE);
 }
 
 void mg_batch_body(MgBatch *b, cudaStream_t s) {
