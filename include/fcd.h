@@ -215,7 +215,8 @@ const char *fcd_last_error(const fcd_ctx *ctx);
 /* ---- Batched form: many independent channels (the Bo_m x Ca regime map of
  * Sec. 3.7 is a grid of separate runs). Each instance is a full context (its
  * own state; every fcd_* call works on it). Two ways to step them (see
- * fcd_batch_tuning): the periodic FP32 instances of one storage form advanced
+ * fcd_batch_tuning): the periodic FP32 instances of one storage form and one
+ * level-0 form of the potential (a tolerance below 1e-4 or not) advanced
  * together by one fixed set of kernels per step, each launched once over a
  * work list of tiles that spans them (phase recovery, a single loop of
  * batched multigrid kernels in which every instance runs the cycle its own
@@ -245,7 +246,8 @@ int fcd_batch_size(const fcd_batch *b);
  * single steps, the first two of which build the graphs, the last four timed
  * alternately; the faster mode is kept (the environment variable
  * FCD_BATCH_MODE=0 or 1 at create fixes it instead). *batched = instances the
- * batched kernels advance, *groups = their groups (each storage form split
+ * batched kernels advance, *groups = their groups (each set of one storage
+ * form and one level-0 potential form split
  * into about one group per 6 M lattice nodes, at most 8, balanced by nodes,
  * each group on its own stream; FCD_BATCH_GROUPS=k at create fixes the
  * split), tile_h[g] for g < tile_h_len = the collide-stream tile height the
