@@ -41,10 +41,10 @@ COLLIDE_BYTES_PER_NODE_F32 = 240
 # rows (null once the source changes). On 1600x200 the 37 MB of output stays in
 # L2 when the launch ends, so only the reads reach DRAM inside the launch.
 NCU_TRAFFIC = {
-    ("1e26f70e1a6dfb72", "1600x200", 4): 38429184 + 244224,
-    ("1e26f70e1a6dfb72", "1600x200", 8): 38431488 + 245760,
-    ("1e26f70e1a6dfb72", "9600x1200", 4): 1383204352 + 1205312768,
-    ("1e26f70e1a6dfb72", "9600x1200", 8): 1383481600 + 1205077504,
+    ("b5b068562d18f977", "1600x200", 4): 38430464 + 242432,
+    ("b5b068562d18f977", "1600x200", 8): 38433536 + 257792,
+    ("b5b068562d18f977", "9600x1200", 4): 1383248896 + 1206289152,
+    ("b5b068562d18f977", "9600x1200", 8): 1383520256 + 1206574080,
 }
 
 
