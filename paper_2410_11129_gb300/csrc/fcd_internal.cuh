@@ -162,6 +162,7 @@ struct MgCtl {
     long long smooth_cycles;       // cumulative lattice-sweep cycles (launch accounting)
     long long twogrid_cycles;      // cumulative two-grid cycles (launch accounting)
     unsigned batch_visits;         // batched solves: blocks of the current residual launch seen
+    long long dispatches;          // cumulative cycle dispatch launches of graph loops (accounting)
 };
 
 // What the phase kernel does besides Eq. 32: reset the solve's control block
@@ -306,6 +307,10 @@ template <typename T>
 void mg_presmooth(MgHost<T> *m, T H0c, T H0s, cudaStream_t s);  // opens every solve
 template <typename T>
 int mg_kernels_per_cycle(const MgHost<T> *m);
+// Graph form of the cycle loop: a one-thread kernel at the top of the loop body
+// that sets the body's switch node from the mode the last head chose.
+template <typename T>
+void mg_cycle_dispatch(MgHost<T> *m, cudaGraphConditionalHandle hswitch, cudaStream_t s);
 // Tangent solves (FP64): explicit right-hand side on level 0; reset of the
 // control block with tolerance tol * max|rhs|; right-hand side along one
 // direction, L(k) dpsi' = b(k, dH0) + b(dk, H0) - L(dk) psi'; copies between

@@ -962,7 +962,9 @@ __global__ void __launch_bounds__(CTA_THREADS) coarse_cta(const Level<T> *lv, in
 // Start of a cycle (one thread, after the lattice residual is complete):
 // converged, capped or non-finite -> record the result and stop; otherwise run
 // a V-cycle, or only lattice sweeps when the residual is already close to the
-// tolerance. Sets the graph's while and switch conditions.
+// tolerance. In a graph it sets the loop and switch conditions (in_graph 1),
+// or the loop condition only (in_graph 3: the loop body's dispatch kernel sets
+// the switch from ctl->mode).
 __device__ void cycle_decide(MgCtl *ctl, cudaGraphConditionalHandle hw,
                              cudaGraphConditionalHandle hi, int in_graph) {
     ctl->cycles_launched++;
@@ -989,12 +991,23 @@ __device__ void cycle_decide(MgCtl *ctl, cudaGraphConditionalHandle hw,
     } else {
         ctl->mode = 0;  // full V-cycle
     }
-    if (in_graph) {
+    if (in_graph == 1) {
         // switch node: 0 V-cycle, 1 lattice sweeps, 2 two-grid, 3 no body
         cudaGraphSetConditional(hi, (unsigned)ctl->mode);
         cudaGraphSetConditional(hw, ctl->keep_going ? 1u : 0u);
+    } else if (in_graph == 3) {  // the loop condition only (the body dispatches the mode)
+        cudaGraphSetConditional(hw, ctl->keep_going ? 1u : 0u);
     }
 }
+
+__global__ void cycle_dispatch_kernel(MgCtl *ctl, cudaGraphConditionalHandle hs) {
+    if (threadIdx.x == 0) {
+        ctl->dispatches++;
+        cudaGraphSetConditional(hs, (unsigned)ctl->mode);
+    }
+}
+
+
 
 // End of a full cycle (one thread): count it, flip the lattice buffer, clear
 // the norm for the next residual.
@@ -1237,6 +1250,11 @@ void mg_destroy(MgHost<T> *m) {
 }
 
 static dim3 g2(int nx, int ny, dim3 b) { return dim3((nx + b.x - 1) / b.x, (ny + b.y - 1) / b.y); }
+
+template <typename T>
+void mg_cycle_dispatch(MgHost<T> *m, cudaGraphConditionalHandle hs, cudaStream_t s) {
+    cycle_dispatch_kernel<<<1, 32, 0, s>>>(m->ctl, hs);
+}
 
 template <typename T>
 void mg_cycle_head(MgHost<T> *m, T H0c, T H0s, cudaGraphConditionalHandle hw,
@@ -1693,6 +1711,7 @@ void mg_psi_io(MgHost<double> *m, int op, double *plane, double *prev, cudaStrea
     template void mg_cycle_twogrid<T>(MgHost<T> *, T, T, cudaStream_t);                          \
     template void mg_presmooth<T>(MgHost<T> *, T, T, cudaStream_t);                              \
     template int mg_kernels_per_cycle<T>(const MgHost<T> *);                                    \
+    template void mg_cycle_dispatch<T>(MgHost<T> *, cudaGraphConditionalHandle, cudaStream_t);    \
     template int mg_levels<T>(const MgHost<T> *);                                               \
     template void mg_set_rhs<T>(MgHost<T> *, const T *);
 FCD_MG_INST(float)

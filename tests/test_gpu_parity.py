@@ -225,16 +225,30 @@ def test_checkpoint_resume_bitwise(fcd):
         b.close()
 
 
-def test_graph_and_host_loop_agree(fcd, monkeypatch):
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp64", 1e-5), ("fp32", 1e-4),
+                                      ("fp32", 1e-5), ("fp32_offset", 1e-5)])
+def test_graph_and_host_loop_agree(fcd, monkeypatch, prec, tol):
+    """The graph's cycle loop (the while form below a tolerance of 1e-5, the IF
+    form from 1e-5 on) and the host-driven loop run the same kernels in the same
+    order: bitwise the same state, and the same cycle counts, after 25 steps that
+    include solves needing more than their first cycle head."""
     from paper_2410_11129_gb300 import fcd as F
-    cfg = dict(parity_cfg(mag_tol=1e-10), precision="fp64")
+    cfg = dict(parity_cfg(mag_tol=tol), precision=prec)
     a = F.Channel(cfg)
+    s0 = a.solver_stats()
     a.step(25)
+    sa = a.solver_stats()
     monkeypatch.setenv("FCD_NO_GRAPH", "1")
     b = F.Channel(cfg)
+    t0 = b.solver_stats()
     b.step(25)
+    sb = b.solver_stats()
     for x, y in zip(a.populations(), b.populations()):
         assert np.array_equal(x, y)
+    assert {k: sa[k] - s0[k] for k in sa} == {k: sb[k] - t0[k] for k in sb}
+    print(prec, tol, {k: sa[k] - s0[k] for k in sa})
+    if tol <= 1e-5:
+        assert sa["heads"] - s0["heads"] > 25  # some solve ran a cycle after its first head
     a.close()
     b.close()
 
