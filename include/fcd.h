@@ -281,7 +281,7 @@ void fcd_batch_destroy(fcd_batch *b);
  * (primal values), fcd_get_field (primal fields), fcd_kernel_launches,
  * fcd_solver_stats, fcd_last_error and fcd_destroy; state snapshots and
  * population import return FCD_ESTATE. Each step runs as one captured CUDA
- * graph (the primal and the four tangent solves as while-node loops, as in
+ * graph (the primal and the four tangent solves as conditional-node loops, as in
  * fcd_step), with no host synchronisation between steps; with the environment
  * variable FCD_NO_GRAPH=1 the solves are driven from the host instead, one
  * synchronisation per multigrid cycle. */
