@@ -2,9 +2,9 @@
 // sweep of arXiv 2410.11129, Sec. 3.7: Bo_m x Ca grids of separate runs).
 //
 // Every instance is a full context (its own state, observables, snapshots).
-// Periodic FP32 instances of one storage form (and one level-0 form of the
-// potential) make a group that one fixed
-// set of batched kernels advances, one CUDA graph per step:
+// Periodic FP32 instances of one storage form and one level-0 form of the
+// potential make a group that one fixed set of batched kernels advances, one
+// CUDA graph per step:
 //   - the phase recovery of every instance in one launch over a work list of
 //     32 x 8 tiles spanning all instances;
 //   - the potential solves of every instance in one loop of batched multigrid
