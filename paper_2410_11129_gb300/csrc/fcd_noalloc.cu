@@ -10,6 +10,7 @@
 // device array reserved when the library is loaded.
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "fcd_internal.cuh"
 
@@ -31,6 +32,12 @@ static_assert(observe_scratch_doubles_of(NOALLOC_MAX_NX, NOALLOC_MAX_NODES / NOA
 // Scratch shared by every call: phase planes, column records, result block.
 static __device__ __align__(256) double noalloc_scratch[NOALLOC_DOUBLES];
 
+// Device address of the scratch array, looked up by the first call on each
+// device (with that device current) and kept for the process.
+constexpr int MAX_DEVICES = 64;
+static double *scratch_addr[MAX_DEVICES];
+static std::mutex scratch_mutex;
+
 // A rejected call returns its status and states the reason on stderr.
 fcd_status noalloc_fail(fcd_status st, const char *msg) {
     fprintf(stderr, "fcd_observe_populations_noalloc: %s\n", msg);
@@ -51,15 +58,22 @@ extern "C" fcd_status fcd_observe_populations_noalloc(const double *g, int nx, i
     if (nx > NOALLOC_MAX_NX || (long long)nx * ny > NOALLOC_MAX_NODES)
         return noalloc_fail(FCD_EINVAL,
                             "lattice larger than the static scratch (nx <= 16384, nx*ny <= 524288)");
-    // The array's address in the current device's context, looked up on every
-    // call (a host-side query that allocates nothing), so that it stays right
-    // after the context is torn down and created again.
-    void *sym = nullptr;
+    // In host code noalloc_scratch names a host-side stand-in, not device memory:
+    // the kernels get the array's device address, set up once per device.
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES)
+        return noalloc_fail(FCD_ECUDA, "cannot query the current device");
+    double *scratch = nullptr;
     {
-        const cudaError_t e = cudaGetSymbolAddress(&sym, noalloc_scratch);
-        if (e != cudaSuccess) return noalloc_fail(FCD_ECUDA, cudaGetErrorString(e));
+        std::lock_guard<std::mutex> lock(scratch_mutex);
+        if (!scratch_addr[dev]) {
+            void *p = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&p, noalloc_scratch);
+            if (e != cudaSuccess) return noalloc_fail(FCD_ECUDA, cudaGetErrorString(e));
+            scratch_addr[dev] = static_cast<double *>(p);
+        }
+        scratch = scratch_addr[dev];
     }
-    double *scratch = static_cast<double *>(sym);
     Phys<double> P;
     memset(&P, 0, sizeof P);
     P.nx = nx;
